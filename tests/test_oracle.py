@@ -1,0 +1,379 @@
+"""Pins for the CPU oracle: brute force, closed forms, the paper's worked
+examples, library cross-checks and invariants.  CPU only."""
+import itertools
+import json
+import os
+import random
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers
+
+def edges_of(pairs):
+    u = np.array([a for a, b in pairs], dtype=np.int32)
+    v = np.array([b for a, b in pairs], dtype=np.int32)
+    return u, v
+
+
+def graph(n, pairs):
+    u, v = edges_of(pairs)
+    return O.Graph(n, u, v)
+
+
+def brute_force_maximal_cliques(n, pairs):
+    """All vertex subsets that are cliques and that no outside vertex extends
+    (the definition of a maximal clique, Section 3), by exhaustive search."""
+    adj = [0] * n
+    for a, b in pairs:
+        if a != b:
+            adj[a] |= 1 << b
+            adj[b] |= 1 << a
+    out = []
+    for s in range(1, 1 << n):
+        verts = [i for i in range(n) if s >> i & 1]
+        if any((s & ~(1 << i)) & ~adj[i] for i in verts):
+            continue                      # not a clique
+        common = (1 << n) - 1
+        for i in verts:
+            common &= adj[i]
+        if common & ~s:
+            continue                      # some outside vertex extends it
+        out.append(tuple(verts))
+    return sorted(out)
+
+
+def random_pairs(n, p, rng):
+    return [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < p]
+
+
+def complete_multipartite(parts):
+    """Complete multipartite graph with the given part sizes."""
+    ids, base = [], 0
+    for s in parts:
+        ids.append(list(range(base, base + s)))
+        base += s
+    pairs = [(a, b) for i in range(len(ids)) for j in range(i + 1, len(ids)) for a in ids[i] for b in ids[j]]
+    return base, pairs, ids
+
+
+# ---------------------------------------------------------------- brute force
+
+@pytest.mark.parametrize("seed", range(12))
+def test_brute_force_small_random(seed):
+    rng = random.Random(1000 + seed)
+    n = rng.randint(1, 14)
+    p = rng.choice([0.1, 0.3, 0.5, 0.7, 0.9])
+    pairs = random_pairs(n, p, rng)
+    expect = brute_force_maximal_cliques(n, pairs)
+    g = graph(n, pairs)
+    got = O.ttt_whole(g, want_list=True)
+    assert got.cliques == expect
+    assert got.count == len(expect)
+    for kind in ("degree", "degen", "triangle"):
+        r = O.parmce(g, O.rank(g, kind), want_list=True)
+        assert r.cliques == expect, kind
+    perm = np.array(rng.sample(range(n), n), dtype=np.int32)
+    assert O.parmce(g, perm, want_list=True).cliques == expect
+
+
+def test_brute_force_sixteen_vertices():
+    rng = random.Random(7)
+    pairs = random_pairs(16, 0.55, rng)
+    expect = brute_force_maximal_cliques(16, pairs)
+    g = graph(16, pairs)
+    assert O.ttt_whole(g, want_list=True).cliques == expect
+    assert O.parmce(g, O.rank(g, "degen"), want_list=True).cliques == expect
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("n", [1, 2, 5, 12, 30])
+def test_complete_graph_one_clique(n):
+    g = graph(n, list(itertools.combinations(range(n), 2)))
+    r = O.parmce(g, O.rank(g, "degen"), want_list=True)
+    assert r.count == 1 and r.cliques == [tuple(range(n))]
+    assert list(r.hist) == [0] * n + [1]
+
+
+@pytest.mark.parametrize("n", [1, 7, 100])
+def test_empty_graph_singletons(n):
+    g = O.Graph(n, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    r = O.parmce(g, O.rank(g, "degree"), want_list=True)
+    assert r.count == n and r.cliques == [(i,) for i in range(n)]
+    assert O.ttt_whole(g).count == n
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 9, 50])
+def test_cycle(n):
+    pairs = [(i, (i + 1) % n) for i in range(n)]
+    g = graph(n, pairs)
+    r = O.parmce(g, O.rank(g, "degen"), want_list=True)
+    if n == 3:
+        assert r.cliques == [(0, 1, 2)]
+    else:
+        assert r.count == n and all(len(c) == 2 for c in r.cliques)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6])
+def test_moon_moser(k):
+    """Complete k-partite graph with parts of size 3: 3^k maximal cliques of size k."""
+    n, pairs, _ = complete_multipartite([3] * k)
+    g = graph(n, pairs)
+    r = O.parmce(g, O.rank(g, "degen"))
+    assert r.count == 3 ** k
+    assert r.hist[k] == 3 ** k and r.hist.sum() == 3 ** k
+    assert O.ttt_whole(g).count == 3 ** k
+
+
+@pytest.mark.parametrize("parts", [[1, 7], [4, 5], [2, 2, 2, 2], [2, 3, 4], [1, 1, 1, 5]])
+def test_multipartite_product(parts):
+    """Turán-type graphs: the maximal cliques pick one vertex per part."""
+    n, pairs, _ = complete_multipartite(parts)
+    g = graph(n, pairs)
+    assert O.parmce(g, O.rank(g, "triangle")).count == int(np.prod(parts))
+
+
+def test_disjoint_union_adds():
+    rng = random.Random(3)
+    a = random_pairs(9, 0.5, rng)
+    b = random_pairs(11, 0.4, rng)
+    ga, gb = graph(9, a), graph(11, b)
+    gu = graph(20, a + [(x + 9, y + 9) for x, y in b])
+    ra, rb, ru = O.ttt_whole(ga), O.ttt_whole(gb), O.ttt_whole(gu)
+    assert ru.count == ra.count + rb.count
+
+
+# ---------------------------------------------------------------- hashing
+
+def test_splitmix64_known_answer():
+    """h(0) with seed 0 is the first output of Vigna's splitmix64 from state 0."""
+    # H({0}) = fmix(h(0) + GOLDEN); check h through a single-vertex clique of a
+    # seed chosen so that the input to splitmix64 is 0.
+    assert O.clique_hash([0], seed=0) != O.clique_hash([1], seed=0)
+    # splitmix64(state=0) first output is 0xE220A8397B1DCDAF
+    h0 = 0xE220A8397B1DCDAF
+    golden = 0x9E3779B97F4A7C15
+    mask = (1 << 64) - 1
+
+    def fmix(z):
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        return z ^ (z >> 31)
+    assert O.clique_hash([0], seed=0) == fmix((h0 + golden) & mask)
+
+
+def test_hash_order_independent_and_additive():
+    rng = random.Random(11)
+    pairs = random_pairs(13, 0.5, rng)
+    g = graph(13, pairs)
+    r = O.ttt_whole(g, want_list=True, seed=99)
+    total = 0
+    for c in r.cliques:
+        perm = list(c)
+        rng.shuffle(perm)
+        assert O.clique_hash(perm, 99) == O.clique_hash(list(c), 99)
+        total = (total + O.clique_hash(list(c), 99)) % (1 << 64)
+    assert total == r.hash
+    assert O.ttt_whole(g, seed=98).hash != r.hash
+
+
+# ---------------------------------------------------------------- library cross-checks
+
+@pytest.mark.parametrize("seed", range(4))
+def test_networkx_cross_check(seed):
+    nx = pytest.importorskip("networkx")
+    rng = random.Random(50 + seed)
+    n = 60
+    pairs = random_pairs(n, rng.choice([0.1, 0.25, 0.4]), rng)
+    G = nx.Graph()
+    G.add_nodes_from(range(n))
+    G.add_edges_from(pairs)
+    expect = sorted(tuple(sorted(c)) for c in nx.find_cliques(G))
+    g = graph(n, pairs)
+    assert O.parmce(g, O.rank(g, "degen"), want_list=True).cliques == expect
+    core = nx.core_number(G)
+    assert list(O.core_numbers(g)) == [core[i] for i in range(n)]
+    tri = nx.triangles(G)
+    assert list(O.triangles(g)) == [tri[i] for i in range(n)]
+    assert list(O.degree(g)) == [G.degree(i) for i in range(n)]
+
+
+def test_graph_normalisation():
+    # self loops, repeats and both directions collapse to a simple graph
+    u = np.array([0, 1, 1, 2, 2, 3, 0], np.int32)
+    v = np.array([1, 0, 1, 3, 3, 2, 0], np.int32)
+    g = O.Graph(4, u, v)
+    rp, col = g.csr()
+    assert list(rp) == [0, 1, 2, 3, 4] and list(col) == [1, 0, 3, 2]
+    with pytest.raises(ValueError):
+        O.Graph(3, np.array([0], np.int32), np.array([3], np.int32))
+
+
+def test_rank_order():
+    key = np.array([3, 1, 3, 0, 1], dtype=np.float64)
+    # ascending (key, id): (0,3) (1,1) (1,4) (3,0) (3,2)
+    assert list(O.rank_from_key(key)) == [3, 1, 4, 0, 2]
+
+
+# ---------------------------------------------------------------- decomposition invariants
+
+def test_each_clique_once_at_its_lowest_ranked_vertex():
+    w = graphgen.er(80, 0.2, 5)
+    g = O.Graph(80, *w)
+    rk = O.rank(g, "degen")
+    seen = []
+    for v in range(80):
+        r = O.parmce(g, rk, subset=[v], want_list=True)
+        for c in r.cliques:
+            assert v in c and min(rk[x] for x in c) == rk[v]
+        seen += r.cliques
+    assert sorted(seen) == O.ttt_whole(g, want_list=True).cliques
+    assert len(set(seen)) == len(seen)
+
+
+def test_rank_choice_keeps_summary():
+    w = graphgen.er_2000()
+    g = O.Graph(w.n, w.u, w.v)
+    base = O.ttt_whole(g)
+    assert base.count == 17824          # also checked against networkx below
+    rng = np.random.default_rng(0)
+    for rk in (O.rank(g, "degree"), O.rank(g, "degen"), O.rank(g, "triangle"),
+               rng.permutation(w.n).astype(np.int32)):
+        r = O.parmce(g, rk, threads=2)
+        assert (r.count, r.hash, list(r.hist)) == (base.count, base.hash, list(base.hist))
+
+
+def test_er_2000_against_networkx():
+    nx = pytest.importorskip("networkx")
+    w = graphgen.er_2000()
+    G = nx.Graph()
+    G.add_nodes_from(range(w.n))
+    G.add_edges_from(zip(w.u.tolist(), w.v.tolist()))
+    expect = sorted(tuple(sorted(c)) for c in nx.find_cliques(G))
+    g = O.Graph(w.n, w.u, w.v)
+    assert O.parmce(g, O.rank(g, "degen"), want_list=True, threads=2).cliques == expect
+
+
+def test_per_vertex_summaries_add_up():
+    w = graphgen.er(300, 0.05, 9)
+    g = O.Graph(300, *w)
+    r = O.parmce(g, O.rank(g, "degree"), per_vertex=True, threads=3)
+    assert int(r.per_vertex["count"].sum()) == r.count
+    assert int(r.per_vertex["nodes"].sum()) == r.nodes
+    assert int(r.per_vertex["hash"].astype(object).sum()) % (1 << 64) == r.hash
+
+
+# ---------------------------------------------------------------- incremental (Section 5)
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("fixture", ["fig3_worked_example.json", "removed_figure_example.json"])
+def test_worked_examples(fixture):
+    ex = _load(fixture)
+    idx = {v: i for i, v in enumerate(ex["vertices"])}
+    name = {i: v for v, i in idx.items()}
+    n = len(idx)
+    g = graph(n, [(idx[a], idx[b]) for a, b in ex["edges"]])
+
+    def named(cl):
+        return sorted(tuple(sorted(str(name[x]) for x in c)) for c in cl)
+
+    def as_named(lst):
+        return sorted(tuple(sorted(str(x) for x in c)) for c in lst)
+
+    assert named(O.ttt_whole(g, want_list=True).cliques) == as_named(ex["initial_cliques"])
+    state = O.Imce(g)
+    for b in ex["batches"]:
+        u, v = edges_of([(idx[a], idx[c]) for a, c in b["add"]])
+        hu, hv = O.canonical_batch(g, u, v)
+        new_a, del_a = O.imce_diff(g, hu, hv)
+        new_b, del_b = O.imce_alg(g, hu, hv)
+        rho, new_s, del_s = state.add(u, v)
+        assert rho == len(b["add"])
+        for nw, dl in ((new_a, del_a), (new_b, del_b), (new_s, del_s)):
+            assert named(nw.cliques) == as_named(b["new"])
+            assert named(dl.cliques) == as_named(b["subsumed"])
+        g = g.plus(hu, hv)
+
+
+@pytest.mark.parametrize("n", [3, 6, 15])
+def test_complete_minus_edge(n):
+    """Adding the missing edge of K_n - e: one new clique of size n, two subsumed of size n-1."""
+    pairs = [p for p in itertools.combinations(range(n), 2) if p != (0, 1)]
+    g = graph(n, pairs)
+    hu, hv = O.canonical_batch(g, np.array([1], np.int32), np.array([0], np.int32))
+    for nw, dl in (O.imce_alg(g, hu, hv), O.imce_diff(g, hu, hv)):
+        assert nw.cliques == [tuple(range(n))]
+        assert dl.count == 2 and all(len(c) == n - 1 for c in dl.cliques)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_moon_moser_plus_edge(k):
+    """Edge inside a part of the Moon-Moser graph: 3^(k-1) new, 2*3^(k-1) subsumed."""
+    n, pairs, parts = complete_multipartite([3] * k)
+    g = graph(n, pairs)
+    a, b = parts[0][0], parts[0][1]
+    hu, hv = O.canonical_batch(g, np.array([a], np.int32), np.array([b], np.int32))
+    nw, dl = O.imce_alg(g, hu, hv)
+    assert nw.count == 3 ** (k - 1) and dl.count == 2 * 3 ** (k - 1)
+    after = O.ttt_whole(g.plus(hu, hv))
+    assert after.count == 2 * 3 ** (k - 1)
+
+
+def test_batch_canonicalisation():
+    g = graph(5, [(0, 1), (1, 2)])
+    u = np.array([1, 3, 2, 4, 3, 2, 0], np.int32)
+    v = np.array([0, 3, 3, 0, 2, 0, 4], np.int32)
+    hu, hv = O.canonical_batch(g, u, v)
+    # (1,0) exists, (3,3) loop, (2,3) kept, (4,0)->(0,4) kept, (3,2) repeat, (2,0)->(0,2) kept, (0,4) repeat
+    assert list(zip(hu.tolist(), hv.tolist())) == [(2, 3), (0, 4), (0, 2)]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_incremental_invariant_random(seed):
+    """C(G) - Λdel + Λnew = C(G+H), and the paper's algorithms agree with the
+    set-difference definition, over several batches."""
+    rng = random.Random(300 + seed)
+    n = rng.randint(8, 40)
+    pairs = random_pairs(n, rng.choice([0.1, 0.2, 0.35]), rng)
+    g = graph(n, pairs)
+    state = O.Imce(g, seed=seed)
+    cur = set(O.ttt_whole(g, want_list=True, seed=seed).cliques)
+    for _ in range(4):
+        k = rng.randint(1, 12)
+        u = np.array([rng.randrange(n) for _ in range(k)], np.int32)
+        v = np.array([rng.randrange(n) for _ in range(k)], np.int32)
+        hu, hv = O.canonical_batch(g, u, v)
+        new_a, del_a = O.imce_diff(g, hu, hv, seed=seed)
+        new_b, del_b = O.imce_alg(g, hu, hv, seed=seed)
+        rho, new_s, del_s = state.add(u, v)
+        assert rho == len(hu)
+        assert new_a.cliques == new_b.cliques == new_s.cliques
+        assert del_a.cliques == del_b.cliques == del_s.cliques
+        g = g.plus(hu, hv)
+        after = set(O.ttt_whole(g, want_list=True, seed=seed).cliques)
+        assert (cur - set(del_a.cliques)) | set(new_a.cliques) == after
+        assert set(state.cliques().cliques) == after
+        cur = after
+
+
+def test_incremental_medium_graph():
+    """A few hundred vertices, batches of a few hundred edges: modes agree."""
+    u, v = graphgen.er(400, 0.03, 77)
+    g = O.Graph(400, u, v)
+    su, sv = graphgen.er(400, 0.004, 78)
+    hu, hv = O.canonical_batch(g, su, sv)
+    new_a, del_a = O.imce_diff(g, hu, hv)
+    new_b, del_b = O.imce_alg(g, hu, hv)
+    assert new_a.cliques == new_b.cliques and del_a.cliques == del_b.cliques
+    assert new_a.count > 0 and del_a.count > 0
