@@ -1,0 +1,252 @@
+/*
+ * libmce_gb300 — maximal clique enumeration on one GB300 (sm_103a).
+ *
+ * Implements the method of Das, Sanei-Mehri and Tirthapura, "Shared-Memory
+ * Parallel Maximal Clique Enumeration from Static and Dynamic Graphs":
+ *   - static MCE: TTT (Algorithm 1) decomposed into one subproblem per vertex
+ *     under a total vertex rank (ParMCE, Algorithm 5), heavy subtrees split
+ *     with the prefix rule of ParTTT (Algorithm 3);
+ *   - incremental MCE for edge additions: new cliques (Algorithm 6 with the
+ *     edge-excluding enumerator of Algorithms 7/9) and subsumed cliques
+ *     (Algorithm 8), with the maximal cliques kept in a device hash index.
+ *
+ * Conventions for every call:
+ *   - Vertex ids are int32 in [0, n).  Graphs are simple and undirected
+ *     (Section 3); inputs are normalised (self loops dropped, direction
+ *     ignored, parallel edges merged; Section 6.1).
+ *   - "device" pointers are CUDA device addresses on the current device;
+ *     "host" pointers are ordinary host memory (pinned memory is faster).
+ *   - The caller owns every buffer it passes; the library never keeps a
+ *     caller pointer after a call returns.  Objects created by the library
+ *     (mce_graph, mce_model, imce_state) are owned by the caller and freed
+ *     with the matching *_free / *_close call.
+ *   - Work is issued on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream).  Calls that return a summary synchronise that stream once to
+ *     read it back; results written to caller device buffers are complete
+ *     when the call returns.
+ *   - The library allocates its own device scratch with the stream-ordered
+ *     allocator and keeps a grow-only workspace per device between calls.
+ *   - Errors are returned as mce_status; on any status other than MCE_OK,
+ *     MCE_EOVERFLOW or MCE_EBUDGET the output structs are left unspecified.
+ *     A CUDA error is reported as MCE_ECUDA and the text is available from
+ *     mce_last_error().  No entry point aborts the process.
+ *
+ * Clique set summary (not part of the paper, which outputs the cliques):
+ *   h(v)     = splitmix64(v xor seed)   (splitmix64 as published by Vigna:
+ *              z = x + 0x9E3779B97F4A7C15, then the 30/27/31 xor-shift-multiply
+ *              finaliser with 0xBF58476D1CE4E5B9 and 0x94D049BB133111EB)
+ *   H(K)     = fmix(sum_{v in K} h(v) + |K| * 0x9E3779B97F4A7C15)  (mod 2^64)
+ *   Hash(C)  = sum_{K in C} H(K)  (mod 2^64)
+ * Both levels are order independent, so no sorting is needed on the device.
+ */
+#ifndef MCE_GB300_H
+#define MCE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mce_status;
+#define MCE_OK 0
+#define MCE_EINVAL (-1)     /* bad argument: null pointer, size, id outside [0, n) */
+#define MCE_ENOMEM (-2)     /* device allocation failed */
+#define MCE_EOVERFLOW (-3)  /* an optional output buffer was too small; summary still exact */
+#define MCE_EBUDGET (-4)    /* node budget exhausted; result marked incomplete */
+#define MCE_ETIMEOUT (-5)   /* a bounded device wait gave up; result incomplete */
+#define MCE_ECUDA (-6)      /* CUDA runtime error */
+#define MCE_ESTATE (-7)     /* object in an unusable state */
+
+/* Largest clique size + 1 that the histogram records. */
+#define MCE_HIST_CAP 1024
+
+/* Vertex rank keys (Section 4.2): rank(v) = position of (key(v), id(v)) in
+ * ascending lexicographic order; a higher key gives a higher rank. */
+enum {
+    MCE_RANK_DEGREE = 0,    /* key = degree */
+    MCE_RANK_DEGEN = 1,     /* key = core number (degeneracy of v) */
+    MCE_RANK_TRIANGLE = 2,  /* key = number of triangles containing v */
+    MCE_RANK_LEARNED = 3,   /* key = cost predicted by an mce_model */
+    MCE_RANK_USER = 4       /* rank given by the caller (a permutation) */
+};
+
+typedef struct mce_graph mce_graph;   /* device-resident CSR */
+typedef struct mce_model mce_model;   /* MLP cost model, weights on the device */
+typedef struct imce_state imce_state; /* graph + its maximal cliques */
+
+typedef struct {
+    int32_t rank_kind;            /* MCE_RANK_* */
+    const int32_t *user_rank;     /* device int32[n], a permutation of [0, n) (MCE_RANK_USER) */
+    const mce_model *model;       /* MCE_RANK_LEARNED */
+    uint64_t node_budget;         /* stop after this many search-tree nodes; 0 = unlimited */
+    uint64_t hash_seed;           /* seed of h(v) */
+    void *stream;                 /* cudaStream_t */
+    /* Optional clique list (device, caller-owned).  Clique i starts at
+     * list_vtx[list_off[i]] with its size, followed by its vertex ids in no
+     * particular order.  Cliques come in no particular order. */
+    int64_t *list_off;            /* int64[list_max_cliques] */
+    int32_t *list_vtx;            /* int32[list_max_words] */
+    int64_t list_max_cliques;
+    int64_t list_max_words;
+    /* Optional per-subproblem outputs (device uint64[n], caller-owned): the
+     * cliques, hash and tree nodes of the subproblem of each vertex v (the
+     * cliques whose lowest-ranked vertex is v). */
+    uint64_t *pv_count;
+    uint64_t *pv_hash;
+    uint64_t *pv_nodes;
+    int32_t split;                /* 1 = split heavy subtrees across warps (default) */
+    int32_t order_by_model;       /* 1 = schedule subproblems by the model's prediction */
+    int32_t warps_per_block;      /* 0 = automatic */
+    int32_t blocks_per_sm;        /* 0 = automatic */
+    uint32_t time_limit_ms;       /* stop the search after this long (MCE_ETIMEOUT); 0 = 600 s */
+} mce_opts;
+
+typedef struct {
+    uint64_t count;               /* maximal cliques */
+    uint64_t hash;                /* Hash(C) */
+    uint64_t tree_nodes;          /* search-tree nodes visited (Algorithm 1 calls) */
+    int32_t hist_len;             /* largest clique size + 1 */
+    int32_t complete;             /* 0 if stopped by the budget or a timeout */
+    uint64_t hist[MCE_HIST_CAP];  /* hist[s] = cliques of size s */
+    int64_t list_cliques;         /* cliques written to the list */
+    int64_t list_words;           /* words written to list_vtx */
+    uint64_t tasks_split;         /* subtrees handed to other warps */
+    int32_t subproblems;          /* vertices with a non-trivial subproblem */
+    float ms_rank;                /* ranking time (key + sort), device time */
+    float ms_enum;                /* enumeration time, device time */
+    float ms_search;              /* device time of the search kernel alone */
+    uint64_t word_ops;            /* 32-bit AND+POPC word operations of the search:
+                                     per node (|cand|+|fini|)*ceil(c/32) for the pivot,
+                                     per child 2*ceil(c/32) + |F| */
+} mce_result;
+
+/* ---------------------------------------------------------------- misc */
+
+const char *mce_strerror(mce_status s);
+/* Text of the last CUDA error seen by this thread, or "". */
+const char *mce_last_error(void);
+/* Fill *o with defaults: degeneracy rank, no budget, seed 0, split on. */
+void mce_opts_init(mce_opts *o);
+/* Number of kernels this library has launched in this process. */
+uint64_t mce_kernel_launches(void);
+
+/* ---------------------------------------------------------------- graphs */
+
+/* Build the CSR of the simple graph behind m raw pairs (u[i], v[i]).
+ * u, v: int32[m], device memory if on_device != 0, else host memory.
+ * Self loops are dropped, direction ignored, repeats merged (Section 3,
+ * Section 6.1).  Errors: MCE_EINVAL for m < 0, n < 0, n >= 2^30 or an id
+ * outside [0, n). */
+mce_status mce_graph_create(const int32_t *u, const int32_t *v, int64_t m, int32_t n,
+                            int32_t on_device, void *stream, mce_graph **g);
+
+/* Copy out the CSR: row_ptr int32[n+1] and col int32[nnz] (device
+ * pointers owned by the graph, valid until mce_graph_free). */
+mce_status mce_graph_csr(const mce_graph *g, int32_t *n, int64_t *nnz,
+                         const int32_t **row_ptr, const int32_t **col);
+
+/* Copy the CSR into caller buffers row_ptr int32[n+1] and col int32[nnz]:
+ * host memory if to_host != 0, else device memory. */
+mce_status mce_graph_copy_csr(const mce_graph *g, int32_t *row_ptr, int32_t *col, int32_t to_host, void *stream);
+
+void mce_graph_free(mce_graph *g);
+
+/* ---------------------------------------------------------------- ranking */
+
+/* Per-vertex key (Section 4.2) into device int64[n]: kind MCE_RANK_DEGREE
+ * (degree), MCE_RANK_DEGEN (core number: v is in the k-core but not the
+ * (k+1)-core) or MCE_RANK_TRIANGLE (triangles containing v). */
+mce_status mce_vertex_key(const mce_graph *g, int32_t kind, void *stream, int64_t *key);
+
+/* rank_out: device int32[n], rank(v) = position of (key(v), v) in ascending
+ * order, for opts->rank_kind. */
+mce_status mce_rank(const mce_graph *g, const mce_opts *opts, int32_t *rank_out);
+
+/* ---------------------------------------------------------------- static MCE */
+
+/* All maximal cliques of g (ParMCE, Algorithm 5, with TTT, Algorithm 1, on
+ * each subproblem): count, size histogram, set hash, tree nodes; optional
+ * clique list and per-subproblem outputs through opts. */
+mce_status mce_enumerate(const mce_graph *g, const mce_opts *opts, mce_result *res);
+
+/* ---------------------------------------------------------------- learned cost model */
+
+/* Per-vertex features, device float[n*8], row-major:
+ *   0 log1p(degree)              1 core number
+ *   2 log1p(triangles)           3 mean log1p(neighbour degree)
+ *   4 std log1p(neighbour degree) 5 max log1p(neighbour degree)
+ *   6 log1p(#higher-degree-rank neighbours)  7 local clustering 2t/(d(d-1)) */
+mce_status mce_features(const mce_graph *g, void *stream, float *feat);
+
+/* MLP 8 -> hidden -> hidden -> 1, ReLU, weights initialised from `seed`. */
+mce_status mce_model_create(int32_t hidden, uint64_t seed, mce_model **m);
+void mce_model_free(mce_model *m);
+/* Weights as host float arrays in the order W1[h*8], b1[h], W2[h*h], b2[h],
+ * w3[h], b3[1] (row-major, y = W x + b); n_params = 8h + h + h*h + h + h + 1. */
+int64_t mce_model_num_params(const mce_model *m);
+mce_status mce_model_get(const mce_model *m, float *host_params);
+mce_status mce_model_set(mce_model *m, const float *host_params);
+/* Mean-squared-error loss and its gradient over `rows` samples (device
+ * feat[rows*8], label[rows]) in FP32; grad: host float[n_params]. */
+mce_status mce_model_loss_grad(const mce_model *m, const float *feat, const float *label, int32_t rows,
+                               void *stream, float *loss, float *host_grad);
+/* `epochs` passes of minibatch Adam over device feat/label; *loss_out =
+ * last epoch's mean loss. */
+mce_status mce_model_train(mce_model *m, const float *feat, const float *label, int32_t rows,
+                           int32_t epochs, int32_t batch, float lr, uint64_t seed, void *stream,
+                           float *loss_out);
+/* Predictions (device float[rows]); bf16 = 1 uses BF16 weights and
+ * activations with FP32 accumulation, else FP32. */
+mce_status mce_model_predict(const mce_model *m, const float *feat, int32_t rows, int32_t bf16,
+                             void *stream, float *out);
+
+/* ---------------------------------------------------------------- batched MCE */
+
+/* Maximal cliques of k disjoint graphs in one persistent launch.  The
+ * graphs are the vertex ranges [graph_ptr[i], graph_ptr[i+1]) of the
+ * disjoint union described by (u, v, m, n); graph_ptr is host int32[k+1].
+ * Per graph (device buffers, caller-owned): counts uint64[k], hashes
+ * uint64[k], status int32[k] (MCE_OK, or MCE_EBUDGET when the graph used up
+ * opts->node_budget nodes).  The budget applies per graph.  *total receives
+ * the summary over all graphs. */
+mce_status mce_enumerate_batched(const mce_graph *g, const int32_t *graph_ptr, int32_t k,
+                                 const mce_opts *opts, uint64_t *counts, uint64_t *hashes,
+                                 int32_t *status, mce_result *total);
+
+/* ---------------------------------------------------------------- incremental MCE */
+
+typedef struct {
+    int64_t applied;              /* new edges of the batch (ρ) */
+    int64_t dropped;              /* self loops, existing edges, repeats */
+    uint64_t new_count, new_hash; /* Λnew = C(G+H) \ C(G) */
+    uint64_t sub_count, sub_hash; /* Λdel = C(G) \ C(G+H) */
+    int32_t new_hist_len, sub_hist_len;
+    uint64_t new_hist[MCE_HIST_CAP];
+    uint64_t sub_hist[MCE_HIST_CAP];
+    uint64_t alive;               /* |C(G+H)| after the batch */
+    float ms;                     /* device time of the batch */
+} imce_delta;
+
+/* Take a copy of g and compute C(g) into a device clique index. */
+mce_status imce_open(const mce_graph *g, const mce_opts *opts, imce_state **s);
+/* Add k raw pairs (device if on_device, else host): canonicalise
+ * (Algorithm 6 line 2 order = arrival order; self loops, existing edges and
+ * repeats dropped), then Λnew (Algorithms 6, 7), Λdel (Algorithm 8), and
+ * update the graph and the index.  All or nothing: on an error the state is
+ * unchanged.  Optional lists (device, caller-owned; same layout as the
+ * mce_opts list) receive Λnew and Λdel when not NULL. */
+mce_status imce_add_edges(imce_state *s, const int32_t *u, const int32_t *v, int64_t k,
+                          int32_t on_device, imce_delta *out);
+/* Current graph (owned by the state). */
+const mce_graph *imce_graph(const imce_state *s);
+/* Alive cliques of the index into a caller list (layout as mce_opts). */
+mce_status imce_cliques(const imce_state *s, int64_t *list_off, int32_t *list_vtx,
+                        int64_t max_cliques, int64_t max_words, int64_t *n_cliques, int64_t *n_words);
+void imce_close(imce_state *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCE_GB300_H */

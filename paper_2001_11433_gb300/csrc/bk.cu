@@ -1,0 +1,853 @@
+// Persistent warp-cooperative Bron-Kerbosch (TTT) engine.
+//
+// One warp runs one search at a time.  A search is either a whole
+// subproblem (ParMCE, Algorithm 5: K = {v}, cand = Γ+(v), fini = the
+// lower-ranked neighbours; or ParIMCENew, Algorithm 6: K = {u, v},
+// cand = Γ(u) ∩ Γ(v), fini = ∅) or a piece of one handed over by another
+// warp.  The search is Algorithm 1 (TTT) on an explicit stack:
+//
+//   node:   if cand = fini = ∅ emit K; else pivot p ∈ cand ∪ fini maximising
+//           |cand ∩ Γ(p)| (ties: smallest vertex id), ext = cand \ Γ(p);
+//   child:  for q ∈ ext in ascending id: (K+q, cand ∩ Γ(q), fini ∩ Γ(q)),
+//           then cand -= q, fini += q.
+//
+// Subproblem layout (per warp, shared memory when it fits, else a private
+// global workspace): local vertices [0, c) are the candidates (ascending id),
+// [c, W) the lower-ranked neighbours that touch a candidate.  Row A[x] is the
+// bitset of candidates adjacent to local x (⌈c/32⌉ words, odd stride so
+// that lanes reading different rows hit different banks).  cand and the
+// candidates moved to fini ("finic") are bitsets over candidate columns; the
+// lower-ranked part of fini is an index list F that each child partitions in
+// place (vertices adjacent to q first), so a frame only stores its length.
+// A fini vertex with no candidate neighbour can never block or pivot below
+// the current node, so the pivot step drops it from F.
+//
+// Splitting (ParTTT, Algorithm 3): the children of a node only depend on the
+// ext vertices before them, so a warp that sees idle warps hands the upper
+// half of the remaining ext of its shallowest open frame to a device queue as
+// (K, cand \ ext_lo, fini ∪ ext_lo, ext_hi).  Thieves rebuild the subproblem
+// (deterministic layout) and continue from that frame.
+//
+// Incremental mode (Algorithm 7): X[x] = local vertices joined to x by an
+// earlier new edge e_j, j < i.  conf = ∪_{w ∈ K} X[w] is kept per frame; at
+// node entry cand ∩ conf moves to fini.  Such a q can lie in no output clique
+// (K+q would contain an excluded edge) yet still blocks non-maximal ones, the
+// effect of Algorithm 9's "cand -= q; fini += q; continue".
+#include "bk.cuh"
+
+namespace mce {
+
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+
+struct Ws {
+    int32_t w, c, W, f, wc, S;   // local vertices, candidates, kept vertices, kept fini, words, stride
+    int32_t *gid;
+    uint32_t *A;
+    uint32_t *X;                  // IMCE exclusion rows
+    int32_t *F, *Fs;
+    uint32_t *fr;                 // frames
+    int32_t *kpath;               // K path of the current task (local ids)
+    int32_t frw;                  // words per frame
+};
+
+__device__ __forceinline__ uint32_t *fr_cand(const Ws &s, int d) { return s.fr + (int64_t)d * s.frw; }
+__device__ __forceinline__ uint32_t *fr_finic(const Ws &s, int d) { return s.fr + (int64_t)d * s.frw + s.wc; }
+__device__ __forceinline__ uint32_t *fr_ext(const Ws &s, int d) { return s.fr + (int64_t)d * s.frw + 2 * s.wc; }
+__device__ __forceinline__ uint32_t *fr_conf(const Ws &s, int d) { return s.fr + (int64_t)d * s.frw + 3 * s.wc; }
+__device__ __forceinline__ uint32_t *fr_meta(const Ws &s, int d) { return s.fr + (int64_t)d * s.frw + 4 * s.wc; }
+// meta: [0] F length, [1] q (local id added at this frame, -1 at the task root), [2..3] hash sum
+
+__device__ __forceinline__ uint64_t meta_hsum(const uint32_t *m) { return (uint64_t)m[2] | ((uint64_t)m[3] << 32); }
+__device__ __forceinline__ void meta_set_hsum(uint32_t *m, uint64_t h) {
+    m[2] = (uint32_t)h;
+    m[3] = (uint32_t)(h >> 32);
+}
+
+__device__ __forceinline__ void ws_layout(Ws &s, uint32_t *base, int32_t w, int32_t c, int32_t mode) {
+    s.w = w;
+    s.c = c;
+    s.wc = (c + 31) >> 5;
+    s.S = (s.wc & 1) ? s.wc : s.wc + 1;
+    s.frw = 4 * s.wc + 4;
+    uint32_t *p = base;
+    s.gid = reinterpret_cast<int32_t *>(p);
+    p += w;
+    s.A = p;
+    p += (int64_t)w * s.S;
+    s.F = reinterpret_cast<int32_t *>(p);
+    p += (w - c);
+    s.Fs = reinterpret_cast<int32_t *>(p);
+    p += (w - c);
+    s.fr = p;
+    p += (int64_t)(c + 2) * s.frw;
+    s.kpath = reinterpret_cast<int32_t *>(p);
+    p += (c + 2);
+    s.X = (mode == BK_IMCE) ? p : nullptr;
+}
+
+// warp: true if any of the n words is non-zero
+__device__ __forceinline__ bool warp_any(const uint32_t *a, int n, int lane) {
+    bool nz = false;
+    for (int k = lane; k < n; k += 32) nz |= a[k] != 0;
+    return __any_sync(FULL, nz);
+}
+
+// warp: position of the lowest set bit of a[0..n), or -1
+__device__ __forceinline__ int warp_first_bit(const uint32_t *a, int n, int lane) {
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + lane;
+        const uint32_t x = k < n ? a[k] : 0u;
+        const uint32_t b = __ballot_sync(FULL, x != 0);
+        if (b) {
+            const int src = __ffs(b) - 1;
+            const uint32_t xs = __shfl_sync(FULL, x, src);
+            return ((k0 + src) << 5) + (__ffs(xs) - 1);
+        }
+    }
+    return -1;
+}
+
+// warp: number of set bits of a[0..n)
+__device__ __forceinline__ int warp_popc(const uint32_t *a, int n, int lane) {
+    int c = 0;
+    for (int k = lane; k < n; k += 32) c += __popc(a[k]);
+    return __reduce_add_sync(FULL, c);
+}
+
+// binary search of y in sorted g[0..c); -1 if absent
+__device__ __forceinline__ int bsearch_i32(const int32_t *g, int c, int32_t y) {
+    int lo = 0, hi = c;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (g[mid] < y) lo = mid + 1; else hi = mid;
+    }
+    return (lo < c && g[lo] == y) ? lo : -1;
+}
+
+// Partition F[0..len) so that the entries with pred true come first; the
+// others follow (both kept).  Returns the number with pred true.  Each chunk
+// is read into registers before any lane writes, and writes to the front only
+// reach positions already read.
+template <class Pred>
+__device__ int partition_F(const Ws &s, int len, int lane, Pred pred) {
+    int wpos = 0, spos = 0;
+    for (int b0 = 0; b0 < len; b0 += 32) {
+        const int i = b0 + lane;
+        const bool valid = i < len;
+        const int32_t u = valid ? s.F[i] : 0;
+        const bool pr = valid && pred(u);
+        const uint32_t bp = __ballot_sync(FULL, pr);
+        const uint32_t bn = __ballot_sync(FULL, valid && !pr);
+        __syncwarp();
+        if (pr) s.F[wpos + __popc(bp & lanemask_lt())] = u;
+        if (valid && !pr) s.Fs[spos + __popc(bn & lanemask_lt())] = u;
+        wpos += __popc(bp);
+        spos += __popc(bn);
+        __syncwarp();
+    }
+    for (int i = lane; i < spos; i += 32) s.F[wpos + i] = s.Fs[i];
+    __syncwarp();
+    return wpos;
+}
+
+// ------------------------------------------------------------------ subproblem build
+
+// ParMCE subproblem of v (Algorithm 5).  Local order: Γ+(v) (the candidates,
+// ascending id), then the lower-ranked neighbours (ascending id).  Row A[x]
+// marks the candidates adjacent to x.  Every candidate y adjacent to x has
+// rank(y) > rank(v) > rank(x) when x is lower ranked, so y ∈ Γ+(x); for two
+// candidates the edge lies in Γ+ of the lower-ranked one.  Scanning Γ+(x) for
+// every local x therefore finds each needed adjacency exactly once.
+__device__ void build_mce(const BkParams &P, Ws &s, int32_t v, int lane) {
+    const int32_t r0 = P.row_ptr[v], w = P.row_ptr[v + 1] - r0;
+    const int32_t u0 = P.up_ptr[v], c = P.up_ptr[v + 1] - u0;
+    for (int i = lane; i < c; i += 32) s.gid[i] = P.up_col[u0 + i];
+    {
+        const int32_t rv = P.rank[v];
+        int out = c;
+        for (int e0 = 0; e0 < w; e0 += 32) {
+            const int e = e0 + lane;
+            int32_t x = 0;
+            bool low = false;
+            if (e < w) {
+                x = P.col[r0 + e];
+                low = P.rank[x] < rv;
+            }
+            const uint32_t b = __ballot_sync(FULL, low);
+            if (low) s.gid[out + __popc(b & lanemask_lt())] = x;
+            out += __popc(b);
+        }
+    }
+    const int64_t awords = (int64_t)w * s.S;
+    for (int64_t k = lane; k < awords; k += 32) s.A[k] = 0u;
+    __syncwarp();
+    for (int x = lane; x < w; x += 32) {
+        const int32_t gx = s.gid[x];
+        const int32_t e1 = P.up_ptr[gx + 1];
+        for (int32_t e = P.up_ptr[gx]; e < e1; ++e) {
+            const int j = bsearch_i32(s.gid, c, P.up_col[e]);
+            if (j >= 0) {
+                atomicOr(&s.A[(int64_t)x * s.S + (j >> 5)], 1u << (j & 31));
+                if (x < c) atomicOr(&s.A[(int64_t)j * s.S + (x >> 5)], 1u << (x & 31));
+            }
+        }
+    }
+    __syncwarp();
+    // keep the lower-ranked neighbours that touch a candidate; rows only move down
+    int f = 0;
+    for (int b0 = c; b0 < w; b0 += 32) {
+        const int x = b0 + lane;
+        bool nz = false;
+        if (x < w)
+            for (int k = 0; k < s.wc; ++k) nz |= s.A[(int64_t)x * s.S + k] != 0u;
+        uint32_t keep = __ballot_sync(FULL, nz);
+        while (keep) {
+            const int l = __ffs(keep) - 1;
+            keep &= keep - 1;
+            const int src = b0 + l, dst = c + f;
+            if (src != dst) {
+                for (int k = lane; k < s.S; k += 32) s.A[(int64_t)dst * s.S + k] = s.A[(int64_t)src * s.S + k];
+                if (lane == 0) s.gid[dst] = s.gid[src];
+            }
+            ++f;
+            __syncwarp();
+        }
+    }
+    s.f = f;
+    s.W = c + f;
+    for (int i = lane; i < f; i += 32) s.F[i] = c + i;
+    __syncwarp();
+}
+
+// ParIMCENew subproblem of new edge i = (u, v) (Algorithm 6): local vertices
+// are V_e \ {u, v} = Γ'(u) ∩ Γ'(v), all candidates; fini is empty.
+// Adjacency within V_e comes from the degree-oriented Γ'+ lists; X rows and
+// the root conflict set from the batch adjacency restricted to indices < i.
+__device__ void build_imce(const BkParams &P, Ws &s, int32_t i, int lane) {
+    const int32_t u = P.eu[i], v = P.ev[i];
+    int32_t a = u, b = v;
+    if (P.row_ptr[a + 1] - P.row_ptr[a] > P.row_ptr[b + 1] - P.row_ptr[b]) {
+        a = v;
+        b = u;
+    }
+    const int32_t a0 = P.row_ptr[a], la = P.row_ptr[a + 1] - a0;
+    const int32_t b0 = P.row_ptr[b], lb = P.row_ptr[b + 1] - b0;
+    int c = 0;
+    for (int e0 = 0; e0 < la; e0 += 32) {
+        const int e = e0 + lane;
+        int32_t x = 0;
+        bool hit = false;
+        if (e < la) {
+            x = P.col[a0 + e];
+            hit = bsearch_i32(P.col + b0, lb, x) >= 0;
+        }
+        const uint32_t bl = __ballot_sync(FULL, hit);
+        if (hit) s.gid[c + __popc(bl & lanemask_lt())] = x;
+        c += __popc(bl);
+    }
+    __syncwarp();
+    // the layout was sized for the bound min(deg); re-derive it for the actual c
+    s.c = c;
+    s.wc = (c + 31) >> 5;
+    s.S = (s.wc & 1) ? s.wc : s.wc + 1;
+    s.frw = 4 * s.wc + 4;
+    s.w = c;
+    s.W = c;
+    s.f = 0;
+    {
+        uint32_t *p = reinterpret_cast<uint32_t *>(s.gid) + c;
+        s.A = p;
+        p += (int64_t)c * s.S;
+        s.F = reinterpret_cast<int32_t *>(p);
+        s.Fs = s.F;
+        s.fr = p;
+        p += (int64_t)(c + 2) * s.frw;
+        s.kpath = reinterpret_cast<int32_t *>(p);
+        p += (c + 2);
+        s.X = p;
+    }
+    uint32_t *root_conf = fr_conf(s, 0);
+    const int64_t rows = (int64_t)c * s.S;
+    for (int64_t k = lane; k < rows; k += 32) {
+        s.A[k] = 0u;
+        s.X[k] = 0u;
+    }
+    for (int k = lane; k < s.wc; k += 32) root_conf[k] = 0u;
+    __syncwarp();
+    for (int x = lane; x < c; x += 32) {
+        const int32_t gx = s.gid[x];
+        for (int32_t e = P.up_ptr[gx]; e < P.up_ptr[gx + 1]; ++e) {
+            const int j = bsearch_i32(s.gid, c, P.up_col[e]);
+            if (j >= 0) {
+                atomicOr(&s.A[(int64_t)x * s.S + (j >> 5)], 1u << (j & 31));
+                atomicOr(&s.A[(int64_t)j * s.S + (x >> 5)], 1u << (x & 31));
+            }
+        }
+        for (int32_t e = P.h_ptr[gx]; e < P.h_ptr[gx + 1]; ++e) {
+            if (P.h_idx[e] >= i) continue;
+            const int j = bsearch_i32(s.gid, c, P.h_adj[e]);
+            if (j >= 0) atomicOr(&s.X[(int64_t)x * s.S + (j >> 5)], 1u << (j & 31));
+        }
+    }
+    for (int t = 0; t < 2; ++t) {
+        const int32_t z = t == 0 ? u : v;
+        for (int32_t e = P.h_ptr[z] + lane; e < P.h_ptr[z + 1]; e += 32) {
+            if (P.h_idx[e] >= i) continue;
+            const int j = bsearch_i32(s.gid, c, P.h_adj[e]);
+            if (j >= 0) atomicOr(&root_conf[j >> 5], 1u << (j & 31));
+        }
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ output
+
+struct Acc {
+    unsigned long long wops;                 // per lane: algorithmic word operations
+    unsigned long long count, hash, nodes;   // per warp, whole launch
+    unsigned long long t_count, t_hash, t_nodes;   // per task
+};
+
+__device__ void emit(const BkParams &P, const Ws &s, int32_t root, int32_t k0, int d, uint64_t hsum, Acc &acc,
+                     unsigned long long *shist, int lane) {
+    const uint32_t size = (uint32_t)(k0 + d);
+    const uint64_t h = clique_hash_from_sum(hsum, size);
+    acc.count++;
+    acc.hash += h;
+    acc.t_count++;
+    acc.t_hash += h;
+    if (lane == 0) {
+        if (size < 256) atomicAdd(&shist[size], 1ULL);
+        else if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
+        else atomicOr(&P.out[OUT_FLAGS], 2ULL);
+        atomicMax(&P.out[OUT_MAXSIZE], (unsigned long long)size);
+    }
+    if (P.list_off) {
+        unsigned long long pos = 0, idx = 0;
+        if (lane == 0) {
+            pos = atomicAdd(&P.out[OUT_LIST_WORDS], (unsigned long long)(size + 1));
+            idx = atomicAdd(&P.out[OUT_LIST_CLIQUES], 1ULL);
+        }
+        pos = __shfl_sync(FULL, pos, 0);
+        idx = __shfl_sync(FULL, idx, 0);
+        if (idx >= (unsigned long long)P.list_max_cliques || pos + size + 1 > (unsigned long long)P.list_max_words) {
+            if (lane == 0) atomicOr(&P.out[OUT_FLAGS], 1ULL);
+            return;
+        }
+        // K = seed vertices, the task's path, then the q of frames 1..d
+        int32_t *dst = P.list_vtx + pos;
+        if (lane == 0) {
+            dst[0] = (int32_t)size;
+            P.list_off[idx] = (int64_t)pos;
+        }
+        int nseed;
+        if (P.mode == BK_MCE) {
+            nseed = 1;
+            if (lane == 0) dst[1] = root;
+        } else {
+            nseed = 2;
+            if (lane == 0) {
+                dst[1] = P.eu[root];
+                dst[2] = P.ev[root];
+            }
+        }
+        const int npath = k0 - nseed;
+        for (int j = lane; j < npath + d; j += 32) {
+            const int32_t loc = j < npath ? s.kpath[j] : (int32_t)fr_meta(s, j - npath + 1)[1];
+            dst[1 + nseed + j] = s.gid[loc];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ task queue
+
+// Reserve arena space and a queue slot; returns arena offset or -1.
+__device__ int64_t queue_reserve(const BkParams &P, int64_t words, int64_t *slot) {
+    const unsigned long long off = atomicAdd(&P.ctl[CTL_ARENA], (unsigned long long)words);
+    if ((int64_t)(off + words) > P.arena_words) return -1;
+    const unsigned long long t = atomicAdd(&P.ctl[CTL_QTAIL], 1ULL);
+    if ((int64_t)t >= P.qcap) return -1;
+    *slot = (int64_t)t;
+    return (int64_t)off;
+}
+
+__device__ void queue_publish(const BkParams &P, int64_t slot, int64_t off) {
+    atomicAdd(&P.ctl[CTL_PENDING], 1ULL);
+    __threadfence();
+    atomicExch(&P.qslot[slot], (uint32_t)(off + 1));
+}
+
+// Pop one task; returns its arena offset or -1.  Waits (bounded) for a
+// claimed slot whose pusher has not published yet.
+__device__ int64_t queue_pop(const BkParams &P) {
+    for (int tries = 0; tries < 64; ++tries) {
+        const unsigned long long h = *(volatile unsigned long long *)&P.ctl[CTL_QHEAD];
+        unsigned long long t = *(volatile unsigned long long *)&P.ctl[CTL_QTAIL];
+        if (t > (unsigned long long)P.qcap) t = (unsigned long long)P.qcap;
+        if (h >= t) return -1;
+        if (atomicCAS(&P.ctl[CTL_QHEAD], h, h + 1) == h) {
+            const uint64_t t0 = globaltimer_ns();
+            uint32_t v;
+            while ((v = *(volatile uint32_t *)&P.qslot[h]) == 0u) {
+                if (globaltimer_ns() - t0 > P.timeout_ns) {
+                    atomicOr(&P.ctl[CTL_ABORT], 2ULL);
+                    return -1;
+                }
+                __nanosleep(100);
+            }
+            __threadfence();
+            return (int64_t)v - 1;
+        }
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------------ the search
+
+struct Task {
+    int32_t root;        // vertex (MCE) or edge index (IMCE)
+    int32_t kdepth;      // vertices of K beyond the seeds
+    int64_t rec;         // arena offset of a handed-over frame, -1 for a whole subproblem
+};
+
+// Run one task to completion.  Returns false when the launch must stop.
+__device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigned long long *shist,
+                         uint32_t *ws_smem, uint32_t *ws_glob, int lane, int32_t &built, int &node_tick,
+                         uint64_t t_start) {
+    const int32_t root = T.root;
+    // ---- build (or reuse) the subproblem
+    int32_t w, c;
+    if (P.mode == BK_MCE) {
+        w = P.row_ptr[root + 1] - P.row_ptr[root];
+        c = P.up_ptr[root + 1] - P.up_ptr[root];
+    } else {
+        const int32_t du = P.row_ptr[P.eu[root] + 1] - P.row_ptr[P.eu[root]];
+        const int32_t dv = P.row_ptr[P.ev[root] + 1] - P.row_ptr[P.ev[root]];
+        c = du < dv ? du : dv;
+        w = c;
+    }
+    const int64_t need = bk_ws_words(w, c, P.mode);
+    uint32_t *base = (need <= P.smem_words) ? ws_smem : ws_glob;
+    if (need > P.gws_words && base == ws_glob) {
+        if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 4ULL);
+        return false;
+    }
+    ws_layout(s, base, w, c, P.mode);
+    const int k0 = (P.mode == BK_MCE ? 1 : 2) + T.kdepth;
+    if (built != root) {
+        if (P.mode == BK_MCE) {
+            build_mce(P, s, root, lane);
+        } else {
+            build_imce(P, s, root, lane);
+        }
+        built = root;
+    } else if (P.mode == BK_MCE) {
+        // same layout as the previous build; recover W and f from the kept rows
+        // (F[0..f) is rewritten below)
+        int f = 0;
+        for (int b0 = c; b0 < w; b0 += 32) {
+            const int x = b0 + lane;
+            bool nz = false;
+            if (x < w)
+                for (int k = 0; k < s.wc; ++k) nz |= s.A[(int64_t)x * s.S + k] != 0u;
+            f += __popc(__ballot_sync(FULL, nz));
+        }
+        s.f = f;
+        s.W = c + f;
+    } else {
+        build_imce(P, s, root, lane);
+    }
+    // ---- frame 0
+    uint64_t hs0 = P.mode == BK_MCE ? vertex_hash(root, P.seed)
+                                    : vertex_hash(P.eu[root], P.seed) + vertex_hash(P.ev[root], P.seed);
+    bool enter;
+    uint32_t *m0 = fr_meta(s, 0);
+    if (T.rec < 0) {
+        uint32_t *cand = fr_cand(s, 0), *finic = fr_finic(s, 0);
+        for (int k = lane; k < s.wc; k += 32) {
+            const int lo = k << 5;
+            const int nb = s.c - lo;
+            cand[k] = nb >= 32 ? FULL : ((1u << nb) - 1u);
+            finic[k] = 0u;
+            if (P.mode == BK_MCE) fr_conf(s, 0)[k] = 0u;
+        }
+        if (P.mode == BK_MCE) {
+            for (int i = lane; i < s.f; i += 32) s.F[i] = s.c + i;
+        }
+        if (lane == 0) {
+            m0[0] = (uint32_t)s.f;
+            m0[1] = 0xffffffffu;
+        }
+        enter = true;
+    } else {
+        // handed-over frame: path, cand, finic, ext, conf
+        const uint32_t *r = P.arena + T.rec;
+        const int kd = T.kdepth;
+        for (int j = lane; j < kd; j += 32) s.kpath[j] = (int32_t)__ldcg(r + 2 + j);
+        const uint32_t *rb = r + 2 + kd;
+        for (int k = lane; k < s.wc; k += 32) {
+            fr_cand(s, 0)[k] = __ldcg(rb + k);
+            fr_finic(s, 0)[k] = __ldcg(rb + s.wc + k);
+            fr_ext(s, 0)[k] = __ldcg(rb + 2 * s.wc + k);
+            fr_conf(s, 0)[k] = __ldcg(rb + 3 * s.wc + k);
+        }
+        __syncwarp();
+        for (int j = 0; j < kd; ++j) hs0 += vertex_hash(s.gid[s.kpath[j]], P.seed);
+        int flen = 0;
+        if (P.mode == BK_MCE) {
+            // F at this frame: the kept lower-ranked vertices adjacent to the whole path
+            for (int i = lane; i < s.f; i += 32) s.F[i] = s.c + i;
+            __syncwarp();
+            flen = s.f;
+            for (int j = 0; j < kd; ++j) {
+                const int q = s.kpath[j];
+                flen = partition_F(s, flen, lane, [&](int32_t x) {
+                    return (s.A[(int64_t)x * s.S + (q >> 5)] >> (q & 31)) & 1u;
+                });
+            }
+        }
+        if (lane == 0) {
+            m0[0] = (uint32_t)flen;
+            m0[1] = 0xffffffffu;
+        }
+        enter = false;
+    }
+    meta_set_hsum(m0, hs0);
+    __syncwarp();
+
+    int d = 0;
+    for (;;) {
+        if (enter) {
+            acc.nodes++;
+            acc.t_nodes++;
+            uint32_t *cand = fr_cand(s, d), *finic = fr_finic(s, d);
+            uint32_t *meta = fr_meta(s, d);
+            if (P.mode == BK_IMCE) {
+                // Algorithm 7: a candidate joined to K by an earlier new edge cannot extend K
+                const uint32_t *conf = fr_conf(s, d);
+                for (int k = lane; k < s.wc; k += 32) {
+                    const uint32_t x = cand[k] & conf[k];
+                    finic[k] |= x;
+                    cand[k] &= ~x;
+                }
+                __syncwarp();
+            }
+            if (!warp_any(cand, s.wc, lane)) {
+                const bool fin = warp_any(finic, s.wc, lane) || meta[0] != 0u;
+                if (!fin) emit(P, s, root, k0, d, meta_hsum(meta), acc, shist, lane);
+                goto pop;
+            }
+            // ---- pivot: argmax over cand ∪ finic ∪ F of |cand ∩ A[u]|, ties to the smallest id
+            {
+                uint32_t best_cnt = 0;
+                int32_t best_gid = 0x7fffffff, best_loc = -1;
+                for (int k = 0; k < s.wc; ++k) {
+                    const uint32_t mword = cand[k] | finic[k];
+                    if ((mword >> lane) & 1u) {
+                        acc.wops += (unsigned long long)s.wc;
+                        const int u = (k << 5) + lane;
+                        const uint32_t *row = s.A + (int64_t)u * s.S;
+                        uint32_t cnt = 0;
+                        for (int t = 0; t < s.wc; ++t) cnt += __popc(cand[t] & row[t]);
+                        const int32_t g = s.gid[u];
+                        if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
+                            best_cnt = cnt;
+                            best_gid = g;
+                            best_loc = u;
+                        }
+                    }
+                }
+                const int flen = (int)meta[0];
+                if (flen) {
+                    // counts for F, dropping members with no candidate neighbour
+                    const int nf = partition_F(s, flen, lane, [&](int32_t u) {
+                        const uint32_t *row = s.A + (int64_t)u * s.S;
+                        uint32_t cnt = 0;
+                        for (int t = 0; t < s.wc; ++t) cnt += __popc(cand[t] & row[t]);
+                        return cnt != 0u;
+                    });
+                    acc.wops += (unsigned long long)s.wc * (unsigned long long)((flen - lane + 31) / 32);
+                    for (int i = lane; i < nf; i += 32) {
+                        const int u = s.F[i];
+                        const uint32_t *row = s.A + (int64_t)u * s.S;
+                        uint32_t cnt = 0;
+                        for (int t = 0; t < s.wc; ++t) cnt += __popc(cand[t] & row[t]);
+                        const int32_t g = s.gid[u];
+                        if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
+                            best_cnt = cnt;
+                            best_gid = g;
+                            best_loc = u;
+                        }
+                    }
+                    if (lane == 0) meta[0] = (uint32_t)nf;
+                }
+                // warp argmax (lanes without a candidate hold best_loc = -1)
+                const uint32_t key_cnt = best_loc >= 0 ? best_cnt + 1u : 0u;
+                const uint32_t mx = __reduce_max_sync(FULL, key_cnt);
+                const uint32_t gkey = (key_cnt == mx) ? (uint32_t)best_gid : 0xffffffffu;
+                const uint32_t mg = __reduce_min_sync(FULL, gkey);
+                const uint32_t who = __ballot_sync(FULL, key_cnt == mx && (uint32_t)best_gid == mg);
+                const int p = __shfl_sync(FULL, best_loc, __ffs(who) - 1);
+                const uint32_t *prow = s.A + (int64_t)p * s.S;
+                uint32_t *ext = fr_ext(s, d);
+                for (int k = lane; k < s.wc; k += 32) ext[k] = cand[k] & ~prow[k];
+                __syncwarp();
+            }
+            enter = false;
+            // ---- periodic checks: budget, abort, splitting
+            if (++node_tick >= 64) {
+                node_tick = 0;
+                unsigned long long ab = 0, hungry = 0;
+                if (lane == 0) {
+                    if (globaltimer_ns() - t_start > P.max_run_ns) atomicOr(&P.ctl[CTL_ABORT], 2ULL);
+                    ab = *(volatile unsigned long long *)&P.ctl[CTL_ABORT];
+                    if (P.node_budget) {
+                        const unsigned long long tot = atomicAdd(&P.ctl[CTL_NODES], 64ULL) + 64ULL;
+                        if (tot > P.node_budget) {
+                            atomicOr(&P.ctl[CTL_ABORT], 1ULL);
+                            ab |= 1ULL;
+                        }
+                    }
+                    if (P.graph_nodes) {
+                        const int32_t gg = P.graph_of[P.mode == BK_MCE ? root : P.eu[root]];
+                        const unsigned long long tot = atomicAdd(&P.graph_nodes[gg], 64ULL) + 64ULL;
+                        if (P.graph_budget && tot > P.graph_budget) ab |= 16ULL;
+                    }
+                    if (P.split) {
+                        hungry = *(volatile unsigned long long *)&P.ctl[CTL_HUNGRY];
+                        const unsigned long long qh = *(volatile unsigned long long *)&P.ctl[CTL_QHEAD];
+                        const unsigned long long qt = *(volatile unsigned long long *)&P.ctl[CTL_QTAIL];
+                        if (qt > qh && qt - qh >= hungry) hungry = 0;
+                    }
+                }
+                ab = __shfl_sync(FULL, ab, 0);
+                hungry = __shfl_sync(FULL, hungry, 0);
+                if (ab & 1ULL) return false;
+                if (ab & 2ULL) return false;
+                if (ab & 16ULL) return true;   // this graph is over its budget: drop the task
+                if (hungry) {
+                    // shallowest frame with at least two unexplored children
+                    for (int dd = 0; dd <= d; ++dd) {
+                        const uint32_t *ext = fr_ext(s, dd);
+                        const int rem = warp_popc(ext, s.wc, lane);
+                        if (rem < 2) continue;
+                        const int kd = T.kdepth + dd;
+                        const int64_t words = 2 + kd + 4 * (int64_t)s.wc;
+                        int64_t off = -1, slot = -1;
+                        if (lane == 0) off = queue_reserve(P, words, &slot);
+                        off = __shfl_sync(FULL, off, 0);
+                        slot = __shfl_sync(FULL, slot, 0);
+                        if (off < 0) break;
+                        // lower half stays here, upper half goes
+                        const int keep = rem / 2;
+                        uint32_t *rec = P.arena + off;
+                        if (lane == 0) {
+                            rec[0] = (uint32_t)root;
+                            rec[1] = (uint32_t)kd;
+                        }
+                        for (int j = lane; j < kd; j += 32)
+                            rec[2 + j] = (uint32_t)(j < T.kdepth ? s.kpath[j] : (int32_t)fr_meta(s, j - T.kdepth + 1)[1]);
+                        uint32_t *rb = rec + 2 + kd;
+                        uint32_t *cand = fr_cand(s, dd), *finic = fr_finic(s, dd), *ext2 = fr_ext(s, dd);
+                        const uint32_t *conf = fr_conf(s, dd);
+                        // ext_lo = the `keep` lowest bits of ext
+                        int seen = 0;
+                        for (int k0w = 0; k0w < s.wc; k0w += 32) {
+                            const int k = k0w + lane;
+                            const uint32_t e = k < s.wc ? ext2[k] : 0u;
+                            const int pc = __popc(e);
+                            int incl = pc;
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const int y = __shfl_up_sync(FULL, incl, o);
+                                if (lane >= o) incl += y;
+                            }
+                            const int before = seen + incl - pc;
+                            uint32_t lo = 0u;
+                            if (k < s.wc) {
+                                if (before + pc <= keep) lo = e;
+                                else if (before < keep) {
+                                    uint32_t x = e;
+                                    for (int t = 0; t < keep - before; ++t) {
+                                        const uint32_t bit = x & (0u - x);
+                                        lo |= bit;
+                                        x ^= bit;
+                                    }
+                                }
+                                rb[k] = cand[k] & ~lo;               // cand \ ext_lo
+                                rb[s.wc + k] = finic[k] | lo;        // fini ∪ ext_lo
+                                rb[2 * s.wc + k] = e & ~lo;          // ext_hi
+                                rb[3 * s.wc + k] = conf[k];
+                                ext2[k] = lo;
+                            }
+                            seen += __shfl_sync(FULL, incl, 31);
+                        }
+                        __threadfence();
+                        __syncwarp();
+                        if (lane == 0) {
+                            queue_publish(P, slot, off);
+                            atomicAdd(&P.out[OUT_SPLITS], 1ULL);
+                        }
+                        break;
+                    }
+                }
+            }
+        }
+        // ---- next child of frame d
+        {
+            uint32_t *ext = fr_ext(s, d);
+            const int q = warp_first_bit(ext, s.wc, lane);
+            if (q < 0) goto pop;
+            const int qw = q >> 5;
+            const uint32_t qb = 1u << (q & 31);
+            uint32_t *cand = fr_cand(s, d), *finic = fr_finic(s, d);
+            uint32_t *ncand = fr_cand(s, d + 1), *nfinic = fr_finic(s, d + 1);
+            const uint32_t *qrow = s.A + (int64_t)q * s.S;
+            for (int k = lane; k < s.wc; k += 32) {
+                ncand[k] = cand[k] & qrow[k];
+                nfinic[k] = finic[k] & qrow[k];
+                fr_ext(s, d + 1)[k] = 0u;
+                if (P.mode == BK_IMCE) fr_conf(s, d + 1)[k] = fr_conf(s, d)[k] | s.X[(int64_t)q * s.S + k];
+            }
+            const uint32_t *meta = fr_meta(s, d);
+            int nfl = 0;
+            if (meta[0]) {
+                nfl = partition_F(s, (int)meta[0], lane, [&](int32_t x) {
+                    return (s.A[(int64_t)x * s.S + qw] & qb) != 0u;
+                });
+            }
+            __syncwarp();
+            if (lane == 0) {
+                acc.wops += 2ull * (unsigned long long)s.wc + (unsigned long long)meta[0];
+                ext[qw] &= ~qb;
+                cand[qw] &= ~qb;
+                finic[qw] |= qb;
+                uint32_t *nm = fr_meta(s, d + 1);
+                nm[0] = (uint32_t)nfl;
+                nm[1] = (uint32_t)q;
+                meta_set_hsum(nm, meta_hsum(meta) + vertex_hash(s.gid[q], P.seed));
+            }
+            __syncwarp();
+            ++d;
+            enter = true;
+            continue;
+        }
+    pop:
+        if (d == 0) break;
+        --d;
+        enter = false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_bk(BkParams P) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);   // 256 bins
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nw_block = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) shist[i] = 0ULL;
+    __syncthreads();
+    uint32_t *ws_smem = smem + 512 + (int64_t)wib * P.smem_words;
+    const int64_t gwarp = (int64_t)blockIdx.x * nw_block + wib;
+    uint32_t *ws_glob = P.gws + gwarp * P.gws_words;
+    Acc acc = {0, 0, 0, 0, 0, 0, 0};
+    Ws s;
+    int32_t built = -1;
+    int node_tick = 0;
+    bool hungry = false;
+    uint64_t idle_since = 0;
+    const uint64_t t_start = globaltimer_ns();
+    for (;;) {
+        // ---- acquire work: queued pieces first, then the next subproblem
+        Task T;
+        T.root = -1;
+        T.kdepth = 0;
+        T.rec = -1;
+        int kind = 0;   // 0 none, 1 subproblem, 2 piece, 3 stop
+        if (lane == 0) {
+            if (*(volatile unsigned long long *)&P.ctl[CTL_ABORT] & 3ULL) {
+                kind = 3;
+            } else {
+                const int64_t off = queue_pop(P);
+                if (off >= 0) {
+                    kind = 2;
+                    T.rec = off;
+                    T.root = (int32_t)__ldcg(P.arena + off);
+                    T.kdepth = (int32_t)__ldcg(P.arena + off + 1);
+                } else if (*(volatile unsigned long long *)&P.ctl[CTL_NEXT] < (unsigned long long)P.n_sub) {
+                    const unsigned long long i = atomicAdd(&P.ctl[CTL_NEXT], 1ULL);
+                    if (i < (unsigned long long)P.n_sub) {
+                        kind = 1;
+                        T.root = P.order[i];
+                    }
+                }
+                if (kind == 0 && *(volatile unsigned long long *)&P.ctl[CTL_PENDING] == 0ULL) kind = 3;
+            }
+        }
+        kind = __shfl_sync(FULL, kind, 0);
+        if (kind == 3) break;
+        if (kind == 0) {
+            if (!hungry) {
+                hungry = true;
+                idle_since = globaltimer_ns();
+                if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], 1ULL);
+            } else if (globaltimer_ns() - idle_since > P.timeout_ns) {
+                if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 2ULL);
+                break;
+            }
+            __nanosleep(2000);
+            continue;
+        }
+        if (hungry) {
+            hungry = false;
+            if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
+        }
+        T.root = __shfl_sync(FULL, T.root, 0);
+        T.kdepth = __shfl_sync(FULL, T.kdepth, 0);
+        T.rec = __shfl_sync(FULL, T.rec, 0);
+        acc.t_count = acc.t_hash = acc.t_nodes = 0;
+        const bool go_on = run_task(P, s, T, acc, shist, ws_smem, ws_glob, lane, built, node_tick, t_start);
+        if (lane == 0) {
+            if (P.pv_count && P.mode == BK_MCE) {
+                atomicAdd(&P.pv_count[T.root], acc.t_count);
+                atomicAdd(&P.pv_hash[T.root], acc.t_hash);
+                atomicAdd(&P.pv_nodes[T.root], acc.t_nodes);
+            }
+            if (P.g_count) {
+                const int32_t gg = P.graph_of[P.mode == BK_MCE ? T.root : P.eu[T.root]];
+                atomicAdd(&P.g_count[gg], acc.t_count);
+                atomicAdd(&P.g_hash[gg], acc.t_hash);
+            }
+            __threadfence();
+            atomicAdd(&P.ctl[CTL_PENDING], ~0ULL);
+        }
+        if (!go_on) break;
+    }
+    if (hungry && lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
+    {
+        unsigned long long w = acc.wops;
+        for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(FULL, w, o);
+        if (lane == 0) atomicAdd(&P.out[OUT_WORDOPS], w);
+    }
+    if (lane == 0) {
+        atomicAdd(&P.out[OUT_COUNT], acc.count);
+        atomicAdd(&P.out[OUT_HASH], acc.hash);
+        atomicAdd(&P.out[OUT_NODES], acc.nodes);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (shist[i]) atomicAdd(&P.out[OUT_HIST + i], shist[i]);
+}
+
+}  // namespace
+
+mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s) {
+    const size_t smem = (size_t)512 * 4 + (size_t)warps_per_block * p.smem_words * 4;
+    MCE_CUDA(cudaFuncSetAttribute(k_bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned blocks = (unsigned)(num_sms() * blocks_per_sm);
+    MCE_LAUNCH(k_bk, blocks, warps_per_block * 32, smem, s, p);
+    return MCE_OK;
+}
+
+}  // namespace mce

@@ -1,0 +1,100 @@
+// Persistent warp-cooperative Bron-Kerbosch engine (shared by static and
+// incremental enumeration).
+#pragma once
+
+#include "internal.cuh"
+
+namespace mce {
+
+// Control block of one persistent launch (uint64 words).
+enum CtlWord {
+    CTL_NEXT = 0,      // next unclaimed subproblem index
+    CTL_QTAIL = 1,     // queue slots reserved by pushers
+    CTL_QHEAD = 2,     // queue slots claimed by poppers
+    CTL_PENDING = 3,   // subproblems + queued tasks not finished
+    CTL_HUNGRY = 4,    // warps waiting for work
+    CTL_ARENA = 5,     // words of the task arena in use
+    CTL_NODES = 6,     // tree nodes, for the budget
+    CTL_ABORT = 7,     // 1 = budget, 2 = timeout, 4 = workspace too small, 8 = bad task
+    CTL_WORDS = 8
+};
+
+// Output block (uint64 words); the size histogram follows at OUT_HIST.
+enum OutWord {
+    OUT_COUNT = 0,
+    OUT_HASH = 1,
+    OUT_NODES = 2,
+    OUT_MAXSIZE = 3,
+    OUT_LIST_CLIQUES = 4,
+    OUT_LIST_WORDS = 5,
+    OUT_FLAGS = 6,     // 1 = list overflow, 2 = histogram overflow
+    OUT_SPLITS = 7,
+    OUT_WORDOPS = 8,
+    OUT_HIST = 16,
+    OUT_WORDS = 16 + MCE_HIST_CAP
+};
+
+// Mode of a subproblem.
+enum BkMode {
+    BK_MCE = 0,    // ParMCE subproblem of vertex v (Algorithm 5)
+    BK_IMCE = 1    // new cliques of edge e_i (Algorithm 6 with the exclusion of Algorithm 7)
+};
+
+struct BkParams {
+    int32_t mode;
+    // graph
+    const int32_t *row_ptr, *col;
+    const int32_t *up_ptr, *up_col;   // Γ+ lists (by rank for MCE, by degree rank of G+H for IMCE)
+    const int32_t *rank;              // MCE only
+    // subproblems
+    const int32_t *order;             // MCE: vertices; IMCE: edge indices, in processing order
+    int32_t n_sub;
+    // IMCE: batch edges e_1..e_rho (arrival order) and the new-edge adjacency
+    const int32_t *eu, *ev;
+    const int32_t *h_ptr, *h_adj, *h_idx;   // per vertex: new neighbours and edge indices
+    const int32_t *graph_of;          // batched MCE: graph id of each vertex (or null)
+    unsigned long long *graph_nodes;  // batched MCE: tree nodes per graph
+    uint64_t graph_budget;
+    uint64_t seed;
+    // per-warp workspace
+    uint32_t *gws;
+    int64_t gws_words;
+    int32_t smem_words;
+    // task queue
+    uint32_t *arena;
+    int64_t arena_words;
+    uint32_t *qslot;
+    int64_t qcap;
+    unsigned long long *ctl;
+    // outputs
+    unsigned long long *out;
+    int64_t *list_off;
+    int32_t *list_vtx;
+    int64_t list_max_cliques, list_max_words;
+    unsigned long long *pv_count, *pv_hash, *pv_nodes;   // per subproblem id
+    unsigned long long *g_count, *g_hash;                // batched: per graph
+    uint64_t node_budget;
+    int32_t split;
+    uint64_t timeout_ns;      // bound on any single wait
+    uint64_t max_run_ns;      // bound on a warp's time in one launch
+};
+
+// Workspace words needed by a subproblem with w local vertices of which c
+// are candidates (same formula on host and device).
+__host__ __device__ inline int64_t bk_ws_words(int64_t w, int64_t c, int32_t mode) {
+    const int64_t wc = (c + 31) / 32;
+    const int64_t S = (wc & 1) ? wc : wc + 1;
+    const int64_t fr = 4 * wc + 4;                  // cand, finic, ext, conf + meta
+    int64_t words = w                               // gid
+                    + w * S                         // A rows
+                    + 2 * (w - c)                   // F and its scratch
+                    + (c + 2) * fr                  // frames
+                    + (c + 2)                       // K path of the task
+                    + 8;
+    if (mode == BK_IMCE) words += (c + 2) * S;      // exclusion rows
+    return words;
+}
+
+mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s);
+
+}  // namespace mce

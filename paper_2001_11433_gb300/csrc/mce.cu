@@ -1,0 +1,348 @@
+// Static MCE: ParMCE (Algorithm 5) over all vertices.
+//
+//   1. rank (Section 4.2 keys or a given rank) and Γ+ lists;
+//   2. prepass: isolated vertices are maximal cliques {v} (Algorithm 1 with
+//      cand = fini = ∅); a vertex with no higher-ranked neighbour but some
+//      lower-ranked one has an empty subproblem; the rest are scheduled;
+//   3. order the subproblems, heaviest expected first (|Γ+(v)|, then degree,
+//      or a learned cost), and run the persistent search kernel.
+#include "bk.cuh"
+#include "mce_host.h"
+
+namespace mce {
+
+namespace {
+
+constexpr int32_t kCBits = 20, kWBits = 21;
+
+__global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ up_ptr, int32_t n,
+                              int32_t idb, uint64_t seed, const float *cost, unsigned long long *out,
+                              unsigned long long *pv_count, unsigned long long *pv_hash,
+                              unsigned long long *pv_nodes, int32_t *flag, uint64_t *keys,
+                              unsigned long long *req_max, const int32_t *graph_of, unsigned long long *g_count,
+                              unsigned long long *g_hash, int64_t *list_off, int32_t *list_vtx,
+                              int64_t list_max_cliques, int64_t list_max_words) {
+    unsigned long long cnt = 0, hsh = 0, nodes = 0, req = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t w = row_ptr[v + 1] - row_ptr[v];
+        const int32_t c = up_ptr[v + 1] - up_ptr[v];
+        int32_t f = 0;
+        if (w == 0) {
+            const uint64_t h = clique_hash_from_sum(vertex_hash((int32_t)v, seed), 1);
+            cnt++;
+            hsh += h;
+            nodes++;
+            if (pv_count) {
+                pv_count[v] = 1;
+                pv_hash[v] = h;
+                pv_nodes[v] = 1;
+            }
+            if (g_count) {
+                atomicAdd(&g_count[graph_of[v]], 1ULL);
+                atomicAdd(&g_hash[graph_of[v]], (unsigned long long)h);
+            }
+            if (list_off) {
+                const unsigned long long idx = atomicAdd(&out[OUT_LIST_CLIQUES], 1ULL);
+                const unsigned long long pos = atomicAdd(&out[OUT_LIST_WORDS], 2ULL);
+                if ((int64_t)idx < list_max_cliques && (int64_t)pos + 2 <= list_max_words) {
+                    list_off[idx] = (int64_t)pos;
+                    list_vtx[pos] = 1;
+                    list_vtx[pos + 1] = (int32_t)v;
+                } else {
+                    atomicOr(&out[OUT_FLAGS], 1ULL);
+                }
+            }
+        } else if (c == 0) {
+            nodes++;
+            if (pv_count) pv_nodes[v] = 1;
+        } else {
+            f = 1;
+            uint64_t k;
+            if (cost) {
+                // descending predicted cost: invert the order-preserving float map
+                uint32_t b = __float_as_uint(cost[v]);
+                b ^= (b >> 31) ? 0xffffffffu : 0x80000000u;
+                k = ((uint64_t)(~b) << idb) | (uint64_t)v;
+            } else {
+                const uint64_t cc = (uint64_t)min(c, (1 << kCBits) - 1);
+                const uint64_t ww = (uint64_t)min(w, (1 << kWBits) - 1);
+                k = ((((1ULL << kCBits) - 1 - cc) << (idb + kWBits)) | (((1ULL << kWBits) - 1 - ww) << idb)) |
+                    (uint64_t)v;
+            }
+            keys[v] = k;
+            req = max(req, (unsigned long long)bk_ws_words(w, c, BK_MCE));
+        }
+        flag[v] = f;
+    }
+    for (int o = 16; o; o >>= 1) {
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        hsh += __shfl_xor_sync(0xffffffffu, hsh, o);
+        nodes += __shfl_xor_sync(0xffffffffu, nodes, o);
+        req = max(req, __shfl_xor_sync(0xffffffffu, req, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cnt) {
+            atomicAdd(&out[OUT_COUNT], cnt);
+            atomicAdd(&out[OUT_HASH], hsh);
+            atomicAdd(&out[OUT_HIST + 1], cnt);
+            atomicMax(&out[OUT_MAXSIZE], 1ULL);
+        }
+        if (nodes) atomicAdd(&out[OUT_NODES], nodes);
+        if (req) atomicMax(req_max, req);
+    }
+}
+
+__global__ void k_gather_active(const int32_t *flag_scan, const uint64_t *keys, int32_t n, uint64_t *out) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        if (flag_scan[v + 1] != flag_scan[v]) out[flag_scan[v]] = keys[v];
+}
+
+__global__ void k_order_from_keys(const uint64_t *keys, int32_t m, int32_t idb, int32_t *order) {
+    const uint64_t mask = (1ULL << idb) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        order[i] = (int32_t)(keys[i] & mask);
+}
+
+__global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
+
+struct EvPair {
+    cudaEvent_t a, b;
+    ~EvPair() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+}  // namespace
+
+LaunchShape launch_shape(const mce_opts *o) {
+    LaunchShape ls;
+    ls.warps_per_block = (o && o->warps_per_block > 0) ? o->warps_per_block : 8;
+    if (ls.warps_per_block > 8) ls.warps_per_block = 8;
+    ls.blocks_per_sm = (o && o->blocks_per_sm > 0) ? o->blocks_per_sm : 4;
+    // shared memory per SM is 228 KB with 1 KB reserved per block
+    const int64_t per_block = (int64_t)228 * 1024 / ls.blocks_per_sm - 1024;
+    int64_t words = (per_block - 2048) / 4 / ls.warps_per_block;
+    words &= ~int64_t(3);
+    if (words < 0) words = 0;
+    ls.smem_words = (int32_t)words;
+    return ls;
+}
+
+mce_status run_bk(BkParams &P, const LaunchShape &ls, int64_t req_max, cudaStream_t s, DevBuf &gws, DevBuf &arena,
+                  DevBuf &qslot, DevBuf &ctl) {
+    const int64_t nwarps = (int64_t)num_sms() * ls.blocks_per_sm * ls.warps_per_block;
+    P.gws_words = req_max > ls.smem_words ? req_max : 16;
+    P.smem_words = ls.smem_words;
+    MCE_TRY(gws.alloc((size_t)nwarps * P.gws_words * 4, s));
+    P.gws = gws.as<uint32_t>();
+    P.arena_words = (int64_t)1 << 26;
+    P.qcap = (int64_t)1 << 22;
+    MCE_TRY(arena.alloc((size_t)P.arena_words * 4, s));
+    MCE_TRY(qslot.alloc((size_t)P.qcap * 4, s));
+    MCE_CUDA(cudaMemsetAsync(qslot.p, 0, (size_t)P.qcap * 4, s));
+    MCE_TRY(ctl.alloc(CTL_WORDS * sizeof(unsigned long long), s));
+    MCE_CUDA(cudaMemsetAsync(ctl.p, 0, CTL_WORDS * sizeof(unsigned long long), s));
+    P.arena = arena.as<uint32_t>();
+    P.qslot = qslot.as<uint32_t>();
+    P.ctl = ctl.as<unsigned long long>();
+    MCE_LAUNCH(k_set_u64, 1, 1, 0, s, P.ctl + CTL_PENDING, (unsigned long long)P.n_sub);
+    if (P.timeout_ns == 0) P.timeout_ns = 60ULL * 1000000000ULL;
+    if (P.max_run_ns == 0) P.max_run_ns = 600ULL * 1000000000ULL;
+    return launch_bk(P, ls.warps_per_block, ls.blocks_per_sm, s);
+}
+
+mce_status compute_rank(const mce_graph *g, const mce_opts *o, cudaStream_t s, int32_t *rank) {
+    const int32_t n = g->n;
+    if (n == 0) return MCE_OK;
+    switch (o->rank_kind) {
+        case MCE_RANK_USER:
+            if (!o->user_rank) {
+                g_last_error = "MCE_RANK_USER without user_rank";
+                return MCE_EINVAL;
+            }
+            MCE_CUDA(cudaMemcpyAsync(rank, o->user_rank, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+            return MCE_OK;
+        case MCE_RANK_LEARNED: {
+            if (!o->model) {
+                g_last_error = "MCE_RANK_LEARNED without a model";
+                return MCE_EINVAL;
+            }
+            DevBuf feat, score;
+            MCE_TRY(feat.alloc((size_t)n * 8 * 4, s));
+            MCE_TRY(score.alloc((size_t)n * 4, s));
+            MCE_TRY(features(g, s, feat.as<float>()));
+            MCE_TRY(model_predict(o->model, feat.as<float>(), n, 1, s, score.as<float>()));
+            return rank_from_key_f32(score.as<float>(), n, g->id_bits, s, rank);
+        }
+        case MCE_RANK_DEGREE:
+        case MCE_RANK_DEGEN:
+        case MCE_RANK_TRIANGLE: {
+            DevBuf key;
+            MCE_TRY(key.alloc((size_t)n * 8, s));
+            MCE_TRY(vertex_key(g, o->rank_kind, s, key.as<int64_t>()));
+            return rank_from_key_i64(key.as<int64_t>(), n, g->id_bits, s, rank);
+        }
+        default:
+            g_last_error = "unknown rank kind";
+            return MCE_EINVAL;
+    }
+}
+
+mce_status read_result(const DevBuf &out, const DevBuf &ctl, cudaStream_t s, mce_result *res) {
+    static_assert(OUT_WORDS * 8 < 16384, "output block");
+    unsigned long long h[OUT_WORDS];
+    unsigned long long c[CTL_WORDS];
+    MCE_CUDA(cudaMemcpyAsync(h, out.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    if (ctl.p) MCE_CUDA(cudaMemcpyAsync(c, ctl.p, sizeof(c), cudaMemcpyDeviceToHost, s));
+    else for (int i = 0; i < CTL_WORDS; ++i) c[i] = 0;
+    MCE_CUDA(cudaStreamSynchronize(s));
+    res->count = h[OUT_COUNT];
+    res->hash = h[OUT_HASH];
+    res->tree_nodes = h[OUT_NODES];
+    res->hist_len = (int32_t)(h[OUT_MAXSIZE] ? h[OUT_MAXSIZE] + 1 : 0);
+    if (res->hist_len > MCE_HIST_CAP) res->hist_len = MCE_HIST_CAP;
+    for (int i = 0; i < MCE_HIST_CAP; ++i) res->hist[i] = i < res->hist_len ? h[OUT_HIST + i] : 0;
+    res->list_cliques = (int64_t)h[OUT_LIST_CLIQUES];
+    res->list_words = (int64_t)h[OUT_LIST_WORDS];
+    res->tasks_split = h[OUT_SPLITS];
+    res->word_ops = h[OUT_WORDOPS];
+    res->complete = (c[CTL_ABORT] & 3ULL) ? 0 : 1;
+    if (c[CTL_ABORT] & 4ULL) {
+        g_last_error = "search workspace smaller than a subproblem";
+        return MCE_ESTATE;
+    }
+    if (c[CTL_ABORT] & 2ULL) {
+        g_last_error = "a bounded device wait gave up";
+        return MCE_ETIMEOUT;
+    }
+    if (c[CTL_ABORT] & 1ULL) return MCE_EBUDGET;
+    if (h[OUT_FLAGS] & 1ULL) return MCE_EOVERFLOW;
+    if (h[OUT_FLAGS] & 2ULL) {
+        g_last_error = "clique larger than the histogram";
+        return MCE_EOVERFLOW;
+    }
+    return MCE_OK;
+}
+
+mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, const int32_t *graph_of,
+                     unsigned long long *graph_nodes, uint64_t graph_budget, unsigned long long *g_count,
+                     unsigned long long *g_hash) {
+    cudaStream_t s = (cudaStream_t)o->stream;
+    const int32_t n = g->n;
+    const int32_t idb = g->id_bits;
+    if (idb > 64 - kCBits - kWBits) {
+        g_last_error = "too many vertices for the subproblem order key";
+        return MCE_EINVAL;
+    }
+    cudaEvent_t e0, e1, e2;
+    MCE_CUDA(cudaEventCreate(&e0));
+    MCE_CUDA(cudaEventCreate(&e1));
+    MCE_CUDA(cudaEventCreate(&e2));
+    struct EvGuard {
+        cudaEvent_t a, b, c;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            cudaEventDestroy(c);
+        }
+    } evg{e0, e1, e2};
+    MCE_CUDA(cudaEventRecord(e0, s));
+    DevBuf rank, out, up_ptr, up_col, flag, keys, tmp, order, cost;
+    MCE_TRY(rank.alloc((size_t)(n + 1) * 4, s));
+    MCE_TRY(compute_rank(g, o, s, rank.as<int32_t>()));
+    MCE_CUDA(cudaEventRecord(e1, s));
+    int64_t up_nnz = 0;
+    MCE_TRY(build_up_lists(g, rank.as<int32_t>(), s, up_ptr, up_col, &up_nnz));
+    const float *costp = nullptr;
+    if (o->order_by_model && o->model) {
+        DevBuf feat;
+        MCE_TRY(feat.alloc((size_t)n * 8 * 4 + 16, s));
+        MCE_TRY(cost.alloc((size_t)n * 4 + 16, s));
+        MCE_TRY(features(g, s, feat.as<float>()));
+        MCE_TRY(model_predict(o->model, feat.as<float>(), n, 1, s, cost.as<float>()));
+        costp = cost.as<float>();
+    }
+    MCE_TRY(out.alloc(OUT_WORDS * 8, s));
+    MCE_CUDA(cudaMemsetAsync(out.p, 0, OUT_WORDS * 8, s));
+    MCE_TRY(flag.alloc((size_t)(n + 1) * 4, s));
+    MCE_TRY(keys.alloc((size_t)(n + 1) * 8, s));
+    DevBuf reqb;
+    MCE_TRY(reqb.alloc(8, s));
+    MCE_CUDA(cudaMemsetAsync(reqb.p, 0, 8, s));
+    if (o->pv_count) {
+        MCE_CUDA(cudaMemsetAsync(o->pv_count, 0, (size_t)n * 8, s));
+        MCE_CUDA(cudaMemsetAsync(o->pv_hash, 0, (size_t)n * 8, s));
+        MCE_CUDA(cudaMemsetAsync(o->pv_nodes, 0, (size_t)n * 8, s));
+    }
+    if (n > 0)
+        MCE_LAUNCH(k_mce_prepass, grid_for(n, 256), 256, 0, s, g->row_ptr, up_ptr.as<int32_t>(), n, idb, o->hash_seed,
+                   costp, out.as<unsigned long long>(), (unsigned long long *)o->pv_count,
+                   (unsigned long long *)o->pv_hash, (unsigned long long *)o->pv_nodes, flag.as<int32_t>(),
+                   keys.as<uint64_t>(), reqb.as<unsigned long long>(), graph_of, g_count, g_hash, o->list_off,
+                   o->list_vtx, o->list_max_cliques, o->list_max_words);
+    MCE_TRY(exclusive_scan_i32(flag.as<int32_t>(), flag.as<int32_t>(), n, s));
+    int32_t n_act = 0;
+    unsigned long long req_max = 0;
+    MCE_CUDA(cudaMemcpyAsync(&n_act, flag.as<int32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
+    MCE_CUDA(cudaMemcpyAsync(&req_max, reqb.p, 8, cudaMemcpyDeviceToHost, s));
+    MCE_CUDA(cudaStreamSynchronize(s));
+    res->subproblems = n_act;
+    DevBuf gws, arena, qslot, ctl;
+    if (n_act > 0) {
+        MCE_TRY(tmp.alloc((size_t)n_act * 8 * 2, s));
+        MCE_TRY(order.alloc((size_t)n_act * 4, s));
+        uint64_t *act = tmp.as<uint64_t>(), *act_tmp = act + n_act;
+        MCE_LAUNCH(k_gather_active, grid_for(n, 256), 256, 0, s, flag.as<int32_t>(), keys.as<uint64_t>(), n, act);
+        MCE_TRY(radix_sort_u64(act, act_tmp, n_act, 64, s));
+        MCE_LAUNCH(k_order_from_keys, grid_for(n_act, 256), 256, 0, s, act, n_act, idb, order.as<int32_t>());
+        BkParams P{};
+        P.mode = BK_MCE;
+        P.row_ptr = g->row_ptr;
+        P.col = g->col;
+        P.up_ptr = up_ptr.as<int32_t>();
+        P.up_col = up_col.as<int32_t>();
+        P.rank = rank.as<int32_t>();
+        P.order = order.as<int32_t>();
+        P.n_sub = n_act;
+        P.graph_of = graph_of;
+        P.graph_nodes = graph_nodes;
+        P.graph_budget = graph_budget;
+        P.g_count = g_count;
+        P.g_hash = g_hash;
+        P.seed = o->hash_seed;
+        P.out = out.as<unsigned long long>();
+        P.list_off = o->list_off;
+        P.list_vtx = o->list_vtx;
+        P.list_max_cliques = o->list_max_cliques;
+        P.list_max_words = o->list_max_words;
+        P.pv_count = (unsigned long long *)o->pv_count;
+        P.pv_hash = (unsigned long long *)o->pv_hash;
+        P.pv_nodes = (unsigned long long *)o->pv_nodes;
+        P.node_budget = o->node_budget;
+        P.split = o->split;
+        P.max_run_ns = (uint64_t)o->time_limit_ms * 1000000ULL;
+        const LaunchShape ls = launch_shape(o);
+        cudaEvent_t k0, k1;
+        MCE_CUDA(cudaEventCreate(&k0));
+        MCE_CUDA(cudaEventCreate(&k1));
+        EvPair kg{k0, k1};
+        MCE_CUDA(cudaEventRecord(k0, s));
+        MCE_TRY(run_bk(P, ls, (int64_t)req_max, s, gws, arena, qslot, ctl));
+        MCE_CUDA(cudaEventRecord(k1, s));
+        MCE_CUDA(cudaEventSynchronize(k1));
+        float ks = 0;
+        cudaEventElapsedTime(&ks, k0, k1);
+        res->ms_search = ks;
+    }
+    MCE_CUDA(cudaEventRecord(e2, s));
+    mce_status st = read_result(out, ctl, s, res);
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, e0, e1);
+    cudaEventElapsedTime(&b, e1, e2);
+    res->ms_rank = a;
+    res->ms_enum = b;
+    return st;
+}
+
+}  // namespace mce

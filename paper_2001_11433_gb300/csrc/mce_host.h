@@ -1,0 +1,26 @@
+// Host-side declarations shared by the orchestration files.
+#pragma once
+
+#include "bk.cuh"
+
+namespace mce {
+
+struct LaunchShape {
+    int32_t warps_per_block = 8;
+    int32_t blocks_per_sm = 4;
+    int32_t smem_words = 0;
+};
+
+LaunchShape launch_shape(const mce_opts *o);
+mce_status run_bk(BkParams &P, const LaunchShape &ls, int64_t req_max, cudaStream_t s, DevBuf &gws, DevBuf &arena,
+                  DevBuf &qslot, DevBuf &ctl);
+mce_status compute_rank(const mce_graph *g, const mce_opts *o, cudaStream_t s, int32_t *rank);
+mce_status read_result(const DevBuf &out, const DevBuf &ctl, cudaStream_t s, mce_result *res);
+mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, const int32_t *graph_of,
+                     unsigned long long *graph_nodes, uint64_t graph_budget, unsigned long long *g_count,
+                     unsigned long long *g_hash);
+// learned cost model (mlp.cu)
+mce_status model_predict(const mce_model *m, const float *feat, int32_t rows, int32_t bf16, cudaStream_t s,
+                         float *out);
+
+}  // namespace mce

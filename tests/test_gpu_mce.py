@@ -1,0 +1,241 @@
+"""GPU parity of static MCE against the CPU oracle (through the C-ABI)."""
+import itertools
+import json
+import os
+import random
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+def gpu_graph(mce, n, u, v, device=True):
+    return mce.Graph(n, _t(u), _t(v)) if device else mce.Graph(n, u, v)
+
+
+def per_vertex_bufs(n):
+    import torch
+    return tuple(torch.zeros(max(n, 1), dtype=torch.int64, device="cuda") for _ in range(3))
+
+
+def list_bufs(max_cliques, max_words):
+    import torch
+    return (torch.empty(max_cliques, dtype=torch.int64, device="cuda"),
+            torch.empty(max_words, dtype=torch.int32, device="cuda"))
+
+
+def u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def assert_same_summary(r, o):
+    assert r.count == o.count
+    assert r.hash == o.hash
+    assert list(r.hist) == list(o.hist)
+
+
+def random_pairs(n, p, rng):
+    return [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < p]
+
+
+def rmat(scale, seed=5):
+    u, v = graphgen.rmat(scale, 16 << scale, 0.57, 0.19, 0.19, seed)
+    return 1 << scale, u, v
+
+
+# ---------------------------------------------------------------- ingest and keys
+
+@pytest.mark.parametrize("case", ["er", "rmat12", "messy", "empty", "isolated"])
+def test_csr_matches_oracle(gpu_lib, case):
+    mce = gpu_lib
+    if case == "er":
+        w = graphgen.er_2000()
+        n, u, v = w.n, w.u, w.v
+    elif case == "rmat12":
+        n, u, v = rmat(12)
+    elif case == "messy":
+        rng = np.random.default_rng(1)
+        n = 777
+        u = rng.integers(0, n, 20000).astype(np.int32)
+        v = rng.integers(0, n, 20000).astype(np.int32)
+        u[:50] = v[:50]                                        # self loops
+        u, v = np.concatenate([u, v]), np.concatenate([v, u])  # both directions and repeats
+    elif case == "empty":
+        n, u, v = 5, np.zeros(0, np.int32), np.zeros(0, np.int32)
+    else:
+        n, u, v = 1000, np.array([3, 4, 999], np.int32), np.array([4, 5, 0], np.int32)
+    og = O.Graph(n, u, v)
+    rp, col = og.csr()
+    for dev in (True, False):
+        g = gpu_graph(mce, n, u, v, device=dev)
+        grp, gcol = g.csr()
+        assert np.array_equal(grp.astype(np.int64), rp)
+        assert np.array_equal(gcol, col)
+
+
+def test_invalid_vertex_id(gpu_lib):
+    mce = gpu_lib
+    with pytest.raises(mce.MceError) as e:
+        mce.Graph(10, np.array([1, 10], np.int32), np.array([2, 3], np.int32))
+    assert e.value.status == mce.MCE_EINVAL
+
+
+@pytest.mark.parametrize("case", ["er", "rmat13", "dense"])
+def test_vertex_keys_and_ranks(gpu_lib, case):
+    mce = gpu_lib
+    if case == "er":
+        w = graphgen.er_2000()
+        n, u, v = w.n, w.u, w.v
+    elif case == "rmat13":
+        n, u, v = rmat(13)
+    else:
+        n = 300
+        u, v = graphgen.er(n, 0.4, 3)
+    og = O.Graph(n, u, v)
+    g = gpu_graph(mce, n, u, v)
+    assert np.array_equal(mce.vertex_key(g, "degree").cpu().numpy(), O.degree(og))
+    assert np.array_equal(mce.vertex_key(g, "degen").cpu().numpy(), O.core_numbers(og).astype(np.int64))
+    assert np.array_equal(mce.vertex_key(g, "triangle").cpu().numpy(), O.triangles(og))
+    for kind in ("degree", "degen", "triangle"):
+        assert np.array_equal(mce.rank(g, rank=kind).cpu().numpy(), O.rank(og, kind)), kind
+
+
+# ---------------------------------------------------------------- enumeration: small exact cases
+
+def _check_lists(mce, n, pairs, expect, **kw):
+    u = np.array([a for a, b in pairs], np.int32)
+    v = np.array([b for a, b in pairs], np.int32)
+    g = mce.Graph(n, u, v)
+    off, vtx = list_bufs(4096, 65536)
+    r = mce.enumerate_cliques(g, list_buf=(off, vtx), **kw)
+    got = mce.decode_list(off, vtx, r.list_cliques)
+    assert got == expect
+    assert r.count == len(expect)
+    return r
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_small_random_vs_brute_force_oracle(gpu_lib, seed):
+    rng = random.Random(500 + seed)
+    n = rng.randint(1, 40)
+    pairs = random_pairs(n, rng.choice([0.1, 0.3, 0.5, 0.8]), rng)
+    og = O.Graph(n, np.array([a for a, b in pairs], np.int32), np.array([b for a, b in pairs], np.int32))
+    expect = O.ttt_whole(og, want_list=True).cliques
+    for kind in ("degree", "degen", "triangle"):
+        _check_lists(gpu_lib, n, pairs, expect, rank=kind)
+
+
+@pytest.mark.parametrize("shape", ["K1", "K2", "K33", "K64", "K70", "empty9", "C3", "C4", "C50", "mm4", "mm6"])
+def test_closed_forms(gpu_lib, shape):
+    mce = gpu_lib
+    if shape.startswith("K"):
+        n = int(shape[1:])
+        pairs = list(itertools.combinations(range(n), 2))
+        expect = [tuple(range(n))]
+    elif shape.startswith("empty"):
+        n = int(shape[5:])
+        pairs = []
+        expect = [(i,) for i in range(n)]
+    elif shape.startswith("C"):
+        n = int(shape[1:])
+        pairs = [(i, (i + 1) % n) for i in range(n)]
+        expect = [(0, 1, 2)] if n == 3 else sorted(tuple(sorted(p)) for p in pairs)
+    else:
+        k = int(shape[2:])
+        parts = [list(range(3 * i, 3 * i + 3)) for i in range(k)]
+        n = 3 * k
+        pairs = [(a, b) for i in range(k) for j in range(i + 1, k) for a in parts[i] for b in parts[j]]
+        expect = sorted(tuple(sorted(c)) for c in itertools.product(*parts))
+    _check_lists(mce, n, pairs, expect)
+
+
+def test_er_2000_full_list(gpu_lib):
+    mce = gpu_lib
+    w = graphgen.er_2000()
+    og = O.Graph(w.n, w.u, w.v)
+    expect = O.ttt_whole(og, want_list=True).cliques
+    with open(os.path.join(GOLDEN, "er_2000.json")) as f:
+        gold = json.load(f)
+    assert len(expect) == gold["count"]
+    g = gpu_graph(mce, w.n, w.u, w.v)
+    off, vtx = list_bufs(40000, 200000)
+    r = mce.enumerate_cliques(g, list_buf=(off, vtx))
+    assert mce.decode_list(off, vtx, r.list_cliques) == expect
+    assert r.count == gold["count"] and r.hash == int(gold["hash"]) and list(r.hist) == gold["hist"]
+
+
+# ---------------------------------------------------------------- per-subproblem parity incl. tree nodes
+
+@pytest.mark.parametrize("kind", ["degree", "degen", "triangle"])
+@pytest.mark.parametrize("split", [False, True])
+def test_rmat13_per_vertex_exact(gpu_lib, kind, split):
+    """Each subproblem's count, hash and search-tree node count equal the
+    oracle's under the same rank and pivot tie-break."""
+    mce = gpu_lib
+    n, u, v = rmat(13)
+    og = O.Graph(n, u, v)
+    rk = O.rank(og, kind)
+    o = O.parmce(og, rk, per_vertex=True, threads=4)
+    g = gpu_graph(mce, n, u, v)
+    pv = per_vertex_bufs(n)
+    r = mce.enumerate_cliques(g, rank=kind, per_vertex=pv, split=split)
+    assert_same_summary(r, o)
+    assert r.tree_nodes == o.nodes
+    assert np.array_equal(u64(pv[0]), o.per_vertex["count"])
+    assert np.array_equal(u64(pv[1]), o.per_vertex["hash"])
+    assert np.array_equal(u64(pv[2]), o.per_vertex["nodes"])
+
+
+def test_user_rank_random_permutation(gpu_lib):
+    mce = gpu_lib
+    n, u, v = rmat(12, seed=9)
+    og = O.Graph(n, u, v)
+    perm = np.random.default_rng(4).permutation(n).astype(np.int32)
+    o = O.parmce(og, perm, per_vertex=True, threads=4)
+    g = gpu_graph(mce, n, u, v)
+    pv = per_vertex_bufs(n)
+    r = mce.enumerate_cliques(g, rank="user", user_rank=_t(perm), per_vertex=pv)
+    assert_same_summary(r, o)
+    assert np.array_equal(u64(pv[2]), o.per_vertex["nodes"])
+
+
+def test_hash_seed(gpu_lib):
+    mce = gpu_lib
+    w = graphgen.er(500, 0.05, 12)
+    og = O.Graph(500, *w)
+    g = gpu_graph(mce, 500, *w)
+    for seed in (0, 12345, 2 ** 63 + 7):
+        assert mce.enumerate_cliques(g, seed=seed).hash == O.parmce(og, O.rank(og, "degen"), seed=seed).hash
+
+
+# ---------------------------------------------------------------- statuses
+
+def test_node_budget(gpu_lib):
+    mce = gpu_lib
+    n, u, v = rmat(13)
+    g = gpu_graph(mce, n, u, v)
+    r = mce.enumerate_cliques(g, node_budget=1000, allow=(mce.MCE_EBUDGET,))
+    assert r.status == mce.MCE_EBUDGET and not r.complete
+
+
+def test_list_overflow_keeps_summary(gpu_lib):
+    mce = gpu_lib
+    w = graphgen.er_2000()
+    og = O.Graph(w.n, w.u, w.v)
+    o = O.ttt_whole(og)
+    g = gpu_graph(mce, w.n, w.u, w.v)
+    off, vtx = list_bufs(100, 1000)
+    r = mce.enumerate_cliques(g, list_buf=(off, vtx), allow=(mce.MCE_EOVERFLOW,))
+    assert r.status == mce.MCE_EOVERFLOW
+    assert_same_summary(r, o)
