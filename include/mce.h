@@ -100,6 +100,18 @@ typedef struct {
     int32_t warps_per_block;      /* 0 = automatic */
     int32_t blocks_per_sm;        /* 0 = automatic */
     uint32_t time_limit_ms;       /* stop the search after this long (MCE_ETIMEOUT); 0 = 600 s */
+    /* Optional restriction to the subproblems of some vertices (device
+     * int32[subset_len], distinct ids); NULL = every vertex. */
+    const int32_t *subset;
+    int64_t subset_len;
+    int32_t subset_on_host;       /* 1 = subset is host memory (copied in) */
+    /* Abandon a subproblem once its search tree passes this many nodes
+     * (0 = never).  Node credits are exact, so a subproblem is abandoned iff
+     * its tree has more nodes than the budget.  Abandoned subproblems are
+     * counted in mce_result.incomplete; the summary then includes their
+     * partial output, while per-subproblem outputs identify them
+     * (pv_nodes > budget). */
+    uint64_t subproblem_budget;
 } mce_opts;
 
 typedef struct {
@@ -119,6 +131,11 @@ typedef struct {
     uint64_t word_ops;            /* 32-bit AND+POPC word operations of the search:
                                      per node (|cand|+|fini|)*ceil(c/32) for the pivot,
                                      per child 2*ceil(c/32) + |F| */
+    int64_t incomplete;           /* subproblems abandoned by subproblem_budget */
+    uint64_t stats[8];            /* search kernel, summed over warps: [0] ns building subproblems,
+                                     [1] ns searching, [2] ns waiting for work, [3] builds,
+                                     [4] handed-over pieces run, [5] largest busy ns of one
+                                     warp, [6] warps, [7] unused */
 } mce_result;
 
 /* ---------------------------------------------------------------- misc */

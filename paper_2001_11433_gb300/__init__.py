@@ -52,6 +52,10 @@ class Opts(ctypes.Structure):
         ("warps_per_block", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32),
         ("time_limit_ms", ctypes.c_uint32),
+        ("subset", ctypes.c_void_p),
+        ("subset_len", ctypes.c_int64),
+        ("subset_on_host", ctypes.c_int32),
+        ("subproblem_budget", ctypes.c_uint64),
     ]
 
 
@@ -71,6 +75,8 @@ class ResultC(ctypes.Structure):
         ("ms_enum", ctypes.c_float),
         ("ms_search", ctypes.c_float),
         ("word_ops", ctypes.c_uint64),
+        ("incomplete", ctypes.c_int64),
+        ("stats", ctypes.c_uint64 * 8),
     ]
 
 
@@ -192,13 +198,15 @@ class Result:
     ms_search: float = 0.0
     word_ops: int = 0
     status: int = 0
+    stats: tuple = ()
+    incomplete: int = 0
 
 
 def _result(r: ResultC, status: int) -> Result:
     hist = np.array(r.hist[: r.hist_len], dtype=np.uint64)
     return Result(int(r.count), int(r.hash), int(r.tree_nodes), hist, bool(r.complete), int(r.list_cliques),
                   int(r.list_words), int(r.tasks_split), int(r.subproblems), float(r.ms_rank), float(r.ms_enum),
-                  float(r.ms_search), int(r.word_ops), status)
+                  float(r.ms_search), int(r.word_ops), status, tuple(int(x) for x in r.stats), int(r.incomplete))
 
 
 class Graph:
@@ -256,7 +264,7 @@ class Graph:
 
 def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, stream=None, list_buf=None,
               per_vertex=None, split=True, order_by_model=False, warps_per_block=0, blocks_per_sm=0,
-              time_limit_ms=0) -> Opts:
+              time_limit_ms=0, subset=None, subproblem_budget=0) -> Opts:
     o = Opts()
     load().mce_opts_init(ctypes.byref(o))
     o.rank_kind = RANKS[rank] if isinstance(rank, str) else int(rank)
@@ -276,6 +284,10 @@ def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, s
     o.warps_per_block = warps_per_block
     o.blocks_per_sm = blocks_per_sm
     o.time_limit_ms = time_limit_ms
+    if subset is not None:
+        o.subset, o.subset_len = _ptr(subset), int(subset.numel() if hasattr(subset, "numel") else len(subset))
+        o.subset_on_host = int(isinstance(subset, np.ndarray) or not subset.is_cuda)
+    o.subproblem_budget = subproblem_budget
     return o
 
 

@@ -44,6 +44,8 @@ constexpr uint32_t FULL = 0xffffffffu;
 struct Ws {
     int32_t w, c, W, f, wc, S;   // local vertices, candidates, kept vertices, kept fini, words, stride
     int32_t *gid;
+    int32_t *bnd;                 // popc(A[x]): bound on |cand ∩ Γ(x)| at every node
+    int32_t *F0;                  // kept lower-ranked vertices sorted by bnd, descending
     uint32_t *A;
     uint32_t *X;                  // IMCE exclusion rows
     int32_t *F, *Fs;
@@ -74,8 +76,12 @@ __device__ __forceinline__ void ws_layout(Ws &s, uint32_t *base, int32_t w, int3
     uint32_t *p = base;
     s.gid = reinterpret_cast<int32_t *>(p);
     p += w;
+    s.bnd = reinterpret_cast<int32_t *>(p);
+    p += w;
     s.A = p;
     p += (int64_t)w * s.S;
+    s.F0 = reinterpret_cast<int32_t *>(p);
+    p += (w - c);
     s.F = reinterpret_cast<int32_t *>(p);
     p += (w - c);
     s.Fs = reinterpret_cast<int32_t *>(p);
@@ -152,6 +158,75 @@ __device__ int partition_F(const Ws &s, int len, int lane, Pred pred) {
     return wpos;
 }
 
+// F[0..a) and F[a..len) are each sorted by bnd (descending); merge them
+// stably (the first run wins ties) through the scratch array.  Output
+// positions come from ranks in the other run (merge path), so lanes write
+// disjoint slots.
+__device__ void merge_F(const Ws &s, int a, int len, int lane) {
+    const int b = len - a;
+    if (a == 0 || b == 0) return;
+    for (int i = lane; i < a; i += 32) {
+        const int32_t x = s.F[i];
+        const int32_t key = s.bnd[x];
+        int lo = 0, hi = b;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s.bnd[s.F[a + mid]] > key) lo = mid + 1; else hi = mid;
+        }
+        s.Fs[i + lo] = x;
+    }
+    for (int j = lane; j < b; j += 32) {
+        const int32_t x = s.F[a + j];
+        const int32_t key = s.bnd[x];
+        int lo = 0, hi = a;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s.bnd[s.F[mid]] >= key) lo = mid + 1; else hi = mid;
+        }
+        s.Fs[j + lo] = x;
+    }
+    __syncwarp();
+    for (int i = lane; i < len; i += 32) s.F[i] = s.Fs[i];
+    __syncwarp();
+}
+
+// bnd[x] = popc(A[x]) for every kept local vertex, and F0 = the kept
+// lower-ranked vertices [c, W) ordered by bnd descending (counting sort; the
+// frames area serves as the histogram before any frame exists).
+__device__ void sort_F0(const Ws &s, int lane) {
+    for (int x = lane; x < s.W; x += 32) {
+        const uint32_t *row = s.A + (int64_t)x * s.S;
+        int b = 0;
+        for (int k = 0; k < s.wc; ++k) b += __popc(row[k]);
+        s.bnd[x] = b;
+    }
+    if (s.f == 0) {
+        __syncwarp();
+        return;
+    }
+    int32_t *hist = reinterpret_cast<int32_t *>(s.fr);
+    for (int b = lane; b <= s.c; b += 32) hist[b] = 0;
+    __syncwarp();
+    for (int x = s.c + lane; x < s.W; x += 32) atomicAdd(&hist[s.bnd[x]], 1);
+    __syncwarp();
+    // start[b] = number of kept vertices with a larger bound
+    int run = 0;
+    for (int top = s.c; top >= 0; top -= 32) {
+        const int b = top - lane;
+        const int h = b >= 0 ? hist[b] : 0;
+        int incl = h;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (b >= 0) hist[b] = run + incl - h;
+        run += __shfl_sync(FULL, incl, 31);
+    }
+    __syncwarp();
+    for (int x = s.c + lane; x < s.W; x += 32) s.F0[atomicAdd(&hist[s.bnd[x]], 1)] = x;
+    __syncwarp();
+}
+
 // ------------------------------------------------------------------ subproblem build
 
 // ParMCE subproblem of v (Algorithm 5).  Local order: Γ+(v) (the candidates,
@@ -217,8 +292,8 @@ __device__ void build_mce(const BkParams &P, Ws &s, int32_t v, int lane) {
     }
     s.f = f;
     s.W = c + f;
-    for (int i = lane; i < f; i += 32) s.F[i] = c + i;
     __syncwarp();
+    sort_F0(s, lane);
 }
 
 // ParIMCENew subproblem of new edge i = (u, v) (Algorithm 6): local vertices
@@ -258,9 +333,12 @@ __device__ void build_imce(const BkParams &P, Ws &s, int32_t i, int lane) {
     s.f = 0;
     {
         uint32_t *p = reinterpret_cast<uint32_t *>(s.gid) + c;
+        s.bnd = reinterpret_cast<int32_t *>(p);
+        p += c;
         s.A = p;
         p += (int64_t)c * s.S;
-        s.F = reinterpret_cast<int32_t *>(p);
+        s.F0 = reinterpret_cast<int32_t *>(p);
+        s.F = s.F0;
         s.Fs = s.F;
         s.fr = p;
         p += (int64_t)(c + 2) * s.frw;
@@ -300,14 +378,23 @@ __device__ void build_imce(const BkParams &P, Ws &s, int32_t i, int lane) {
         }
     }
     __syncwarp();
+    for (int x = lane; x < c; x += 32) {
+        const uint32_t *row = s.A + (int64_t)x * s.S;
+        int b = 0;
+        for (int k = 0; k < s.wc; ++k) b += __popc(row[k]);
+        s.bnd[x] = b;
+    }
+    __syncwarp();
 }
 
 // ------------------------------------------------------------------ output
 
 struct Acc {
+    unsigned long long build_ns, search_ns, idle_ns, builds, pieces, max_busy;
     unsigned long long wops;                 // per lane: algorithmic word operations
     unsigned long long count, hash, nodes;   // per warp, whole launch
     unsigned long long t_count, t_hash, t_nodes;   // per task
+    unsigned long long t_rep;                      // t_nodes already credited to sub_nodes
 };
 
 __device__ void emit(const BkParams &P, const Ws &s, int32_t root, int32_t k0, int d, uint64_t hsum, Acc &acc,
@@ -363,45 +450,61 @@ __device__ void emit(const BkParams &P, const Ws &s, int32_t root, int32_t k0, i
 
 // ------------------------------------------------------------------ task queue
 
-// Reserve arena space and a queue slot; returns arena offset or -1.
-__device__ int64_t queue_reserve(const BkParams &P, int64_t words, int64_t *slot) {
-    const unsigned long long off = atomicAdd(&P.ctl[CTL_ARENA], (unsigned long long)words);
-    if ((int64_t)(off + words) > P.arena_words) return -1;
-    const unsigned long long t = atomicAdd(&P.ctl[CTL_QTAIL], 1ULL);
-    if ((int64_t)t >= P.qcap) return -1;
-    *slot = (int64_t)t;
-    return (int64_t)off;
-}
-
-__device__ void queue_publish(const BkParams &P, int64_t slot, int64_t off) {
-    atomicAdd(&P.ctl[CTL_PENDING], 1ULL);
-    __threadfence();
-    atomicExch(&P.qslot[slot], (uint32_t)(off + 1));
-}
-
-// Pop one task; returns its arena offset or -1.  Waits (bounded) for a
-// claimed slot whose pusher has not published yet.
-__device__ int64_t queue_pop(const BkParams &P) {
+// Bounded multi-producer multi-consumer ring (sequence numbers per slot, as
+// in D. Vyukov's bounded MPMC queue).  Slot i holds one record of
+// P.slot_words words at P.arena + i * slot_words.  qseq[i] == pos means free
+// for the pusher holding ticket pos; == pos + 1 means published for the
+// popper holding ticket pos; the popper sets it to pos + qcap when done.
+// Neither side ever waits: a full ring refuses the push, an empty ring the pop.
+__device__ int64_t queue_claim_push(const BkParams &P) {
+    unsigned long long pos = *(volatile unsigned long long *)&P.ctl[CTL_QTAIL];
     for (int tries = 0; tries < 64; ++tries) {
-        const unsigned long long h = *(volatile unsigned long long *)&P.ctl[CTL_QHEAD];
-        unsigned long long t = *(volatile unsigned long long *)&P.ctl[CTL_QTAIL];
-        if (t > (unsigned long long)P.qcap) t = (unsigned long long)P.qcap;
-        if (h >= t) return -1;
-        if (atomicCAS(&P.ctl[CTL_QHEAD], h, h + 1) == h) {
-            const uint64_t t0 = globaltimer_ns();
-            uint32_t v;
-            while ((v = *(volatile uint32_t *)&P.qslot[h]) == 0u) {
-                if (globaltimer_ns() - t0 > P.timeout_ns) {
-                    atomicOr(&P.ctl[CTL_ABORT], 2ULL);
-                    return -1;
-                }
-                __nanosleep(100);
-            }
-            __threadfence();
-            return (int64_t)v - 1;
+        const unsigned long long seq = *(volatile unsigned long long *)&P.qseq[pos % (unsigned long long)P.qcap];
+        const long long dif = (long long)seq - (long long)pos;
+        if (dif == 0) {
+            const unsigned long long prev = atomicCAS(&P.ctl[CTL_QTAIL], pos, pos + 1);
+            if (prev == pos) return (int64_t)pos;
+            pos = prev;
+        } else if (dif < 0) {
+            return -1;
+        } else {
+            pos = *(volatile unsigned long long *)&P.ctl[CTL_QTAIL];
         }
     }
     return -1;
+}
+
+__device__ void queue_publish(const BkParams &P, int64_t pos) {
+    atomicAdd(&P.ctl[CTL_PENDING], 1ULL);
+    __threadfence();
+    atomicExch(&P.qseq[(unsigned long long)pos % (unsigned long long)P.qcap], (unsigned long long)pos + 1ULL);
+}
+
+__device__ int64_t queue_claim_pop(const BkParams &P) {
+    unsigned long long pos = *(volatile unsigned long long *)&P.ctl[CTL_QHEAD];
+    for (int tries = 0; tries < 64; ++tries) {
+        const unsigned long long seq = *(volatile unsigned long long *)&P.qseq[pos % (unsigned long long)P.qcap];
+        const long long dif = (long long)seq - (long long)(pos + 1);
+        if (dif == 0) {
+            const unsigned long long prev = atomicCAS(&P.ctl[CTL_QHEAD], pos, pos + 1);
+            if (prev == pos) {
+                __threadfence();
+                return (int64_t)pos;
+            }
+            pos = prev;
+        } else if (dif < 0) {
+            return -1;
+        } else {
+            pos = *(volatile unsigned long long *)&P.ctl[CTL_QHEAD];
+        }
+    }
+    return -1;
+}
+
+__device__ void queue_release(const BkParams &P, int64_t pos) {
+    __threadfence();
+    atomicExch(&P.qseq[(unsigned long long)pos % (unsigned long long)P.qcap],
+               (unsigned long long)pos + (unsigned long long)P.qcap);
 }
 
 // ------------------------------------------------------------------ the search
@@ -414,8 +517,8 @@ struct Task {
 
 // Run one task to completion.  Returns false when the launch must stop.
 __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigned long long *shist,
-                         uint32_t *ws_smem, uint32_t *ws_glob, int lane, int32_t &built, int &node_tick,
-                         uint64_t t_start) {
+                         uint32_t *ws_smem, uint32_t *ws_glob, const uint32_t *taskbuf, int lane,
+                         int32_t &built, int &node_tick, uint64_t t_start) {
     const int32_t root = T.root;
     // ---- build (or reuse) the subproblem
     int32_t w, c;
@@ -434,30 +537,18 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
         if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 4ULL);
         return false;
     }
-    ws_layout(s, base, w, c, P.mode);
+    ws_layout(s, base, w, c, P.mode);   // same pointers as the last build of `root`; f and W kept
     const int k0 = (P.mode == BK_MCE ? 1 : 2) + T.kdepth;
-    if (built != root) {
+    const uint64_t tb = globaltimer_ns();
+    if (built != root || P.mode == BK_IMCE) {
         if (P.mode == BK_MCE) {
             build_mce(P, s, root, lane);
         } else {
             build_imce(P, s, root, lane);
         }
         built = root;
-    } else if (P.mode == BK_MCE) {
-        // same layout as the previous build; recover W and f from the kept rows
-        // (F[0..f) is rewritten below)
-        int f = 0;
-        for (int b0 = c; b0 < w; b0 += 32) {
-            const int x = b0 + lane;
-            bool nz = false;
-            if (x < w)
-                for (int k = 0; k < s.wc; ++k) nz |= s.A[(int64_t)x * s.S + k] != 0u;
-            f += __popc(__ballot_sync(FULL, nz));
-        }
-        s.f = f;
-        s.W = c + f;
-    } else {
-        build_imce(P, s, root, lane);
+        acc.builds++;
+        acc.build_ns += globaltimer_ns() - tb;
     }
     // ---- frame 0
     uint64_t hs0 = P.mode == BK_MCE ? vertex_hash(root, P.seed)
@@ -474,7 +565,7 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
             if (P.mode == BK_MCE) fr_conf(s, 0)[k] = 0u;
         }
         if (P.mode == BK_MCE) {
-            for (int i = lane; i < s.f; i += 32) s.F[i] = s.c + i;
+            for (int i = lane; i < s.f; i += 32) s.F[i] = s.F0[i];
         }
         if (lane == 0) {
             m0[0] = (uint32_t)s.f;
@@ -482,23 +573,24 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
         }
         enter = true;
     } else {
-        // handed-over frame: path, cand, finic, ext, conf
-        const uint32_t *r = P.arena + T.rec;
+        // handed-over frame (copied to this warp's task buffer): path, cand, finic, ext, conf
+        const uint32_t *r = taskbuf;
         const int kd = T.kdepth;
-        for (int j = lane; j < kd; j += 32) s.kpath[j] = (int32_t)__ldcg(r + 2 + j);
+        for (int j = lane; j < kd; j += 32) s.kpath[j] = (int32_t)r[2 + j];
         const uint32_t *rb = r + 2 + kd;
         for (int k = lane; k < s.wc; k += 32) {
-            fr_cand(s, 0)[k] = __ldcg(rb + k);
-            fr_finic(s, 0)[k] = __ldcg(rb + s.wc + k);
-            fr_ext(s, 0)[k] = __ldcg(rb + 2 * s.wc + k);
-            fr_conf(s, 0)[k] = __ldcg(rb + 3 * s.wc + k);
+            fr_cand(s, 0)[k] = rb[k];
+            fr_finic(s, 0)[k] = rb[s.wc + k];
+            fr_ext(s, 0)[k] = rb[2 * s.wc + k];
+            fr_conf(s, 0)[k] = rb[3 * s.wc + k];
         }
         __syncwarp();
         for (int j = 0; j < kd; ++j) hs0 += vertex_hash(s.gid[s.kpath[j]], P.seed);
         int flen = 0;
         if (P.mode == BK_MCE) {
-            // F at this frame: the kept lower-ranked vertices adjacent to the whole path
-            for (int i = lane; i < s.f; i += 32) s.F[i] = s.c + i;
+            // F at this frame: the kept lower-ranked vertices adjacent to the whole path,
+            // still ordered by bnd (the partition is stable)
+            for (int i = lane; i < s.f; i += 32) s.F[i] = s.F0[i];
             __syncwarp();
             flen = s.f;
             for (int j = 0; j < kd; ++j) {
@@ -559,29 +651,32 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
                         }
                     }
                 }
+                // F is ordered by bnd = popc(A[u]) >= |cand ∩ A[u]|; once the bound
+                // of the next entries drops below the best count none of them can
+                // win (a tie needs count == best), so the scan stops there.
                 const int flen = (int)meta[0];
                 if (flen) {
-                    // counts for F, dropping members with no candidate neighbour
-                    const int nf = partition_F(s, flen, lane, [&](int32_t u) {
-                        const uint32_t *row = s.A + (int64_t)u * s.S;
-                        uint32_t cnt = 0;
-                        for (int t = 0; t < s.wc; ++t) cnt += __popc(cand[t] & row[t]);
-                        return cnt != 0u;
-                    });
-                    acc.wops += (unsigned long long)s.wc * (unsigned long long)((flen - lane + 31) / 32);
-                    for (int i = lane; i < nf; i += 32) {
-                        const int u = s.F[i];
-                        const uint32_t *row = s.A + (int64_t)u * s.S;
-                        uint32_t cnt = 0;
-                        for (int t = 0; t < s.wc; ++t) cnt += __popc(cand[t] & row[t]);
-                        const int32_t g = s.gid[u];
-                        if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
-                            best_cnt = cnt;
-                            best_gid = g;
-                            best_loc = u;
+                    uint32_t thr = __reduce_max_sync(FULL, best_loc >= 0 ? best_cnt + 1u : 0u);
+                    for (int b0 = 0; b0 < flen; b0 += 32) {
+                        const int i = b0 + lane;
+                        if (i < flen) {
+                            const int u = s.F[i];
+                            if ((uint32_t)s.bnd[u] + 1u >= thr) {
+                                const uint32_t *row = s.A + (int64_t)u * s.S;
+                                uint32_t cnt = 0;
+                                for (int t = 0; t < s.wc; ++t) cnt += __popc(cand[t] & row[t]);
+                                acc.wops += (unsigned long long)s.wc;
+                                const int32_t g = s.gid[u];
+                                if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
+                                    best_cnt = cnt;
+                                    best_gid = g;
+                                    best_loc = u;
+                                }
+                            }
                         }
+                        thr = __reduce_max_sync(FULL, best_loc >= 0 ? best_cnt + 1u : 0u);
+                        if (b0 + 32 < flen && (uint32_t)s.bnd[s.F[b0 + 32]] + 1u < thr) break;
                     }
-                    if (lane == 0) meta[0] = (uint32_t)nf;
                 }
                 // warp argmax (lanes without a candidate hold best_loc = -1)
                 const uint32_t key_cnt = best_loc >= 0 ? best_cnt + 1u : 0u;
@@ -610,6 +705,12 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
                             ab |= 1ULL;
                         }
                     }
+                    if (P.sub_nodes) {
+                        const unsigned long long delta = acc.t_nodes - acc.t_rep;
+                        acc.t_rep = acc.t_nodes;
+                        const unsigned long long tot = atomicAdd(&P.sub_nodes[root], delta) + delta;
+                        if (tot > P.sub_budget) ab |= 16ULL;
+                    }
                     if (P.graph_nodes) {
                         const int32_t gg = P.graph_of[P.mode == BK_MCE ? root : P.eu[root]];
                         const unsigned long long tot = atomicAdd(&P.graph_nodes[gg], 64ULL) + 64ULL;
@@ -626,7 +727,7 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
                 hungry = __shfl_sync(FULL, hungry, 0);
                 if (ab & 1ULL) return false;
                 if (ab & 2ULL) return false;
-                if (ab & 16ULL) return true;   // this graph is over its budget: drop the task
+                if (ab & 16ULL) return true;   // this graph / subproblem is over its budget: drop the task
                 if (hungry) {
                     // shallowest frame with at least two unexplored children
                     for (int dd = 0; dd <= d; ++dd) {
@@ -634,15 +735,14 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
                         const int rem = warp_popc(ext, s.wc, lane);
                         if (rem < 2) continue;
                         const int kd = T.kdepth + dd;
-                        const int64_t words = 2 + kd + 4 * (int64_t)s.wc;
-                        int64_t off = -1, slot = -1;
-                        if (lane == 0) off = queue_reserve(P, words, &slot);
-                        off = __shfl_sync(FULL, off, 0);
-                        slot = __shfl_sync(FULL, slot, 0);
-                        if (off < 0) break;
+                        int64_t pos = -1;
+                        if (lane == 0) pos = queue_claim_push(P);
+                        pos = __shfl_sync(FULL, pos, 0);
+                        if (pos < 0) break;
                         // lower half stays here, upper half goes
                         const int keep = rem / 2;
-                        uint32_t *rec = P.arena + off;
+                        uint32_t *rec = P.arena + (int64_t)((unsigned long long)pos % (unsigned long long)P.qcap) *
+                                                      P.slot_words;
                         if (lane == 0) {
                             rec[0] = (uint32_t)root;
                             rec[1] = (uint32_t)kd;
@@ -686,7 +786,7 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
                         __threadfence();
                         __syncwarp();
                         if (lane == 0) {
-                            queue_publish(P, slot, off);
+                            queue_publish(P, pos);
                             atomicAdd(&P.out[OUT_SPLITS], 1ULL);
                         }
                         break;
@@ -735,13 +835,23 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
         }
     pop:
         if (d == 0) break;
+        if (P.mode == BK_MCE) {
+            // put frame d-1's F back in bnd order (the child split it into adjacent | rest)
+            const int a = (int)fr_meta(s, d)[0], len = (int)fr_meta(s, d - 1)[0];
+            if (a > 0 && a < len) merge_F(s, a, len, lane);
+        }
         --d;
         enter = false;
     }
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_bk(BkParams P) {
+__global__ void k_init_seq(unsigned long long *seq, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        seq[i] = (unsigned long long)i;
+}
+
+__global__ void __launch_bounds__(256, 4) k_bk(BkParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
     unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);   // 256 bins
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -751,7 +861,8 @@ __global__ void __launch_bounds__(256) k_bk(BkParams P) {
     uint32_t *ws_smem = smem + 512 + (int64_t)wib * P.smem_words;
     const int64_t gwarp = (int64_t)blockIdx.x * nw_block + wib;
     uint32_t *ws_glob = P.gws + gwarp * P.gws_words;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0};
+    uint32_t *taskbuf = P.taskbuf + gwarp * P.slot_words;
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     Ws s;
     int32_t built = -1;
     int node_tick = 0;
@@ -765,16 +876,14 @@ __global__ void __launch_bounds__(256) k_bk(BkParams P) {
         T.kdepth = 0;
         T.rec = -1;
         int kind = 0;   // 0 none, 1 subproblem, 2 piece, 3 stop
+        int64_t qpos = -1;
         if (lane == 0) {
             if (*(volatile unsigned long long *)&P.ctl[CTL_ABORT] & 3ULL) {
                 kind = 3;
             } else {
-                const int64_t off = queue_pop(P);
-                if (off >= 0) {
+                qpos = queue_claim_pop(P);
+                if (qpos >= 0) {
                     kind = 2;
-                    T.rec = off;
-                    T.root = (int32_t)__ldcg(P.arena + off);
-                    T.kdepth = (int32_t)__ldcg(P.arena + off + 1);
                 } else if (*(volatile unsigned long long *)&P.ctl[CTL_NEXT] < (unsigned long long)P.n_sub) {
                     const unsigned long long i = atomicAdd(&P.ctl[CTL_NEXT], 1ULL);
                     if (i < (unsigned long long)P.n_sub) {
@@ -787,13 +896,33 @@ __global__ void __launch_bounds__(256) k_bk(BkParams P) {
         }
         kind = __shfl_sync(FULL, kind, 0);
         if (kind == 3) break;
+        if (kind == 2) {
+            // copy the record out of the ring and free its slot at once
+            qpos = __shfl_sync(FULL, qpos, 0);
+            const uint32_t *src = P.arena + (int64_t)((unsigned long long)qpos % (unsigned long long)P.qcap) *
+                                                P.slot_words;
+            for (int64_t k = lane; k < P.slot_words; k += 32) taskbuf[k] = __ldcg(src + k);
+            __syncwarp();
+            if (lane == 0) {
+                T.root = (int32_t)taskbuf[0];
+                T.kdepth = (int32_t)taskbuf[1];
+                T.rec = 1;
+                queue_release(P, qpos);
+            }
+        }
         if (kind == 0) {
+            // Waiting is legitimate while other warps still work; only the
+            // launch-wide time bound ends it.
+            const uint64_t now = globaltimer_ns();
             if (!hungry) {
                 hungry = true;
-                idle_since = globaltimer_ns();
+                idle_since = now;
                 if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], 1ULL);
-            } else if (globaltimer_ns() - idle_since > P.timeout_ns) {
+            } else if (now - t_start > P.max_run_ns + P.timeout_ns) {
                 if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 2ULL);
+                acc.idle_ns += now - idle_since;
+                hungry = false;
+                if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
                 break;
             }
             __nanosleep(2000);
@@ -801,14 +930,19 @@ __global__ void __launch_bounds__(256) k_bk(BkParams P) {
         }
         if (hungry) {
             hungry = false;
+            acc.idle_ns += globaltimer_ns() - idle_since;
             if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
         }
+        if (kind == 2) acc.pieces++;
         T.root = __shfl_sync(FULL, T.root, 0);
         T.kdepth = __shfl_sync(FULL, T.kdepth, 0);
         T.rec = __shfl_sync(FULL, T.rec, 0);
-        acc.t_count = acc.t_hash = acc.t_nodes = 0;
-        const bool go_on = run_task(P, s, T, acc, shist, ws_smem, ws_glob, lane, built, node_tick, t_start);
+        acc.t_count = acc.t_hash = acc.t_nodes = acc.t_rep = 0;
+        const uint64_t t0 = globaltimer_ns();
+        const bool go_on = run_task(P, s, T, acc, shist, ws_smem, ws_glob, taskbuf, lane, built, node_tick, t_start);
+        acc.max_busy += globaltimer_ns() - t0;
         if (lane == 0) {
+            if (P.sub_nodes && acc.t_nodes > acc.t_rep) atomicAdd(&P.sub_nodes[T.root], acc.t_nodes - acc.t_rep);
             if (P.pv_count && P.mode == BK_MCE) {
                 atomicAdd(&P.pv_count[T.root], acc.t_count);
                 atomicAdd(&P.pv_hash[T.root], acc.t_hash);
@@ -824,7 +958,19 @@ __global__ void __launch_bounds__(256) k_bk(BkParams P) {
         }
         if (!go_on) break;
     }
-    if (hungry && lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
+    if (hungry) {
+        acc.idle_ns += globaltimer_ns() - idle_since;
+        if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
+    }
+    if (lane == 0) {
+        atomicAdd(&P.out[OUT_BUILD_NS], acc.build_ns);
+        atomicAdd(&P.out[OUT_SEARCH_NS], acc.max_busy - acc.build_ns);
+        atomicAdd(&P.out[OUT_IDLE_NS], acc.idle_ns);
+        atomicAdd(&P.out[OUT_BUILDS], acc.builds);
+        atomicAdd(&P.out[OUT_PIECES], acc.pieces);
+        atomicMax(&P.out[OUT_MAXBUSY_NS], acc.max_busy);
+        atomicAdd(&P.out[OUT_NWARPS], 1ULL);
+    }
     {
         unsigned long long w = acc.wops;
         for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(FULL, w, o);
@@ -841,6 +987,11 @@ __global__ void __launch_bounds__(256) k_bk(BkParams P) {
 }
 
 }  // namespace
+
+mce_status init_queue_seq(unsigned long long *seq, int64_t n, cudaStream_t s) {
+    MCE_LAUNCH(k_init_seq, grid_for(n, 256), 256, 0, s, seq, n);
+    return MCE_OK;
+}
 
 mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s) {
     const size_t smem = (size_t)512 * 4 + (size_t)warps_per_block * p.smem_words * 4;

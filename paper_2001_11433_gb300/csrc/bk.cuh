@@ -9,11 +9,11 @@ namespace mce {
 // Control block of one persistent launch (uint64 words).
 enum CtlWord {
     CTL_NEXT = 0,      // next unclaimed subproblem index
-    CTL_QTAIL = 1,     // queue slots reserved by pushers
-    CTL_QHEAD = 2,     // queue slots claimed by poppers
+    CTL_QTAIL = 1,     // ring tickets taken by pushers
+    CTL_QHEAD = 2,     // ring tickets taken by poppers
     CTL_PENDING = 3,   // subproblems + queued tasks not finished
     CTL_HUNGRY = 4,    // warps waiting for work
-    CTL_ARENA = 5,     // words of the task arena in use
+    CTL_UNUSED = 5,
     CTL_NODES = 6,     // tree nodes, for the budget
     CTL_ABORT = 7,     // 1 = budget, 2 = timeout, 4 = workspace too small, 8 = bad task
     CTL_WORDS = 8
@@ -30,6 +30,13 @@ enum OutWord {
     OUT_FLAGS = 6,     // 1 = list overflow, 2 = histogram overflow
     OUT_SPLITS = 7,
     OUT_WORDOPS = 8,
+    OUT_BUILD_NS = 9,      // summed over warps: time building subproblems
+    OUT_SEARCH_NS = 10,    //                    time searching
+    OUT_IDLE_NS = 11,      //                    time waiting for work
+    OUT_BUILDS = 12,       // subproblem builds
+    OUT_PIECES = 13,       // handed-over pieces run
+    OUT_MAXBUSY_NS = 14,   // largest build + search time of one warp
+    OUT_NWARPS = 15,
     OUT_HIST = 16,
     OUT_WORDS = 16 + MCE_HIST_CAP
 };
@@ -60,11 +67,13 @@ struct BkParams {
     uint32_t *gws;
     int64_t gws_words;
     int32_t smem_words;
-    // task queue
+    // task ring: qcap slots of slot_words words, sequence numbers, and one
+    // private record buffer per warp
     uint32_t *arena;
-    int64_t arena_words;
-    uint32_t *qslot;
+    int64_t slot_words;
+    unsigned long long *qseq;
     int64_t qcap;
+    uint32_t *taskbuf;
     unsigned long long *ctl;
     // outputs
     unsigned long long *out;
@@ -74,6 +83,8 @@ struct BkParams {
     unsigned long long *pv_count, *pv_hash, *pv_nodes;   // per subproblem id
     unsigned long long *g_count, *g_hash;                // batched: per graph
     uint64_t node_budget;
+    unsigned long long *sub_nodes;    // exact nodes per subproblem (with sub_budget)
+    uint64_t sub_budget;
     int32_t split;
     uint64_t timeout_ns;      // bound on any single wait
     uint64_t max_run_ns;      // bound on a warp's time in one launch
@@ -85,9 +96,9 @@ __host__ __device__ inline int64_t bk_ws_words(int64_t w, int64_t c, int32_t mod
     const int64_t wc = (c + 31) / 32;
     const int64_t S = (wc & 1) ? wc : wc + 1;
     const int64_t fr = 4 * wc + 4;                  // cand, finic, ext, conf + meta
-    int64_t words = w                               // gid
+    int64_t words = 2 * w                           // gid, bnd
                     + w * S                         // A rows
-                    + 2 * (w - c)                   // F and its scratch
+                    + 3 * (w - c)                   // F0 (sorted), F and its scratch
                     + (c + 2) * fr                  // frames
                     + (c + 2)                       // K path of the task
                     + 8;
@@ -96,5 +107,6 @@ __host__ __device__ inline int64_t bk_ws_words(int64_t w, int64_t c, int32_t mod
 }
 
 mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s);
+mce_status init_queue_seq(unsigned long long *seq, int64_t n, cudaStream_t s);
 
 }  // namespace mce

@@ -150,16 +150,23 @@ __global__ void k_merge_rows(const int32_t *row_ptr, const int32_t *col, const i
 
 __global__ void k_edge_order_keys(const int32_t *row_ptr2, const int32_t *eu, const int32_t *ev, int32_t rho,
                                   int32_t IB, uint64_t *keys, unsigned long long *req) {
-    unsigned long long r = 0;
+    unsigned long long r = 0, cm = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rho; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t du = row_ptr2[eu[i] + 1] - row_ptr2[eu[i]];
         const int32_t dv = row_ptr2[ev[i] + 1] - row_ptr2[ev[i]];
         const int32_t c = min(du, dv);
         r = max(r, (unsigned long long)bk_ws_words(c, c, BK_IMCE));
+        cm = max(cm, (unsigned long long)c);
         keys[i] = ((uint64_t)((1u << 30) - 1 - (uint32_t)c) << IB) | (uint64_t)i;
     }
-    for (int o = 16; o; o >>= 1) r = max(r, __shfl_xor_sync(FULL, r, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(req, r);
+    for (int o = 16; o; o >>= 1) {
+        r = max(r, __shfl_xor_sync(FULL, r, o));
+        cm = max(cm, __shfl_xor_sync(FULL, cm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(req, r);
+        atomicMax(req + 1, cm);
+    }
 }
 
 __global__ void k_keys_low(const uint64_t *keys, int32_t m, int32_t IB, int32_t *out) {
@@ -714,14 +721,14 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
     MCE_TRY(okeys.alloc((size_t)rho * 8, s));
     MCE_TRY(otmp.alloc((size_t)rho * 8, s));
     MCE_TRY(order.alloc((size_t)rho * 4, s));
-    MCE_TRY(reqb.alloc(8, s));
-    MCE_CUDA(cudaMemsetAsync(reqb.p, 0, 8, s));
+    MCE_TRY(reqb.alloc(16, s));
+    MCE_CUDA(cudaMemsetAsync(reqb.p, 0, 16, s));
     MCE_LAUNCH(k_edge_order_keys, grid_for(rho, 256), 256, 0, s, g2->row_ptr, eu.as<int32_t>(), ev.as<int32_t>(), rho,
                IBr, okeys.as<uint64_t>(), reqb.as<unsigned long long>());
     MCE_TRY(radix_sort_u64(okeys.as<uint64_t>(), otmp.as<uint64_t>(), rho, 30 + IBr, s));
     MCE_LAUNCH(k_keys_low, grid_for(rho, 256), 256, 0, s, okeys.as<uint64_t>(), rho, IBr, order.as<int32_t>());
-    unsigned long long req_max = 0;
-    MCE_CUDA(cudaMemcpyAsync(&req_max, reqb.p, 8, cudaMemcpyDeviceToHost, s));
+    unsigned long long reqc[2] = {0, 0};
+    MCE_CUDA(cudaMemcpyAsync(reqc, reqb.p, 16, cudaMemcpyDeviceToHost, s));
     MCE_CUDA(cudaStreamSynchronize(s));
     MCE_TRY(nout.alloc(OUT_WORDS * 8, s));
     DevBuf nloff, nlvtx;
@@ -751,12 +758,12 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
         P.list_max_cliques = mc;
         P.list_max_words = mw;
         P.split = S->opts.split;
-        DevBuf gws, arena, qslot, ctl;
+        BkBuffers bb;
         const LaunchShape ls = launch_shape(&S->opts);
-        MCE_TRY(run_bk(P, ls, (int64_t)req_max, s, gws, arena, qslot, ctl));
+        MCE_TRY(run_bk(P, ls, (int64_t)reqc[0], (int64_t)reqc[1], s, bb));
         unsigned long long c[CTL_WORDS];
         MCE_CUDA(cudaMemcpyAsync(hn, nout.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
-        MCE_CUDA(cudaMemcpyAsync(c, ctl.p, sizeof(c), cudaMemcpyDeviceToHost, s));
+        MCE_CUDA(cudaMemcpyAsync(c, bb.ctl.p, sizeof(c), cudaMemcpyDeviceToHost, s));
         MCE_CUDA(cudaStreamSynchronize(s));
         if (c[CTL_ABORT] & 2ULL) {
             g_last_error = "imce: a bounded device wait gave up";

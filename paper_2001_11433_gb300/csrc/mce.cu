@@ -21,9 +21,13 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
                               unsigned long long *pv_nodes, int32_t *flag, uint64_t *keys,
                               unsigned long long *req_max, const int32_t *graph_of, unsigned long long *g_count,
                               unsigned long long *g_hash, int64_t *list_off, int32_t *list_vtx,
-                              int64_t list_max_cliques, int64_t list_max_words) {
-    unsigned long long cnt = 0, hsh = 0, nodes = 0, req = 0;
+                              int64_t list_max_cliques, int64_t list_max_words, const uint8_t *in_subset) {
+    unsigned long long cnt = 0, hsh = 0, nodes = 0, req = 0, cmax = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (in_subset && !in_subset[v]) {
+            flag[v] = 0;
+            continue;
+        }
         const int32_t w = row_ptr[v + 1] - row_ptr[v];
         const int32_t c = up_ptr[v + 1] - up_ptr[v];
         int32_t f = 0;
@@ -71,6 +75,7 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
             }
             keys[v] = k;
             req = max(req, (unsigned long long)bk_ws_words(w, c, BK_MCE));
+            cmax = max(cmax, (unsigned long long)c);
         }
         flag[v] = f;
     }
@@ -79,6 +84,7 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
         hsh += __shfl_xor_sync(0xffffffffu, hsh, o);
         nodes += __shfl_xor_sync(0xffffffffu, nodes, o);
         req = max(req, __shfl_xor_sync(0xffffffffu, req, o));
+        cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
     }
     if ((threadIdx.x & 31) == 0) {
         if (cnt) {
@@ -89,7 +95,24 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
         }
         if (nodes) atomicAdd(&out[OUT_NODES], nodes);
         if (req) atomicMax(req_max, req);
+        if (cmax) atomicMax(req_max + 1, cmax);
     }
+}
+
+__global__ void k_subset_mask(const int32_t *subset, int64_t m, int32_t n, uint8_t *mask, int32_t *bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = subset[i];
+        if (v < 0 || v >= n) atomicOr(bad, 1);
+        else mask[v] = 1;
+    }
+}
+
+__global__ void k_count_over(const unsigned long long *nodes, int32_t n, uint64_t budget, unsigned long long *cnt) {
+    unsigned long long c = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        c += nodes[v] > budget;
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
 }
 
 __global__ void k_gather_active(const int32_t *flag_scan, const uint64_t *keys, int32_t n, uint64_t *out) {
@@ -129,23 +152,29 @@ LaunchShape launch_shape(const mce_opts *o) {
     return ls;
 }
 
-mce_status run_bk(BkParams &P, const LaunchShape &ls, int64_t req_max, cudaStream_t s, DevBuf &gws, DevBuf &arena,
-                  DevBuf &qslot, DevBuf &ctl) {
+mce_status run_bk(BkParams &P, const LaunchShape &ls, int64_t req_max, int64_t cmax, cudaStream_t s, BkBuffers &b) {
     const int64_t nwarps = (int64_t)num_sms() * ls.blocks_per_sm * ls.warps_per_block;
     P.gws_words = req_max > ls.smem_words ? req_max : 16;
     P.smem_words = ls.smem_words;
-    MCE_TRY(gws.alloc((size_t)nwarps * P.gws_words * 4, s));
-    P.gws = gws.as<uint32_t>();
-    P.arena_words = (int64_t)1 << 26;
-    P.qcap = (int64_t)1 << 22;
-    MCE_TRY(arena.alloc((size_t)P.arena_words * 4, s));
-    MCE_TRY(qslot.alloc((size_t)P.qcap * 4, s));
-    MCE_CUDA(cudaMemsetAsync(qslot.p, 0, (size_t)P.qcap * 4, s));
-    MCE_TRY(ctl.alloc(CTL_WORDS * sizeof(unsigned long long), s));
-    MCE_CUDA(cudaMemsetAsync(ctl.p, 0, CTL_WORDS * sizeof(unsigned long long), s));
-    P.arena = arena.as<uint32_t>();
-    P.qslot = qslot.as<uint32_t>();
-    P.ctl = ctl.as<unsigned long long>();
+    MCE_TRY(b.gws.alloc((size_t)nwarps * P.gws_words * 4, s));
+    P.gws = b.gws.as<uint32_t>();
+    // one ring slot holds (root, depth, path <= c, cand, finic, ext, conf)
+    const int64_t wcmax = (cmax + 31) / 32;
+    P.slot_words = (2 + cmax + 4 * wcmax + 3) & ~int64_t(3);
+    int64_t cap = ((int64_t)1 << 26) / P.slot_words;
+    if (cap > ((int64_t)1 << 16)) cap = (int64_t)1 << 16;
+    if (cap < 1024) cap = 1024;
+    P.qcap = cap;
+    MCE_TRY(b.arena.alloc((size_t)P.qcap * P.slot_words * 4, s));
+    MCE_TRY(b.qseq.alloc((size_t)P.qcap * 8, s));
+    MCE_TRY(b.taskbuf.alloc((size_t)nwarps * P.slot_words * 4, s));
+    MCE_TRY(init_queue_seq(b.qseq.as<unsigned long long>(), P.qcap, s));
+    MCE_TRY(b.ctl.alloc(CTL_WORDS * sizeof(unsigned long long), s));
+    MCE_CUDA(cudaMemsetAsync(b.ctl.p, 0, CTL_WORDS * sizeof(unsigned long long), s));
+    P.arena = b.arena.as<uint32_t>();
+    P.qseq = b.qseq.as<unsigned long long>();
+    P.taskbuf = b.taskbuf.as<uint32_t>();
+    P.ctl = b.ctl.as<unsigned long long>();
     MCE_LAUNCH(k_set_u64, 1, 1, 0, s, P.ctl + CTL_PENDING, (unsigned long long)P.n_sub);
     if (P.timeout_ns == 0) P.timeout_ns = 60ULL * 1000000000ULL;
     if (P.max_run_ns == 0) P.max_run_ns = 600ULL * 1000000000ULL;
@@ -207,6 +236,8 @@ mce_status read_result(const DevBuf &out, const DevBuf &ctl, cudaStream_t s, mce
     res->list_words = (int64_t)h[OUT_LIST_WORDS];
     res->tasks_split = h[OUT_SPLITS];
     res->word_ops = h[OUT_WORDOPS];
+    for (int i = 0; i < 7; ++i) res->stats[i] = h[OUT_BUILD_NS + i];
+    res->stats[7] = 0;
     res->complete = (c[CTL_ABORT] & 3ULL) ? 0 : 1;
     if (c[CTL_ABORT] & 4ULL) {
         g_last_error = "search workspace smaller than a subproblem";
@@ -267,9 +298,35 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
     MCE_CUDA(cudaMemsetAsync(out.p, 0, OUT_WORDS * 8, s));
     MCE_TRY(flag.alloc((size_t)(n + 1) * 4, s));
     MCE_TRY(keys.alloc((size_t)(n + 1) * 8, s));
-    DevBuf reqb;
-    MCE_TRY(reqb.alloc(8, s));
-    MCE_CUDA(cudaMemsetAsync(reqb.p, 0, 8, s));
+    DevBuf reqb, mask;
+    MCE_TRY(reqb.alloc(16, s));
+    MCE_CUDA(cudaMemsetAsync(reqb.p, 0, 16, s));
+    const uint8_t *maskp = nullptr;
+    DevBuf hsub;
+    const int32_t *subp = o->subset;
+    if (o->subset && o->subset_on_host && o->subset_len > 0) {
+        MCE_TRY(hsub.alloc((size_t)o->subset_len * 4, s));
+        MCE_CUDA(cudaMemcpyAsync(hsub.p, o->subset, (size_t)o->subset_len * 4, cudaMemcpyHostToDevice, s));
+        subp = hsub.as<int32_t>();
+    }
+    if (o->subset) {
+        DevBuf bad;
+        MCE_TRY(bad.alloc(4, s));
+        MCE_TRY(mask.alloc((size_t)n + 16, s));
+        MCE_CUDA(cudaMemsetAsync(mask.p, 0, (size_t)n + 16, s));
+        MCE_CUDA(cudaMemsetAsync(bad.p, 0, 4, s));
+        if (o->subset_len > 0)
+            MCE_LAUNCH(k_subset_mask, grid_for(o->subset_len, 256), 256, 0, s, subp, o->subset_len, n,
+                       mask.as<uint8_t>(), bad.as<int32_t>());
+        int32_t hb = 0;
+        MCE_CUDA(cudaMemcpyAsync(&hb, bad.p, 4, cudaMemcpyDeviceToHost, s));
+        MCE_CUDA(cudaStreamSynchronize(s));
+        if (hb) {
+            g_last_error = "mce_enumerate: subset holds an id outside [0, n)";
+            return MCE_EINVAL;
+        }
+        maskp = mask.as<uint8_t>();
+    }
     if (o->pv_count) {
         MCE_CUDA(cudaMemsetAsync(o->pv_count, 0, (size_t)n * 8, s));
         MCE_CUDA(cudaMemsetAsync(o->pv_hash, 0, (size_t)n * 8, s));
@@ -280,15 +337,16 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
                    costp, out.as<unsigned long long>(), (unsigned long long *)o->pv_count,
                    (unsigned long long *)o->pv_hash, (unsigned long long *)o->pv_nodes, flag.as<int32_t>(),
                    keys.as<uint64_t>(), reqb.as<unsigned long long>(), graph_of, g_count, g_hash, o->list_off,
-                   o->list_vtx, o->list_max_cliques, o->list_max_words);
+                   o->list_vtx, o->list_max_cliques, o->list_max_words, maskp);
     MCE_TRY(exclusive_scan_i32(flag.as<int32_t>(), flag.as<int32_t>(), n, s));
     int32_t n_act = 0;
-    unsigned long long req_max = 0;
+    unsigned long long reqc[2] = {0, 0};
     MCE_CUDA(cudaMemcpyAsync(&n_act, flag.as<int32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
-    MCE_CUDA(cudaMemcpyAsync(&req_max, reqb.p, 8, cudaMemcpyDeviceToHost, s));
+    MCE_CUDA(cudaMemcpyAsync(reqc, reqb.p, 16, cudaMemcpyDeviceToHost, s));
     MCE_CUDA(cudaStreamSynchronize(s));
     res->subproblems = n_act;
-    DevBuf gws, arena, qslot, ctl;
+    BkBuffers bb;
+    DevBuf subn;
     if (n_act > 0) {
         MCE_TRY(tmp.alloc((size_t)n_act * 8 * 2, s));
         MCE_TRY(order.alloc((size_t)n_act * 4, s));
@@ -320,6 +378,12 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         P.pv_hash = (unsigned long long *)o->pv_hash;
         P.pv_nodes = (unsigned long long *)o->pv_nodes;
         P.node_budget = o->node_budget;
+        if (o->subproblem_budget) {
+            MCE_TRY(subn.alloc((size_t)n * 8, s));
+            MCE_CUDA(cudaMemsetAsync(subn.p, 0, (size_t)n * 8, s));
+            P.sub_nodes = subn.as<unsigned long long>();
+            P.sub_budget = o->subproblem_budget;
+        }
         P.split = o->split;
         P.max_run_ns = (uint64_t)o->time_limit_ms * 1000000ULL;
         const LaunchShape ls = launch_shape(o);
@@ -328,7 +392,7 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         MCE_CUDA(cudaEventCreate(&k1));
         EvPair kg{k0, k1};
         MCE_CUDA(cudaEventRecord(k0, s));
-        MCE_TRY(run_bk(P, ls, (int64_t)req_max, s, gws, arena, qslot, ctl));
+        MCE_TRY(run_bk(P, ls, (int64_t)reqc[0], (int64_t)reqc[1], s, bb));
         MCE_CUDA(cudaEventRecord(k1, s));
         MCE_CUDA(cudaEventSynchronize(k1));
         float ks = 0;
@@ -336,7 +400,18 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         res->ms_search = ks;
     }
     MCE_CUDA(cudaEventRecord(e2, s));
-    mce_status st = read_result(out, ctl, s, res);
+    if (subn.p) {
+        DevBuf cnt;
+        MCE_TRY(cnt.alloc(8, s));
+        MCE_CUDA(cudaMemsetAsync(cnt.p, 0, 8, s));
+        MCE_LAUNCH(k_count_over, grid_for(n, 256), 256, 0, s, subn.as<unsigned long long>(), n, o->subproblem_budget,
+                   cnt.as<unsigned long long>());
+        unsigned long long hc = 0;
+        MCE_CUDA(cudaMemcpyAsync(&hc, cnt.p, 8, cudaMemcpyDeviceToHost, s));
+        MCE_CUDA(cudaStreamSynchronize(s));
+        res->incomplete = (int64_t)hc;
+    }
+    mce_status st = read_result(out, bb.ctl, s, res);
     float a = 0, b = 0;
     cudaEventElapsedTime(&a, e0, e1);
     cudaEventElapsedTime(&b, e1, e2);

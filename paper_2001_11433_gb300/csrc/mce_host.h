@@ -12,8 +12,10 @@ struct LaunchShape {
 };
 
 LaunchShape launch_shape(const mce_opts *o);
-mce_status run_bk(BkParams &P, const LaunchShape &ls, int64_t req_max, cudaStream_t s, DevBuf &gws, DevBuf &arena,
-                  DevBuf &qslot, DevBuf &ctl);
+struct BkBuffers {
+    DevBuf gws, arena, qseq, taskbuf, ctl;
+};
+mce_status run_bk(BkParams &P, const LaunchShape &ls, int64_t req_max, int64_t cmax, cudaStream_t s, BkBuffers &b);
 mce_status compute_rank(const mce_graph *g, const mce_opts *o, cudaStream_t s, int32_t *rank);
 mce_status read_result(const DevBuf &out, const DevBuf &ctl, cudaStream_t s, mce_result *res);
 mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, const int32_t *graph_of,

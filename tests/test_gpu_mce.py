@@ -239,3 +239,30 @@ def test_list_overflow_keeps_summary(gpu_lib):
     r = mce.enumerate_cliques(g, list_buf=(off, vtx), allow=(mce.MCE_EOVERFLOW,))
     assert r.status == mce.MCE_EOVERFLOW
     assert_same_summary(r, o)
+
+
+def test_subset_and_subproblem_budget(gpu_lib):
+    """A subproblem is abandoned iff its search tree exceeds the budget; the
+    completed ones are exact, and a subset run reproduces the oracle's
+    restricted decomposition."""
+    mce = gpu_lib
+    n, u, v = rmat(12, seed=11)
+    og = O.Graph(n, u, v)
+    rk = O.rank(og, "degen")
+    o = O.parmce(og, rk, per_vertex=True, threads=4)
+    nodes = o.per_vertex["nodes"]
+    budget = int(np.percentile(nodes[nodes > 1], 95))
+    g = gpu_graph(mce, n, u, v)
+    pv = per_vertex_bufs(n)
+    r = mce.enumerate_cliques(g, per_vertex=pv, subproblem_budget=budget)
+    ok = nodes <= budget
+    assert r.incomplete == int((~ok).sum()) > 0
+    assert np.array_equal(u64(pv[2])[ok], nodes[ok])
+    assert np.array_equal(u64(pv[0])[ok], o.per_vertex["count"][ok])
+    assert np.array_equal(u64(pv[1])[ok], o.per_vertex["hash"][ok])
+    assert (u64(pv[2])[~ok] > budget).all()
+    sub = np.nonzero(ok)[0].astype(np.int32)
+    r2 = mce.enumerate_cliques(g, subset=_t(sub))
+    o2 = O.parmce(og, rk, subset=sub, threads=4)
+    assert_same_summary(r2, o2)
+    assert r2.tree_nodes == o2.nodes and r2.incomplete == 0
