@@ -262,6 +262,33 @@ mce_status imce_cliques(const imce_state *s, int64_t *list_off, int32_t *list_vt
                         int64_t max_cliques, int64_t max_words, int64_t *n_cliques, int64_t *n_words);
 void imce_close(imce_state *s);
 
+/* ---------------------------------------------------------------- no-allocation entry point */
+
+/* Size of the fixed device scratch array used by mce_enumerate_noalloc. */
+#define MCE_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* Static maximal clique enumeration that allocates no memory.  The paper has
+ * no counterpart; this exists for callers that cannot allocate device memory
+ * when they enumerate (an allocator that owns all device memory, a service
+ * that must not grow after start-up).
+ *
+ * row_ptr int32[n+1] and col int32[nnz]: a simple undirected graph as CSR
+ * on the device, rows sorted (e.g. from mce_graph_csr); rank int32[n]: a
+ * permutation of [0, n) on the device (e.g. from mce_rank).  Subproblems run
+ * in vertex order; the result (count, hash, histogram, tree nodes) equals
+ * mce_enumerate with the same rank and seed.  Clique lists, per-subproblem
+ * outputs and budgets are not offered here.
+ *
+ * All intermediate data lives in one library-owned device array of
+ * MCE_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * exit.  Graphs whose working data exceeds it (or with more than 4194303
+ * vertices) are rejected with MCE_EINVAL and a message in mce_last_error().
+ * The first call on a device looks up the array's address (with that device
+ * current); make it before any stream capture.  Calls share the array: calls
+ * that overlap on the GPU race and must be serialised by the caller. */
+mce_status mce_enumerate_noalloc(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,
+                                 const int32_t *rank, uint64_t hash_seed, void *stream, mce_result *res);
+
 #ifdef __cplusplus
 }
 #endif

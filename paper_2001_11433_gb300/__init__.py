@@ -127,6 +127,7 @@ SIGNATURES = {
     "imce_graph": ([_vp], _vp),
     "imce_cliques": ([_vp, _vp, _vp, _i64, _i64, _P(_i64), _P(_i64)], _i32),
     "imce_close": ([_vp], None),
+    "mce_enumerate_noalloc": ([_vp, _vp, _i32, _i64, _vp, _u64, _vp, _P(ResultC)], _i32),
 }
 
 
@@ -299,6 +300,19 @@ def enumerate_cliques(g: Graph, allow=(MCE_OK,), **kw) -> Result:
     st = lib.mce_enumerate(g._h, ctypes.byref(o), ctypes.byref(r))
     if st not in allow:
         _check(st, "mce_enumerate")
+    return _result(r, st)
+
+
+def enumerate_noalloc(g: Graph, rank_dev, seed: int = 0, stream=None) -> Result:
+    """mce_enumerate_noalloc on the CSR held by `g` with a device rank."""
+    lib = load()
+    n, nnz, rp, cl = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib.mce_graph_csr(g._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(cl)),
+           "mce_graph_csr")
+    r = ResultC()
+    st = lib.mce_enumerate_noalloc(rp, cl, n.value, nnz.value, _ptr(rank_dev), seed, _stream_ptr(stream),
+                                   ctypes.byref(r))
+    _check(st, "mce_enumerate_noalloc")
     return _result(r, st)
 
 
