@@ -96,9 +96,13 @@ typedef struct {
     uint64_t *pv_hash;
     uint64_t *pv_nodes;
     int32_t split;                /* 1 = split heavy subtrees across warps (default) */
+    uint32_t split_nodes;         /* with split: a task hands over a piece every this many nodes even
+                                     when no warp waits (0 = 2048); pieces also go to waiting warps */
     int32_t order_by_model;       /* 1 = schedule subproblems by the model's prediction */
     int32_t warps_per_block;      /* 0 = automatic */
     int32_t blocks_per_sm;        /* 0 = automatic */
+    int32_t shared_words;         /* per-warp shared-memory workspace words (0 = none, the default:
+                                     the global workspaces then get the whole L1) */
     uint32_t time_limit_ms;       /* stop the search after this long (MCE_ETIMEOUT); 0 = 600 s */
     /* Optional restriction to the subproblems of some vertices (device
      * int32[subset_len], distinct ids); NULL = every vertex. */
@@ -135,7 +139,8 @@ typedef struct {
     uint64_t stats[8];            /* search kernel, summed over warps: [0] ns building subproblems,
                                      [1] ns searching, [2] ns waiting for work, [3] builds,
                                      [4] handed-over pieces run, [5] largest busy ns of one
-                                     warp, [6] warps, [7] unused */
+                                     warp, [6] warps, [7] ns from the last subproblem claim to
+                                     the end of the launch */
 } mce_result;
 
 /* ---------------------------------------------------------------- misc */

@@ -48,9 +48,11 @@ class Opts(ctypes.Structure):
         ("pv_hash", ctypes.c_void_p),
         ("pv_nodes", ctypes.c_void_p),
         ("split", ctypes.c_int32),
+        ("split_nodes", ctypes.c_uint32),
         ("order_by_model", ctypes.c_int32),
         ("warps_per_block", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32),
+        ("shared_words", ctypes.c_int32),
         ("time_limit_ms", ctypes.c_uint32),
         ("subset", ctypes.c_void_p),
         ("subset_len", ctypes.c_int64),
@@ -265,7 +267,7 @@ class Graph:
 
 def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, stream=None, list_buf=None,
               per_vertex=None, split=True, order_by_model=False, warps_per_block=0, blocks_per_sm=0,
-              time_limit_ms=0, subset=None, subproblem_budget=0) -> Opts:
+              time_limit_ms=0, subset=None, subproblem_budget=0, shared_words=0, split_nodes=0) -> Opts:
     o = Opts()
     load().mce_opts_init(ctypes.byref(o))
     o.rank_kind = RANKS[rank] if isinstance(rank, str) else int(rank)
@@ -281,9 +283,11 @@ def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, s
     if per_vertex is not None:
         o.pv_count, o.pv_hash, o.pv_nodes = (_ptr(t) for t in per_vertex)
     o.split = int(split)
+    o.split_nodes = split_nodes
     o.order_by_model = int(order_by_model)
     o.warps_per_block = warps_per_block
     o.blocks_per_sm = blocks_per_sm
+    o.shared_words = shared_words
     o.time_limit_ms = time_limit_ms
     if subset is not None:
         o.subset, o.subset_len = _ptr(subset), int(subset.numel() if hasattr(subset, "numel") else len(subset))

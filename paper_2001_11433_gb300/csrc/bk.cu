@@ -93,6 +93,33 @@ __device__ __forceinline__ void ws_layout(Ws &s, uint32_t *base, int32_t w, int3
     s.X = (mode == BK_IMCE) ? p : nullptr;
 }
 
+// MCE layout split in a read-only part (possibly shared through the build
+// cache) and the warp's private search state.
+__device__ __forceinline__ void ws_layout_split(Ws &s, uint32_t *shared, uint32_t *priv, int32_t w, int32_t c) {
+    s.w = w;
+    s.c = c;
+    s.wc = (c + 31) >> 5;
+    s.S = (s.wc & 1) ? s.wc : s.wc + 1;
+    s.frw = 4 * s.wc + 4;
+    uint32_t *p = shared + 32;
+    s.gid = reinterpret_cast<int32_t *>(p);
+    p += w;
+    s.bnd = reinterpret_cast<int32_t *>(p);
+    p += w;
+    s.A = p;
+    p += (int64_t)w * s.S;
+    s.F0 = reinterpret_cast<int32_t *>(p);
+    p = priv;
+    s.F = reinterpret_cast<int32_t *>(p);
+    p += (w - c);
+    s.Fs = reinterpret_cast<int32_t *>(p);
+    p += (w - c);
+    s.fr = p;
+    p += (int64_t)(c + 2) * s.frw;
+    s.kpath = reinterpret_cast<int32_t *>(p);
+    s.X = nullptr;
+}
+
 // warp: true if any of the n words is non-zero
 __device__ __forceinline__ bool warp_any(const uint32_t *a, int n, int lane) {
     bool nz = false;
@@ -395,6 +422,7 @@ struct Acc {
     unsigned long long count, hash, nodes;   // per warp, whole launch
     unsigned long long t_count, t_hash, t_nodes;   // per task
     unsigned long long t_rep;                      // t_nodes already credited to sub_nodes
+    unsigned long long t_split;                    // t_nodes at the last hand-over
 };
 
 __device__ void emit(const BkParams &P, const Ws &s, int32_t root, int32_t k0, int d, uint64_t hsum, Acc &acc,
@@ -515,6 +543,357 @@ struct Task {
     int64_t rec;         // arena offset of a handed-over frame, -1 for a whole subproblem
 };
 
+// Budget, abort and splitting checks, made every 64 nodes with the current
+// frame written back to memory.  Returns 0 = go on, 1 = stop the launch,
+// 2 = drop this task (its graph or subproblem is over budget).
+__device__ int periodic(const BkParams &P, Ws &s, const Task &T, Acc &acc, int lane, int d, int32_t root,
+                        uint64_t t_start) {
+    unsigned long long ab = 0, hungry = 0;
+    if (lane == 0) {
+        if (globaltimer_ns() - t_start > P.max_run_ns) atomicOr(&P.ctl[CTL_ABORT], 2ULL);
+        ab = *(volatile unsigned long long *)&P.ctl[CTL_ABORT];
+        if (P.node_budget) {
+            const unsigned long long tot = atomicAdd(&P.ctl[CTL_NODES], 64ULL) + 64ULL;
+            if (tot > P.node_budget) {
+                atomicOr(&P.ctl[CTL_ABORT], 1ULL);
+                ab |= 1ULL;
+            }
+        }
+        if (P.sub_nodes) {
+            const unsigned long long delta = acc.t_nodes - acc.t_rep;
+            acc.t_rep = acc.t_nodes;
+            const unsigned long long tot = atomicAdd(&P.sub_nodes[root], delta) + delta;
+            if (tot > P.sub_budget) ab |= 16ULL;
+        }
+        if (P.graph_nodes) {
+            const int32_t gg = P.graph_of[P.mode == BK_MCE ? root : P.eu[root]];
+            const unsigned long long tot = atomicAdd(&P.graph_nodes[gg], 64ULL) + 64ULL;
+            if (P.graph_budget && tot > P.graph_budget) ab |= 16ULL;
+        }
+        if (P.split) {
+            hungry = *(volatile unsigned long long *)&P.ctl[CTL_HUNGRY];
+            const unsigned long long qh = *(volatile unsigned long long *)&P.ctl[CTL_QHEAD];
+            const unsigned long long qt = *(volatile unsigned long long *)&P.ctl[CTL_QTAIL];
+            const unsigned long long qlen = qt > qh ? qt - qh : 0ULL;
+            if (qlen >= hungry) hungry = 0;
+            // a long-running task spreads its subtree before anybody waits
+            if (!hungry && P.split_nodes && acc.t_nodes - acc.t_split >= P.split_nodes &&
+                qlen < (unsigned long long)P.qcap / 2) hungry = 1;
+        }
+    }
+    ab = __shfl_sync(FULL, ab, 0);
+    hungry = __shfl_sync(FULL, hungry, 0);
+    if (ab & 3ULL) return 1;
+    if (ab & 16ULL) return 2;
+    if (!hungry) return 0;
+    acc.t_split = acc.t_nodes;
+    // shallowest frames with at least two unexplored children; up to four
+    // hand-overs per check when many warps wait
+    int budget = hungry > 4 ? 4 : (int)hungry;
+    for (int dd = 0; dd <= d && budget > 0; ++dd) {
+        const uint32_t *ext = fr_ext(s, dd);
+        const int rem = warp_popc(ext, s.wc, lane);
+        if (rem < 2) continue;
+        const int kd = T.kdepth + dd;
+        int64_t pos = -1;
+        if (lane == 0) pos = queue_claim_push(P);
+        pos = __shfl_sync(FULL, pos, 0);
+        if (pos < 0) break;
+        // lower half stays here, upper half goes
+        const int keep = rem / 2;
+        uint32_t *rec = P.arena + (int64_t)((unsigned long long)pos % (unsigned long long)P.qcap) * P.slot_words;
+        if (lane == 0) {
+            rec[0] = (uint32_t)root;
+            rec[1] = (uint32_t)kd;
+        }
+        for (int j = lane; j < kd; j += 32)
+            rec[2 + j] = (uint32_t)(j < T.kdepth ? s.kpath[j] : (int32_t)fr_meta(s, j - T.kdepth + 1)[1]);
+        uint32_t *rb = rec + 2 + kd;
+        uint32_t *cand = fr_cand(s, dd), *finic = fr_finic(s, dd), *ext2 = fr_ext(s, dd);
+        const uint32_t *conf = fr_conf(s, dd);
+        int seen = 0;
+        for (int k0w = 0; k0w < s.wc; k0w += 32) {
+            const int k = k0w + lane;
+            const uint32_t e = k < s.wc ? ext2[k] : 0u;
+            const int pc = __popc(e);
+            int incl = pc;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int before = seen + incl - pc;
+            uint32_t lo = 0u;
+            if (k < s.wc) {
+                if (before + pc <= keep) lo = e;
+                else if (before < keep) {
+                    uint32_t x = e;
+                    for (int t = 0; t < keep - before; ++t) {
+                        const uint32_t bit = x & (0u - x);
+                        lo |= bit;
+                        x ^= bit;
+                    }
+                }
+                rb[k] = cand[k] & ~lo;               // cand \ ext_lo
+                rb[s.wc + k] = finic[k] | lo;        // fini ∪ ext_lo
+                rb[2 * s.wc + k] = e & ~lo;          // ext_hi
+                rb[3 * s.wc + k] = conf[k];
+                ext2[k] = lo;
+            }
+            seen += __shfl_sync(FULL, incl, 31);
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+            queue_publish(P, pos);
+            atomicAdd(&P.out[OUT_SPLITS], 1ULL);
+        }
+        --budget;
+        --dd;   // the same frame may still hold two or more children
+    }
+    __syncwarp();
+    return 0;
+}
+
+// word k of a set lives in register k / 32 of lane k % 32
+template <int NR>
+__device__ __forceinline__ uint32_t bcast(const uint32_t (&r)[NR], int k) {
+    return __shfl_sync(FULL, (NR == 1 || k < 32) ? r[0] : r[NR - 1], k & 31);
+}
+
+template <int NR>
+__device__ __forceinline__ void frame_store(const Ws &s, int d, int lane, const uint32_t (&rc)[NR],
+                                            const uint32_t (&rf)[NR], const uint32_t (&re)[NR],
+                                            const uint32_t (&rx)[NR]) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int k = lane + 32 * r;
+        if (k < s.wc) {
+            fr_cand(s, d)[k] = rc[r];
+            fr_finic(s, d)[k] = rf[r];
+            fr_ext(s, d)[k] = re[r];
+            fr_conf(s, d)[k] = rx[r];
+        }
+    }
+}
+
+template <int NR>
+__device__ __forceinline__ void frame_load(const Ws &s, int d, int lane, uint32_t (&rc)[NR], uint32_t (&rf)[NR],
+                                           uint32_t (&re)[NR], uint32_t (&rx)[NR]) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int k = lane + 32 * r;
+        const bool in = k < s.wc;
+        rc[r] = in ? fr_cand(s, d)[k] : 0u;
+        rf[r] = in ? fr_finic(s, d)[k] : 0u;
+        re[r] = in ? fr_ext(s, d)[k] : 0u;
+        rx[r] = in ? fr_conf(s, d)[k] : 0u;
+    }
+}
+
+// The search proper (Algorithm 1 on an explicit stack).  The words of the
+// current frame (cand, finic, ext, conf) stay in registers, one word per
+// lane per register; candidate words reach other lanes by warp shuffles.
+// Frames are written to memory only when a child is pushed, and read back
+// when it is popped.  Returns 0 = done, 1 = stop the launch, 2 = dropped.
+template <int NR>
+__device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigned long long *shist, int lane,
+                      int &node_tick, uint64_t t_start, int32_t root, int k0, bool enter) {
+    const int wc = s.wc;
+    uint32_t rc[NR], rf[NR], re[NR], rx[NR];
+    int d = 0;
+    frame_load<NR>(s, 0, lane, rc, rf, re, rx);
+    uint32_t flen = fr_meta(s, 0)[0];
+    uint64_t hsum = meta_hsum(fr_meta(s, 0));
+    for (;;) {
+        if (enter) {
+            acc.nodes++;
+            acc.t_nodes++;
+            if (P.mode == BK_IMCE) {
+                // Algorithm 7: a candidate joined to K by an earlier new edge cannot extend K
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t x = rc[r] & rx[r];
+                    rf[r] |= x;
+                    rc[r] &= ~x;
+                }
+            }
+            bool anyc = false, anyf = false;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                anyc |= rc[r] != 0u;
+                anyf |= rf[r] != 0u;
+            }
+            if (!__any_sync(FULL, anyc)) {
+                if (!__any_sync(FULL, anyf) && flen == 0u) emit(P, s, root, k0, d, hsum, acc, shist, lane);
+                goto pop;
+            }
+            // ---- pivot: argmax over cand ∪ finic ∪ F of |cand ∩ A[u]|, ties to the smallest id
+            {
+                uint32_t best_cnt = 0;
+                int32_t best_gid = 0x7fffffff, best_loc = -1;
+                uint32_t cf[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) cf[r] = rc[r] | rf[r];
+                for (int k = 0; k < wc; ++k) {
+                    const uint32_t mword = bcast<NR>(cf, k);
+                    if (mword == 0u) continue;
+                    const bool mine = (mword >> lane) & 1u;
+                    const uint32_t *row = s.A + (int64_t)((k << 5) + lane) * s.S;
+                    uint32_t cnt = 0;
+                    for (int t = 0; t < wc; ++t) {
+                        const uint32_t cw = bcast<NR>(rc, t);
+                        if (mine) cnt += __popc(cw & row[t]);
+                    }
+                    if (mine) {
+                        acc.wops += (unsigned long long)wc;
+                        const int u = (k << 5) + lane;
+                        const int32_t g = s.gid[u];
+                        if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
+                            best_cnt = cnt;
+                            best_gid = g;
+                            best_loc = u;
+                        }
+                    }
+                }
+                // F is ordered by bnd = popc(A[u]) >= |cand ∩ A[u]|; once the bound
+                // of the next entries drops below the best count none of them can
+                // win (a tie needs count == best), so the scan stops there.
+                if (flen) {
+                    uint32_t thr = __reduce_max_sync(FULL, best_loc >= 0 ? best_cnt + 1u : 0u);
+                    for (int b0 = 0; b0 < (int)flen; b0 += 32) {
+                        const int i = b0 + lane;
+                        int u = 0;
+                        bool take = false;
+                        if (i < (int)flen) {
+                            u = s.F[i];
+                            take = (uint32_t)s.bnd[u] + 1u >= thr;
+                        }
+                        if (__any_sync(FULL, take)) {
+                            const uint32_t *row = s.A + (int64_t)u * s.S;
+                            uint32_t cnt = 0;
+                            for (int t = 0; t < wc; ++t) {
+                                const uint32_t cw = bcast<NR>(rc, t);
+                                if (take) cnt += __popc(cw & row[t]);
+                            }
+                            if (take) {
+                                acc.wops += (unsigned long long)wc;
+                                const int32_t g = s.gid[u];
+                                if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
+                                    best_cnt = cnt;
+                                    best_gid = g;
+                                    best_loc = u;
+                                }
+                            }
+                        }
+                        thr = __reduce_max_sync(FULL, best_loc >= 0 ? best_cnt + 1u : 0u);
+                        if (b0 + 32 < (int)flen && (uint32_t)s.bnd[s.F[b0 + 32]] + 1u < thr) break;
+                    }
+                }
+                // warp argmax (lanes without a candidate hold best_loc = -1)
+                const uint32_t key_cnt = best_loc >= 0 ? best_cnt + 1u : 0u;
+                const uint32_t mx = __reduce_max_sync(FULL, key_cnt);
+                const uint32_t gkey = (key_cnt == mx) ? (uint32_t)best_gid : 0xffffffffu;
+                const uint32_t mg = __reduce_min_sync(FULL, gkey);
+                const uint32_t who = __ballot_sync(FULL, key_cnt == mx && (uint32_t)best_gid == mg);
+                const int p = __shfl_sync(FULL, best_loc, __ffs(who) - 1);
+                const uint32_t *prow = s.A + (int64_t)p * s.S;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const int k = lane + 32 * r;
+                    re[r] = k < wc ? (rc[r] & ~prow[k]) : 0u;
+                }
+            }
+            enter = false;
+            if (++node_tick >= 64) {
+                node_tick = 0;
+                frame_store<NR>(s, d, lane, rc, rf, re, rx);
+                __syncwarp();
+                const int act = periodic(P, s, T, acc, lane, d, root, t_start);
+                if (act) return act;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {   // a hand-over may have shrunk this frame's ext
+                    const int k = lane + 32 * r;
+                    re[r] = k < wc ? fr_ext(s, d)[k] : 0u;
+                }
+            }
+        }
+        // ---- next child of frame d
+        {
+            int q = -1;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (q >= 0) break;
+                const uint32_t b = __ballot_sync(FULL, re[r] != 0u);
+                if (b) {
+                    const int src = __ffs(b) - 1;
+                    const uint32_t xs = __shfl_sync(FULL, re[r], src);
+                    q = ((src + 32 * r) << 5) + (__ffs(xs) - 1);
+                }
+            }
+            if (q < 0) goto pop;
+            const int qw = q >> 5;
+            const uint32_t qb = 1u << (q & 31);
+            const uint32_t *qrow = s.A + (int64_t)q * s.S;
+            uint32_t nc[NR], nf[NR], nx[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int k = lane + 32 * r;
+                const uint32_t a = k < wc ? qrow[k] : 0u;
+                nc[r] = rc[r] & a;
+                nf[r] = rf[r] & a;
+                nx[r] = rx[r];
+                if (P.mode == BK_IMCE && k < wc) nx[r] |= s.X[(int64_t)q * s.S + k];
+                if (k == qw) {
+                    re[r] &= ~qb;
+                    rc[r] &= ~qb;
+                    rf[r] |= qb;
+                }
+            }
+            int nfl = 0;
+            if (flen) {
+                nfl = partition_F(s, (int)flen, lane, [&](int32_t x) {
+                    return (s.A[(int64_t)x * s.S + qw] & qb) != 0u;
+                });
+            }
+            // parent frame to memory (its meta is unchanged), child meta
+            frame_store<NR>(s, d, lane, rc, rf, re, rx);
+            const uint64_t nh = hsum + vertex_hash(s.gid[q], P.seed);
+            if (lane == 0) {
+                acc.wops += 2ull * (unsigned long long)wc + (unsigned long long)flen;
+                uint32_t *nm = fr_meta(s, d + 1);
+                nm[0] = (uint32_t)nfl;
+                nm[1] = (uint32_t)q;
+                meta_set_hsum(nm, nh);
+            }
+            __syncwarp();
+            ++d;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                rc[r] = nc[r];
+                rf[r] = nf[r];
+                rx[r] = nx[r];
+                re[r] = 0u;
+            }
+            flen = (uint32_t)nfl;
+            hsum = nh;
+            enter = true;
+            continue;
+        }
+    pop:
+        if (d == 0) return 0;
+        if (P.mode == BK_MCE) {
+            // put frame d-1's F back in bnd order (the child split it into adjacent | rest)
+            const int a = (int)flen, len = (int)fr_meta(s, d - 1)[0];
+            if (a > 0 && a < len) merge_F(s, a, len, lane);
+        }
+        --d;
+        frame_load<NR>(s, d, lane, rc, rf, re, rx);
+        flen = fr_meta(s, d)[0];
+        hsum = meta_hsum(fr_meta(s, d));
+        enter = false;
+    }
+}
+
 // Run one task to completion.  Returns false when the launch must stop.
 __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigned long long *shist,
                          uint32_t *ws_smem, uint32_t *ws_glob, const uint32_t *taskbuf, int lane,
@@ -537,18 +916,58 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
         if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 4ULL);
         return false;
     }
-    ws_layout(s, base, w, c, P.mode);   // same pointers as the last build of `root`; f and W kept
     const int k0 = (P.mode == BK_MCE ? 1 : 2) + T.kdepth;
     const uint64_t tb = globaltimer_ns();
-    if (built != root || P.mode == BK_IMCE) {
-        if (P.mode == BK_MCE) {
-            build_mce(P, s, root, lane);
-        } else {
-            build_imce(P, s, root, lane);
+    bool ready = false;
+    if (P.mode == BK_MCE && P.cache) {
+        const int64_t sw = bk_shared_words(w, c);
+        long long off = -1;
+        if (lane == 0) {
+            if (T.rec < 0) {
+                const unsigned long long o = atomicAdd(&P.ctl[CTL_CACHE_TOP], (unsigned long long)sw);
+                off = ((int64_t)o + sw <= P.cache_words) ? (long long)o : -1;
+            } else {
+                off = __ldcg(P.cache_off + root);
+            }
         }
-        built = root;
-        acc.builds++;
-        acc.build_ns += globaltimer_ns() - tb;
+        off = __shfl_sync(FULL, off, 0);
+        if (off >= 0) {
+            uint32_t *sh = P.cache + off;
+            ws_layout_split(s, sh, base, w, c);
+            if (T.rec < 0) {
+                // open the subproblem: build it into the cache and publish it
+                build_mce(P, s, root, lane);
+                if (lane == 0) {
+                    sh[0] = (uint32_t)s.W;
+                    sh[1] = (uint32_t)s.f;
+                }
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) atomicExch(reinterpret_cast<unsigned long long *>(P.cache_off + root),
+                                          (unsigned long long)off);
+                acc.builds++;
+                acc.build_ns += globaltimer_ns() - tb;
+            } else {
+                s.W = (int32_t)__ldcg(sh);
+                s.f = (int32_t)__ldcg(sh + 1);
+            }
+            built = -1;   // the private region no longer holds a private build
+            ready = true;
+        }
+    }
+    if (!ready) {
+        if (P.mode == BK_MCE) ws_layout_split(s, base, base + bk_shared_words(w, c), w, c);
+        else ws_layout(s, base, w, c, P.mode);
+        if (built != root || P.mode == BK_IMCE) {   // same pointers as the last build of `root`: f and W kept
+            if (P.mode == BK_MCE) {
+                build_mce(P, s, root, lane);
+            } else {
+                build_imce(P, s, root, lane);
+            }
+            built = root;
+            acc.builds++;
+            acc.build_ns += globaltimer_ns() - tb;
+        }
     }
     // ---- frame 0
     uint64_t hs0 = P.mode == BK_MCE ? vertex_hash(root, P.seed)
@@ -609,241 +1028,10 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
     meta_set_hsum(m0, hs0);
     __syncwarp();
 
-    int d = 0;
-    for (;;) {
-        if (enter) {
-            acc.nodes++;
-            acc.t_nodes++;
-            uint32_t *cand = fr_cand(s, d), *finic = fr_finic(s, d);
-            uint32_t *meta = fr_meta(s, d);
-            if (P.mode == BK_IMCE) {
-                // Algorithm 7: a candidate joined to K by an earlier new edge cannot extend K
-                const uint32_t *conf = fr_conf(s, d);
-                for (int k = lane; k < s.wc; k += 32) {
-                    const uint32_t x = cand[k] & conf[k];
-                    finic[k] |= x;
-                    cand[k] &= ~x;
-                }
-                __syncwarp();
-            }
-            if (!warp_any(cand, s.wc, lane)) {
-                const bool fin = warp_any(finic, s.wc, lane) || meta[0] != 0u;
-                if (!fin) emit(P, s, root, k0, d, meta_hsum(meta), acc, shist, lane);
-                goto pop;
-            }
-            // ---- pivot: argmax over cand ∪ finic ∪ F of |cand ∩ A[u]|, ties to the smallest id
-            {
-                uint32_t best_cnt = 0;
-                int32_t best_gid = 0x7fffffff, best_loc = -1;
-                for (int k = 0; k < s.wc; ++k) {
-                    const uint32_t mword = cand[k] | finic[k];
-                    if ((mword >> lane) & 1u) {
-                        acc.wops += (unsigned long long)s.wc;
-                        const int u = (k << 5) + lane;
-                        const uint32_t *row = s.A + (int64_t)u * s.S;
-                        uint32_t cnt = 0;
-                        for (int t = 0; t < s.wc; ++t) cnt += __popc(cand[t] & row[t]);
-                        const int32_t g = s.gid[u];
-                        if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
-                            best_cnt = cnt;
-                            best_gid = g;
-                            best_loc = u;
-                        }
-                    }
-                }
-                // F is ordered by bnd = popc(A[u]) >= |cand ∩ A[u]|; once the bound
-                // of the next entries drops below the best count none of them can
-                // win (a tie needs count == best), so the scan stops there.
-                const int flen = (int)meta[0];
-                if (flen) {
-                    uint32_t thr = __reduce_max_sync(FULL, best_loc >= 0 ? best_cnt + 1u : 0u);
-                    for (int b0 = 0; b0 < flen; b0 += 32) {
-                        const int i = b0 + lane;
-                        if (i < flen) {
-                            const int u = s.F[i];
-                            if ((uint32_t)s.bnd[u] + 1u >= thr) {
-                                const uint32_t *row = s.A + (int64_t)u * s.S;
-                                uint32_t cnt = 0;
-                                for (int t = 0; t < s.wc; ++t) cnt += __popc(cand[t] & row[t]);
-                                acc.wops += (unsigned long long)s.wc;
-                                const int32_t g = s.gid[u];
-                                if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
-                                    best_cnt = cnt;
-                                    best_gid = g;
-                                    best_loc = u;
-                                }
-                            }
-                        }
-                        thr = __reduce_max_sync(FULL, best_loc >= 0 ? best_cnt + 1u : 0u);
-                        if (b0 + 32 < flen && (uint32_t)s.bnd[s.F[b0 + 32]] + 1u < thr) break;
-                    }
-                }
-                // warp argmax (lanes without a candidate hold best_loc = -1)
-                const uint32_t key_cnt = best_loc >= 0 ? best_cnt + 1u : 0u;
-                const uint32_t mx = __reduce_max_sync(FULL, key_cnt);
-                const uint32_t gkey = (key_cnt == mx) ? (uint32_t)best_gid : 0xffffffffu;
-                const uint32_t mg = __reduce_min_sync(FULL, gkey);
-                const uint32_t who = __ballot_sync(FULL, key_cnt == mx && (uint32_t)best_gid == mg);
-                const int p = __shfl_sync(FULL, best_loc, __ffs(who) - 1);
-                const uint32_t *prow = s.A + (int64_t)p * s.S;
-                uint32_t *ext = fr_ext(s, d);
-                for (int k = lane; k < s.wc; k += 32) ext[k] = cand[k] & ~prow[k];
-                __syncwarp();
-            }
-            enter = false;
-            // ---- periodic checks: budget, abort, splitting
-            if (++node_tick >= 64) {
-                node_tick = 0;
-                unsigned long long ab = 0, hungry = 0;
-                if (lane == 0) {
-                    if (globaltimer_ns() - t_start > P.max_run_ns) atomicOr(&P.ctl[CTL_ABORT], 2ULL);
-                    ab = *(volatile unsigned long long *)&P.ctl[CTL_ABORT];
-                    if (P.node_budget) {
-                        const unsigned long long tot = atomicAdd(&P.ctl[CTL_NODES], 64ULL) + 64ULL;
-                        if (tot > P.node_budget) {
-                            atomicOr(&P.ctl[CTL_ABORT], 1ULL);
-                            ab |= 1ULL;
-                        }
-                    }
-                    if (P.sub_nodes) {
-                        const unsigned long long delta = acc.t_nodes - acc.t_rep;
-                        acc.t_rep = acc.t_nodes;
-                        const unsigned long long tot = atomicAdd(&P.sub_nodes[root], delta) + delta;
-                        if (tot > P.sub_budget) ab |= 16ULL;
-                    }
-                    if (P.graph_nodes) {
-                        const int32_t gg = P.graph_of[P.mode == BK_MCE ? root : P.eu[root]];
-                        const unsigned long long tot = atomicAdd(&P.graph_nodes[gg], 64ULL) + 64ULL;
-                        if (P.graph_budget && tot > P.graph_budget) ab |= 16ULL;
-                    }
-                    if (P.split) {
-                        hungry = *(volatile unsigned long long *)&P.ctl[CTL_HUNGRY];
-                        const unsigned long long qh = *(volatile unsigned long long *)&P.ctl[CTL_QHEAD];
-                        const unsigned long long qt = *(volatile unsigned long long *)&P.ctl[CTL_QTAIL];
-                        if (qt > qh && qt - qh >= hungry) hungry = 0;
-                    }
-                }
-                ab = __shfl_sync(FULL, ab, 0);
-                hungry = __shfl_sync(FULL, hungry, 0);
-                if (ab & 1ULL) return false;
-                if (ab & 2ULL) return false;
-                if (ab & 16ULL) return true;   // this graph / subproblem is over its budget: drop the task
-                if (hungry) {
-                    // shallowest frame with at least two unexplored children
-                    for (int dd = 0; dd <= d; ++dd) {
-                        const uint32_t *ext = fr_ext(s, dd);
-                        const int rem = warp_popc(ext, s.wc, lane);
-                        if (rem < 2) continue;
-                        const int kd = T.kdepth + dd;
-                        int64_t pos = -1;
-                        if (lane == 0) pos = queue_claim_push(P);
-                        pos = __shfl_sync(FULL, pos, 0);
-                        if (pos < 0) break;
-                        // lower half stays here, upper half goes
-                        const int keep = rem / 2;
-                        uint32_t *rec = P.arena + (int64_t)((unsigned long long)pos % (unsigned long long)P.qcap) *
-                                                      P.slot_words;
-                        if (lane == 0) {
-                            rec[0] = (uint32_t)root;
-                            rec[1] = (uint32_t)kd;
-                        }
-                        for (int j = lane; j < kd; j += 32)
-                            rec[2 + j] = (uint32_t)(j < T.kdepth ? s.kpath[j] : (int32_t)fr_meta(s, j - T.kdepth + 1)[1]);
-                        uint32_t *rb = rec + 2 + kd;
-                        uint32_t *cand = fr_cand(s, dd), *finic = fr_finic(s, dd), *ext2 = fr_ext(s, dd);
-                        const uint32_t *conf = fr_conf(s, dd);
-                        // ext_lo = the `keep` lowest bits of ext
-                        int seen = 0;
-                        for (int k0w = 0; k0w < s.wc; k0w += 32) {
-                            const int k = k0w + lane;
-                            const uint32_t e = k < s.wc ? ext2[k] : 0u;
-                            const int pc = __popc(e);
-                            int incl = pc;
-                            for (int o = 1; o < 32; o <<= 1) {
-                                const int y = __shfl_up_sync(FULL, incl, o);
-                                if (lane >= o) incl += y;
-                            }
-                            const int before = seen + incl - pc;
-                            uint32_t lo = 0u;
-                            if (k < s.wc) {
-                                if (before + pc <= keep) lo = e;
-                                else if (before < keep) {
-                                    uint32_t x = e;
-                                    for (int t = 0; t < keep - before; ++t) {
-                                        const uint32_t bit = x & (0u - x);
-                                        lo |= bit;
-                                        x ^= bit;
-                                    }
-                                }
-                                rb[k] = cand[k] & ~lo;               // cand \ ext_lo
-                                rb[s.wc + k] = finic[k] | lo;        // fini ∪ ext_lo
-                                rb[2 * s.wc + k] = e & ~lo;          // ext_hi
-                                rb[3 * s.wc + k] = conf[k];
-                                ext2[k] = lo;
-                            }
-                            seen += __shfl_sync(FULL, incl, 31);
-                        }
-                        __threadfence();
-                        __syncwarp();
-                        if (lane == 0) {
-                            queue_publish(P, pos);
-                            atomicAdd(&P.out[OUT_SPLITS], 1ULL);
-                        }
-                        break;
-                    }
-                }
-            }
-        }
-        // ---- next child of frame d
-        {
-            uint32_t *ext = fr_ext(s, d);
-            const int q = warp_first_bit(ext, s.wc, lane);
-            if (q < 0) goto pop;
-            const int qw = q >> 5;
-            const uint32_t qb = 1u << (q & 31);
-            uint32_t *cand = fr_cand(s, d), *finic = fr_finic(s, d);
-            uint32_t *ncand = fr_cand(s, d + 1), *nfinic = fr_finic(s, d + 1);
-            const uint32_t *qrow = s.A + (int64_t)q * s.S;
-            for (int k = lane; k < s.wc; k += 32) {
-                ncand[k] = cand[k] & qrow[k];
-                nfinic[k] = finic[k] & qrow[k];
-                fr_ext(s, d + 1)[k] = 0u;
-                if (P.mode == BK_IMCE) fr_conf(s, d + 1)[k] = fr_conf(s, d)[k] | s.X[(int64_t)q * s.S + k];
-            }
-            const uint32_t *meta = fr_meta(s, d);
-            int nfl = 0;
-            if (meta[0]) {
-                nfl = partition_F(s, (int)meta[0], lane, [&](int32_t x) {
-                    return (s.A[(int64_t)x * s.S + qw] & qb) != 0u;
-                });
-            }
-            __syncwarp();
-            if (lane == 0) {
-                acc.wops += 2ull * (unsigned long long)s.wc + (unsigned long long)meta[0];
-                ext[qw] &= ~qb;
-                cand[qw] &= ~qb;
-                finic[qw] |= qb;
-                uint32_t *nm = fr_meta(s, d + 1);
-                nm[0] = (uint32_t)nfl;
-                nm[1] = (uint32_t)q;
-                meta_set_hsum(nm, meta_hsum(meta) + vertex_hash(s.gid[q], P.seed));
-            }
-            __syncwarp();
-            ++d;
-            enter = true;
-            continue;
-        }
-    pop:
-        if (d == 0) break;
-        if (P.mode == BK_MCE) {
-            // put frame d-1's F back in bnd order (the child split it into adjacent | rest)
-            const int a = (int)fr_meta(s, d)[0], len = (int)fr_meta(s, d - 1)[0];
-            if (a > 0 && a < len) merge_F(s, a, len, lane);
-        }
-        --d;
-        enter = false;
-    }
-    return true;
+    __syncwarp();
+    const int code = s.wc <= 32 ? search<1>(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter)
+                                : search<2>(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter);
+    return code != 1;
 }
 
 __global__ void k_init_seq(unsigned long long *seq, int64_t n) {
@@ -851,7 +1039,8 @@ __global__ void k_init_seq(unsigned long long *seq, int64_t n) {
         seq[i] = (unsigned long long)i;
 }
 
-__global__ void __launch_bounds__(256, 4) k_bk(BkParams P) {
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
     unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);   // 256 bins
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -862,7 +1051,7 @@ __global__ void __launch_bounds__(256, 4) k_bk(BkParams P) {
     const int64_t gwarp = (int64_t)blockIdx.x * nw_block + wib;
     uint32_t *ws_glob = P.gws + gwarp * P.gws_words;
     uint32_t *taskbuf = P.taskbuf + gwarp * P.slot_words;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     Ws s;
     int32_t built = -1;
     int node_tick = 0;
@@ -889,6 +1078,7 @@ __global__ void __launch_bounds__(256, 4) k_bk(BkParams P) {
                     if (i < (unsigned long long)P.n_sub) {
                         kind = 1;
                         T.root = P.order[i];
+                        if (i + 1 == (unsigned long long)P.n_sub) P.ctl[CTL_T_LAST] = globaltimer_ns();
                     }
                 }
                 if (kind == 0 && *(volatile unsigned long long *)&P.ctl[CTL_PENDING] == 0ULL) kind = 3;
@@ -897,11 +1087,23 @@ __global__ void __launch_bounds__(256, 4) k_bk(BkParams P) {
         kind = __shfl_sync(FULL, kind, 0);
         if (kind == 3) break;
         if (kind == 2) {
-            // copy the record out of the ring and free its slot at once
+            // copy the record out of the ring and free its slot at once; its
+            // length follows from the depth and the root's candidate count
             qpos = __shfl_sync(FULL, qpos, 0);
             const uint32_t *src = P.arena + (int64_t)((unsigned long long)qpos % (unsigned long long)P.qcap) *
                                                 P.slot_words;
-            for (int64_t k = lane; k < P.slot_words; k += 32) taskbuf[k] = __ldcg(src + k);
+            const int32_t r0 = (int32_t)__ldcg(src), kd0 = (int32_t)__ldcg(src + 1);
+            int32_t cr;
+            if (P.mode == BK_MCE) {
+                cr = P.up_ptr[r0 + 1] - P.up_ptr[r0];
+            } else {
+                const int32_t du = P.row_ptr[P.eu[r0] + 1] - P.row_ptr[P.eu[r0]];
+                const int32_t dv = P.row_ptr[P.ev[r0] + 1] - P.row_ptr[P.ev[r0]];
+                cr = du < dv ? du : dv;
+            }
+            int64_t words = 2 + (int64_t)kd0 + 4 * (int64_t)((cr + 31) >> 5);
+            if (words > P.slot_words) words = P.slot_words;
+            for (int64_t k = lane; k < words; k += 32) taskbuf[k] = __ldcg(src + k);
             __syncwarp();
             if (lane == 0) {
                 T.root = (int32_t)taskbuf[0];
@@ -937,7 +1139,7 @@ __global__ void __launch_bounds__(256, 4) k_bk(BkParams P) {
         T.root = __shfl_sync(FULL, T.root, 0);
         T.kdepth = __shfl_sync(FULL, T.kdepth, 0);
         T.rec = __shfl_sync(FULL, T.rec, 0);
-        acc.t_count = acc.t_hash = acc.t_nodes = acc.t_rep = 0;
+        acc.t_count = acc.t_hash = acc.t_nodes = acc.t_rep = acc.t_split = 0;
         const uint64_t t0 = globaltimer_ns();
         const bool go_on = run_task(P, s, T, acc, shist, ws_smem, ws_glob, taskbuf, lane, built, node_tick, t_start);
         acc.max_busy += globaltimer_ns() - t0;
@@ -963,6 +1165,7 @@ __global__ void __launch_bounds__(256, 4) k_bk(BkParams P) {
         if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
     }
     if (lane == 0) {
+        atomicMax(&P.ctl[CTL_T_END], (unsigned long long)globaltimer_ns());
         atomicAdd(&P.out[OUT_BUILD_NS], acc.build_ns);
         atomicAdd(&P.out[OUT_SEARCH_NS], acc.max_busy - acc.build_ns);
         atomicAdd(&P.out[OUT_IDLE_NS], acc.idle_ns);
@@ -995,9 +1198,19 @@ mce_status init_queue_seq(unsigned long long *seq, int64_t n, cudaStream_t s) {
 
 mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s) {
     const size_t smem = (size_t)512 * 4 + (size_t)warps_per_block * p.smem_words * 4;
-    MCE_CUDA(cudaFuncSetAttribute(k_bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned blocks = (unsigned)(num_sms() * blocks_per_sm);
-    MCE_LAUNCH(k_bk, blocks, warps_per_block * 32, smem, s, p);
+    // 4 resident blocks of 256 threads leave 64 registers a thread; fewer
+    // blocks let the compiler keep the search state in more registers
+    if (blocks_per_sm >= 4) {
+        MCE_CUDA(cudaFuncSetAttribute(k_bk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MCE_LAUNCH(k_bk<4>, blocks, warps_per_block * 32, smem, s, p);
+    } else if (blocks_per_sm == 3) {
+        MCE_CUDA(cudaFuncSetAttribute(k_bk<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MCE_LAUNCH(k_bk<3>, blocks, warps_per_block * 32, smem, s, p);
+    } else {
+        MCE_CUDA(cudaFuncSetAttribute(k_bk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MCE_LAUNCH(k_bk<2>, blocks, warps_per_block * 32, smem, s, p);
+    }
     return MCE_OK;
 }
 

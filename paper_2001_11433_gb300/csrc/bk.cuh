@@ -13,10 +13,12 @@ enum CtlWord {
     CTL_QHEAD = 2,     // ring tickets taken by poppers
     CTL_PENDING = 3,   // subproblems + queued tasks not finished
     CTL_HUNGRY = 4,    // warps waiting for work
-    CTL_UNUSED = 5,
+    CTL_CACHE_TOP = 5, // words of the build cache in use
     CTL_NODES = 6,     // tree nodes, for the budget
     CTL_ABORT = 7,     // 1 = budget, 2 = timeout, 4 = workspace too small, 8 = bad task
-    CTL_WORDS = 8
+    CTL_T_LAST = 8,    // globaltimer when the last subproblem was claimed
+    CTL_T_END = 9,     // latest globaltimer at which a warp left the launch
+    CTL_WORDS = 10
 };
 
 // Output block (uint64 words); the size histogram follows at OUT_HIST.
@@ -74,6 +76,11 @@ struct BkParams {
     unsigned long long *qseq;
     int64_t qcap;
     uint32_t *taskbuf;
+    // build cache: the warp that opens a subproblem builds its read-only part
+    // here and publishes the offset in cache_off[v]; pieces reuse it
+    uint32_t *cache;
+    int64_t cache_words;
+    long long *cache_off;
     unsigned long long *ctl;
     // outputs
     unsigned long long *out;
@@ -86,24 +93,36 @@ struct BkParams {
     unsigned long long *sub_nodes;    // exact nodes per subproblem (with sub_budget)
     uint64_t sub_budget;
     int32_t split;
+    uint32_t split_nodes;     // a task hands over a piece after this many nodes (0 = only when warps wait)
     uint64_t timeout_ns;      // bound on any single wait
     uint64_t max_run_ns;      // bound on a warp's time in one launch
 };
 
-// Workspace words needed by a subproblem with w local vertices of which c
-// are candidates (same formula on host and device).
-__host__ __device__ inline int64_t bk_ws_words(int64_t w, int64_t c, int32_t mode) {
+// Words of the read-only part of a built subproblem with w local vertices of
+// which c are candidates: a 32-word header (kept vertices W, kept fini f),
+// then local ids, bounds, bitset rows, and the bound-sorted fini list F0.
+// Rounded to 32 words so that every part starts on a 128-byte line.
+__host__ __device__ inline int64_t bk_shared_words(int64_t w, int64_t c) {
+    const int64_t wc = (c + 31) / 32;
+    const int64_t S = (wc & 1) ? wc : wc + 1;
+    const int64_t words = 32 + 2 * w + w * S + (w - c);
+    return (words + 31) & ~int64_t(31);
+}
+
+// Words of the per-warp search state: F and its scratch, frames, K path,
+// and (incremental mode) the exclusion rows.
+__host__ __device__ inline int64_t bk_private_words(int64_t w, int64_t c, int32_t mode) {
     const int64_t wc = (c + 31) / 32;
     const int64_t S = (wc & 1) ? wc : wc + 1;
     const int64_t fr = 4 * wc + 4;                  // cand, finic, ext, conf + meta
-    int64_t words = 2 * w                           // gid, bnd
-                    + w * S                         // A rows
-                    + 3 * (w - c)                   // F0 (sorted), F and its scratch
-                    + (c + 2) * fr                  // frames
-                    + (c + 2)                       // K path of the task
-                    + 8;
-    if (mode == BK_IMCE) words += (c + 2) * S;      // exclusion rows
-    return words;
+    int64_t words = 2 * (w - c) + (c + 2) * fr + (c + 2) + 8;
+    if (mode == BK_IMCE) words += (c + 2) * S;
+    return (words + 31) & ~int64_t(31);
+}
+
+// Workspace words needed by a subproblem (same formula on host and device).
+__host__ __device__ inline int64_t bk_ws_words(int64_t w, int64_t c, int32_t mode) {
+    return bk_shared_words(w, c) + bk_private_words(w, c, mode);
 }
 
 mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s);

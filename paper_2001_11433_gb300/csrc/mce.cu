@@ -22,7 +22,7 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
                               unsigned long long *req_max, const int32_t *graph_of, unsigned long long *g_count,
                               unsigned long long *g_hash, int64_t *list_off, int32_t *list_vtx,
                               int64_t list_max_cliques, int64_t list_max_words, const uint8_t *in_subset) {
-    unsigned long long cnt = 0, hsh = 0, nodes = 0, req = 0, cmax = 0;
+    unsigned long long cnt = 0, hsh = 0, nodes = 0, req = 0, cmax = 0, shw = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         if (in_subset && !in_subset[v]) {
             flag[v] = 0;
@@ -76,6 +76,7 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
             keys[v] = k;
             req = max(req, (unsigned long long)bk_ws_words(w, c, BK_MCE));
             cmax = max(cmax, (unsigned long long)c);
+            shw += (unsigned long long)bk_shared_words(w, c);
         }
         flag[v] = f;
     }
@@ -85,6 +86,7 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
         nodes += __shfl_xor_sync(0xffffffffu, nodes, o);
         req = max(req, __shfl_xor_sync(0xffffffffu, req, o));
         cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+        shw += __shfl_xor_sync(0xffffffffu, shw, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (cnt) {
@@ -96,6 +98,7 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
         if (nodes) atomicAdd(&out[OUT_NODES], nodes);
         if (req) atomicMax(req_max, req);
         if (cmax) atomicMax(req_max + 1, cmax);
+        if (shw) atomicAdd(req_max + 2, shw);
     }
 }
 
@@ -142,12 +145,18 @@ LaunchShape launch_shape(const mce_opts *o) {
     LaunchShape ls;
     ls.warps_per_block = (o && o->warps_per_block > 0) ? o->warps_per_block : 8;
     if (ls.warps_per_block > 8) ls.warps_per_block = 8;
-    ls.blocks_per_sm = (o && o->blocks_per_sm > 0) ? o->blocks_per_sm : 4;
+    // measured on GB300 (R-MAT 14 and 18): two resident blocks of eight warps,
+    // with the 128-register build of the search kernel, beat three or four
+    ls.blocks_per_sm = (o && o->blocks_per_sm > 0) ? o->blocks_per_sm : 2;
     // shared memory per SM is 228 KB with 1 KB reserved per block
     const int64_t per_block = (int64_t)228 * 1024 / ls.blocks_per_sm - 1024;
     int64_t words = (per_block - 2048) / 4 / ls.warps_per_block;
     words &= ~int64_t(3);
     if (words < 0) words = 0;
+    // Measured on GB300: the per-warp workspaces hit L1 more often when no
+    // shared memory is carved out for them, so slots are opt-in.
+    if (!o || o->shared_words <= 0) words = 0;
+    else if (o->shared_words < words) words = o->shared_words & ~3;
     ls.smem_words = (int32_t)words;
     return ls;
 }
@@ -237,7 +246,7 @@ mce_status read_result(const DevBuf &out, const DevBuf &ctl, cudaStream_t s, mce
     res->tasks_split = h[OUT_SPLITS];
     res->word_ops = h[OUT_WORDOPS];
     for (int i = 0; i < 7; ++i) res->stats[i] = h[OUT_BUILD_NS + i];
-    res->stats[7] = 0;
+    res->stats[7] = (c[CTL_T_END] > c[CTL_T_LAST] && c[CTL_T_LAST]) ? c[CTL_T_END] - c[CTL_T_LAST] : 0;
     res->complete = (c[CTL_ABORT] & 3ULL) ? 0 : 1;
     if (c[CTL_ABORT] & 4ULL) {
         g_last_error = "search workspace smaller than a subproblem";
@@ -299,8 +308,8 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
     MCE_TRY(flag.alloc((size_t)(n + 1) * 4, s));
     MCE_TRY(keys.alloc((size_t)(n + 1) * 8, s));
     DevBuf reqb, mask;
-    MCE_TRY(reqb.alloc(16, s));
-    MCE_CUDA(cudaMemsetAsync(reqb.p, 0, 16, s));
+    MCE_TRY(reqb.alloc(24, s));
+    MCE_CUDA(cudaMemsetAsync(reqb.p, 0, 24, s));
     const uint8_t *maskp = nullptr;
     DevBuf hsub;
     const int32_t *subp = o->subset;
@@ -340,9 +349,9 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
                    o->list_vtx, o->list_max_cliques, o->list_max_words, maskp);
     MCE_TRY(exclusive_scan_i32(flag.as<int32_t>(), flag.as<int32_t>(), n, s));
     int32_t n_act = 0;
-    unsigned long long reqc[2] = {0, 0};
+    unsigned long long reqc[3] = {0, 0, 0};
     MCE_CUDA(cudaMemcpyAsync(&n_act, flag.as<int32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
-    MCE_CUDA(cudaMemcpyAsync(reqc, reqb.p, 16, cudaMemcpyDeviceToHost, s));
+    MCE_CUDA(cudaMemcpyAsync(reqc, reqb.p, 24, cudaMemcpyDeviceToHost, s));
     MCE_CUDA(cudaStreamSynchronize(s));
     res->subproblems = n_act;
     BkBuffers bb;
@@ -385,7 +394,20 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
             P.sub_budget = o->subproblem_budget;
         }
         P.split = o->split;
+        P.split_nodes = o->split ? (o->split_nodes ? o->split_nodes : 2048u) : 0u;
         P.max_run_ns = (uint64_t)o->time_limit_ms * 1000000ULL;
+        // build cache for every subproblem (up to 2^29 words)
+        DevBuf cache, coff;
+        const int64_t cw = (int64_t)reqc[2] < ((int64_t)1 << 29) ? (int64_t)reqc[2] : ((int64_t)1 << 29);
+        if (cw > 0) {
+            MCE_TRY(cache.alloc((size_t)cw * 4 + 512, s));
+            MCE_TRY(coff.alloc((size_t)n * 8, s));
+            MCE_CUDA(cudaMemsetAsync(coff.p, 0xff, (size_t)n * 8, s));
+            // 128-byte aligned start
+            P.cache = reinterpret_cast<uint32_t *>(((uintptr_t)cache.p + 127) & ~(uintptr_t)127);
+            P.cache_words = cw;
+            P.cache_off = coff.as<long long>();
+        }
         const LaunchShape ls = launch_shape(o);
         cudaEvent_t k0, k1;
         MCE_CUDA(cudaEventCreate(&k0));
