@@ -46,6 +46,8 @@ struct Ws {
     int32_t *gid;
     int32_t *bnd;                 // popc(A[x]): bound on |cand ∩ Γ(x)| at every node
     int32_t *F0;                  // kept lower-ranked vertices sorted by bnd, descending
+    uint32_t *Cb;                 // per candidate q: bitset over F0 positions adjacent to q
+    int32_t Wf0;                  // words of one Cb row
     uint32_t *A;
     uint32_t *X;                  // IMCE exclusion rows
     int32_t *F, *Fs;
@@ -91,6 +93,8 @@ __device__ __forceinline__ void ws_layout(Ws &s, uint32_t *base, int32_t w, int3
     s.kpath = reinterpret_cast<int32_t *>(p);
     p += (c + 2);
     s.X = (mode == BK_IMCE) ? p : nullptr;
+    s.Cb = nullptr;
+    s.Wf0 = 0;
 }
 
 // MCE layout split in a read-only part (possibly shared through the build
@@ -109,6 +113,9 @@ __device__ __forceinline__ void ws_layout_split(Ws &s, uint32_t *shared, uint32_
     s.A = p;
     p += (int64_t)w * s.S;
     s.F0 = reinterpret_cast<int32_t *>(p);
+    p += (w - c);
+    s.Wf0 = (w - c + 31) >> 5;
+    s.Cb = p;
     p = priv;
     s.F = reinterpret_cast<int32_t *>(p);
     p += (w - c);
@@ -321,6 +328,47 @@ __device__ void build_mce(const BkParams &P, Ws &s, int32_t v, int lane) {
     s.W = c + f;
     __syncwarp();
     sort_F0(s, lane);
+    // Cb[q] = F0 positions whose vertex is adjacent to candidate q
+    const int64_t cbw = (int64_t)c * s.Wf0;
+    for (int64_t k = lane; k < cbw; k += 32) s.Cb[k] = 0u;
+    __syncwarp();
+    for (int pos = lane; pos < f; pos += 32) {
+        const uint32_t *row = s.A + (int64_t)s.F0[pos] * s.S;
+        for (int k = 0; k < s.wc; ++k) {
+            uint32_t m = row[k];
+            while (m) {
+                const int q = (k << 5) + __ffs(m) - 1;
+                m &= m - 1;
+                atomicOr(&s.Cb[(int64_t)q * s.Wf0 + (pos >> 5)], 1u << (pos & 31));
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// F for a child of the root (or the first step of a handed-over path):
+// F0 ∩ Γ(q) in F0 order, read off q's column bitset.  Returns its length.
+__device__ int compact_cb(const Ws &s, int q, int lane) {
+    const uint32_t *cb = s.Cb + (int64_t)q * s.Wf0;
+    int out = 0;
+    for (int w0 = 0; w0 < s.Wf0; w0 += 32) {
+        const int k = w0 + lane;
+        uint32_t m = k < s.Wf0 ? cb[k] : 0u;
+        const int pc = __popc(m);
+        int incl = pc;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int j = out + incl - pc;
+        while (m) {
+            s.F[j++] = s.F0[(k << 5) + __ffs(m) - 1];
+            m &= m - 1;
+        }
+        out += __shfl_sync(FULL, incl, 31);
+    }
+    __syncwarp();
+    return out;
 }
 
 // ParIMCENew subproblem of new edge i = (u, v) (Algorithm 6): local vertices
@@ -593,13 +641,16 @@ __device__ int periodic(const BkParams &P, Ws &s, const Task &T, Acc &acc, int l
     for (int dd = 0; dd <= d && budget > 0; ++dd) {
         const uint32_t *ext = fr_ext(s, dd);
         const int rem = warp_popc(ext, s.wc, lane);
-        if (rem < 2) continue;
+        // below the current frame a single pending sibling is a whole subtree
+        // worth handing over (this warp stays busy in the child it is in);
+        // at the current frame keep at least one child for this warp
+        if (rem < (dd < d ? 1 : 2)) continue;
         const int kd = T.kdepth + dd;
         int64_t pos = -1;
         if (lane == 0) pos = queue_claim_push(P);
         pos = __shfl_sync(FULL, pos, 0);
         if (pos < 0) break;
-        // lower half stays here, upper half goes
+        // lower half stays here, upper half goes (all of it when one sibling remains below)
         const int keep = rem / 2;
         uint32_t *rec = P.arena + (int64_t)((unsigned long long)pos % (unsigned long long)P.qcap) * P.slot_words;
         if (lane == 0) {
@@ -759,13 +810,14 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                 // of the next entries drops below the best count none of them can
                 // win (a tie needs count == best), so the scan stops there.
                 if (flen) {
+                    const int32_t *Fd = (T.kdepth == 0 && d == 0) ? s.F0 : s.F;
                     uint32_t thr = __reduce_max_sync(FULL, best_loc >= 0 ? best_cnt + 1u : 0u);
                     for (int b0 = 0; b0 < (int)flen; b0 += 32) {
                         const int i = b0 + lane;
                         int u = 0;
                         bool take = false;
                         if (i < (int)flen) {
-                            u = s.F[i];
+                            u = Fd[i];
                             take = (uint32_t)s.bnd[u] + 1u >= thr;
                         }
                         if (__any_sync(FULL, take)) {
@@ -786,7 +838,7 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                             }
                         }
                         thr = __reduce_max_sync(FULL, best_loc >= 0 ? best_cnt + 1u : 0u);
-                        if (b0 + 32 < (int)flen && (uint32_t)s.bnd[s.F[b0 + 32]] + 1u < thr) break;
+                        if (b0 + 32 < (int)flen && (uint32_t)s.bnd[Fd[b0 + 32]] + 1u < thr) break;
                     }
                 }
                 // warp argmax (lanes without a candidate hold best_loc = -1)
@@ -851,9 +903,13 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
             }
             int nfl = 0;
             if (flen) {
-                nfl = partition_F(s, (int)flen, lane, [&](int32_t x) {
-                    return (s.A[(int64_t)x * s.S + qw] & qb) != 0u;
-                });
+                if (T.kdepth == 0 && d == 0) {
+                    nfl = compact_cb(s, q, lane);   // F0 stays untouched at the root
+                } else {
+                    nfl = partition_F(s, (int)flen, lane, [&](int32_t x) {
+                        return (s.A[(int64_t)x * s.S + qw] & qb) != 0u;
+                    });
+                }
             }
             // parent frame to memory (its meta is unchanged), child meta
             frame_store<NR>(s, d, lane, rc, rf, re, rx);
@@ -881,8 +937,9 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
         }
     pop:
         if (d == 0) return 0;
-        if (P.mode == BK_MCE) {
-            // put frame d-1's F back in bnd order (the child split it into adjacent | rest)
+        if (P.mode == BK_MCE && !(T.kdepth == 0 && d == 1)) {
+            // put frame d-1's F back in bnd order (the child split it into adjacent | rest);
+            // the root frame reads F0, which no child touches
             const int a = (int)flen, len = (int)fr_meta(s, d - 1)[0];
             if (a > 0 && a < len) merge_F(s, a, len, lane);
         }
@@ -983,11 +1040,8 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
             finic[k] = 0u;
             if (P.mode == BK_MCE) fr_conf(s, 0)[k] = 0u;
         }
-        if (P.mode == BK_MCE) {
-            for (int i = lane; i < s.f; i += 32) s.F[i] = s.F0[i];
-        }
         if (lane == 0) {
-            m0[0] = (uint32_t)s.f;
+            m0[0] = (uint32_t)s.f;   // the root frame reads F0 itself
             m0[1] = 0xffffffffu;
         }
         enter = true;
@@ -1008,11 +1062,13 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
         int flen = 0;
         if (P.mode == BK_MCE) {
             // F at this frame: the kept lower-ranked vertices adjacent to the whole path,
-            // still ordered by bnd (the partition is stable)
-            for (int i = lane; i < s.f; i += 32) s.F[i] = s.F0[i];
-            __syncwarp();
-            flen = s.f;
-            for (int j = 0; j < kd; ++j) {
+            // in F0 order (the partition is stable).  A root piece reads F0 itself.
+            if (kd == 0) {
+                flen = s.f;
+            } else {
+                flen = compact_cb(s, s.kpath[0], lane);
+            }
+            for (int j = 1; j < kd; ++j) {
                 const int q = s.kpath[j];
                 flen = partition_F(s, flen, lane, [&](int32_t x) {
                     return (s.A[(int64_t)x * s.S + (q >> 5)] >> (q & 31)) & 1u;

@@ -100,12 +100,14 @@ struct BkParams {
 
 // Words of the read-only part of a built subproblem with w local vertices of
 // which c are candidates: a 32-word header (kept vertices W, kept fini f),
-// then local ids, bounds, bitset rows, and the bound-sorted fini list F0.
+// then local ids, bounds, bitset rows, the bound-sorted fini list F0, and one
+// bitset over F0 positions per candidate (its lower-ranked neighbours).
 // Rounded to 32 words so that every part starts on a 128-byte line.
 __host__ __device__ inline int64_t bk_shared_words(int64_t w, int64_t c) {
     const int64_t wc = (c + 31) / 32;
     const int64_t S = (wc & 1) ? wc : wc + 1;
-    const int64_t words = 32 + 2 * w + w * S + (w - c);
+    const int64_t wf = (w - c + 31) / 32;
+    const int64_t words = 32 + 2 * w + w * S + (w - c) + c * wf;
     return (words + 31) & ~int64_t(31);
 }
 
