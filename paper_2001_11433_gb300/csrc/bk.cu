@@ -54,6 +54,7 @@ struct Ws {
     uint32_t *fr;                 // frames
     int32_t *kpath;               // K path of the current task (local ids)
     int32_t frw;                  // words per frame
+    int32_t dcap;                 // frames available
 };
 
 __device__ __forceinline__ uint32_t *fr_cand(const Ws &s, int d) { return s.fr + (int64_t)d * s.frw; }
@@ -89,7 +90,8 @@ __device__ __forceinline__ void ws_layout(Ws &s, uint32_t *base, int32_t w, int3
     s.Fs = reinterpret_cast<int32_t *>(p);
     p += (w - c);
     s.fr = p;
-    p += (int64_t)(c + 2) * s.frw;
+    s.dcap = (int32_t)bk_depth_cap(c);
+    p += (int64_t)s.dcap * s.frw;
     s.kpath = reinterpret_cast<int32_t *>(p);
     p += (c + 2);
     s.X = (mode == BK_IMCE) ? p : nullptr;
@@ -122,7 +124,8 @@ __device__ __forceinline__ void ws_layout_split(Ws &s, uint32_t *shared, uint32_
     s.Fs = reinterpret_cast<int32_t *>(p);
     p += (w - c);
     s.fr = p;
-    p += (int64_t)(c + 2) * s.frw;
+    s.dcap = (int32_t)bk_depth_cap(c);
+    p += (int64_t)s.dcap * s.frw;
     s.kpath = reinterpret_cast<int32_t *>(p);
     s.X = nullptr;
 }
@@ -416,7 +419,8 @@ __device__ void build_imce(const BkParams &P, Ws &s, int32_t i, int lane) {
         s.F = s.F0;
         s.Fs = s.F;
         s.fr = p;
-        p += (int64_t)(c + 2) * s.frw;
+        s.dcap = (int32_t)bk_depth_cap(c);
+        p += (int64_t)s.dcap * s.frw;
         s.kpath = reinterpret_cast<int32_t *>(p);
         p += (c + 2);
         s.X = p;
@@ -911,6 +915,10 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                     });
                 }
             }
+            if (d + 2 > s.dcap) {   // deeper than the frame stack: stop with an error
+                if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 4ULL);
+                return 1;
+            }
             // parent frame to memory (its meta is unchanged), child meta
             frame_store<NR>(s, d, lane, rc, rf, re, rx);
             const uint64_t nh = hsum + vertex_hash(s.gid[q], P.seed);
@@ -951,6 +959,149 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
     }
 }
 
+// The same search for candidate sets wider than 64 words (more than 2048
+// candidates, which some ranks produce for hubs): frames stay in memory and
+// every set operation loops over its words.  Returns as search<NR>.
+__device__ int search_mem(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigned long long *shist, int lane,
+                          int &node_tick, uint64_t t_start, int32_t root, int k0, bool enter) {
+    const int wc = s.wc;
+    int d = 0;
+    for (;;) {
+        uint32_t *cand = fr_cand(s, d), *finic = fr_finic(s, d), *ext = fr_ext(s, d);
+        uint32_t *meta = fr_meta(s, d);
+        if (enter) {
+            acc.nodes++;
+            acc.t_nodes++;
+            if (P.mode == BK_IMCE) {
+                const uint32_t *conf = fr_conf(s, d);
+                for (int k = lane; k < wc; k += 32) {
+                    const uint32_t x = cand[k] & conf[k];
+                    finic[k] |= x;
+                    cand[k] &= ~x;
+                }
+                __syncwarp();
+            }
+            if (!warp_any(cand, wc, lane)) {
+                const bool fin = warp_any(finic, wc, lane) || meta[0] != 0u;
+                if (!fin) emit(P, s, root, k0, d, meta_hsum(meta), acc, shist, lane);
+                goto pop;
+            }
+            {
+                uint32_t best_cnt = 0;
+                int32_t best_gid = 0x7fffffff, best_loc = -1;
+                for (int k = 0; k < wc; ++k) {
+                    const uint32_t mword = cand[k] | finic[k];
+                    if ((mword >> lane) & 1u) {
+                        acc.wops += (unsigned long long)wc;
+                        const int u = (k << 5) + lane;
+                        const uint32_t *row = s.A + (int64_t)u * s.S;
+                        uint32_t cnt = 0;
+                        for (int t = 0; t < wc; ++t) cnt += __popc(cand[t] & row[t]);
+                        const int32_t g = s.gid[u];
+                        if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
+                            best_cnt = cnt;
+                            best_gid = g;
+                            best_loc = u;
+                        }
+                    }
+                }
+                const int flen = (int)meta[0];
+                if (flen) {
+                    const int32_t *Fd = (T.kdepth == 0 && d == 0) ? s.F0 : s.F;
+                    uint32_t thr = __reduce_max_sync(FULL, best_loc >= 0 ? best_cnt + 1u : 0u);
+                    for (int b0 = 0; b0 < flen; b0 += 32) {
+                        const int i = b0 + lane;
+                        if (i < flen) {
+                            const int u = Fd[i];
+                            if ((uint32_t)s.bnd[u] + 1u >= thr) {
+                                const uint32_t *row = s.A + (int64_t)u * s.S;
+                                uint32_t cnt = 0;
+                                for (int t = 0; t < wc; ++t) cnt += __popc(cand[t] & row[t]);
+                                acc.wops += (unsigned long long)wc;
+                                const int32_t g = s.gid[u];
+                                if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
+                                    best_cnt = cnt;
+                                    best_gid = g;
+                                    best_loc = u;
+                                }
+                            }
+                        }
+                        thr = __reduce_max_sync(FULL, best_loc >= 0 ? best_cnt + 1u : 0u);
+                        if (b0 + 32 < flen && (uint32_t)s.bnd[Fd[b0 + 32]] + 1u < thr) break;
+                    }
+                }
+                const uint32_t key_cnt = best_loc >= 0 ? best_cnt + 1u : 0u;
+                const uint32_t mx = __reduce_max_sync(FULL, key_cnt);
+                const uint32_t gkey = (key_cnt == mx) ? (uint32_t)best_gid : 0xffffffffu;
+                const uint32_t mg = __reduce_min_sync(FULL, gkey);
+                const uint32_t who = __ballot_sync(FULL, key_cnt == mx && (uint32_t)best_gid == mg);
+                const int p = __shfl_sync(FULL, best_loc, __ffs(who) - 1);
+                const uint32_t *prow = s.A + (int64_t)p * s.S;
+                for (int k = lane; k < wc; k += 32) ext[k] = cand[k] & ~prow[k];
+                __syncwarp();
+            }
+            enter = false;
+            if (++node_tick >= 64) {
+                node_tick = 0;
+                const int act = periodic(P, s, T, acc, lane, d, root, t_start);
+                if (act) return act;
+            }
+        }
+        {
+            const int q = warp_first_bit(ext, wc, lane);
+            if (q < 0) goto pop;
+            const int qw = q >> 5;
+            const uint32_t qb = 1u << (q & 31);
+            if (d + 2 > s.dcap) {
+                if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 4ULL);
+                return 1;
+            }
+            const uint32_t *qrow = s.A + (int64_t)q * s.S;
+            uint32_t *ncand = fr_cand(s, d + 1), *nfinic = fr_finic(s, d + 1);
+            for (int k = lane; k < wc; k += 32) {
+                ncand[k] = cand[k] & qrow[k];
+                nfinic[k] = finic[k] & qrow[k];
+                fr_ext(s, d + 1)[k] = 0u;
+                fr_conf(s, d + 1)[k] = fr_conf(s, d)[k] | (P.mode == BK_IMCE ? s.X[(int64_t)q * s.S + k] : 0u);
+            }
+            int nfl = 0;
+            const int flen = (int)meta[0];
+            if (flen) {
+                if (T.kdepth == 0 && d == 0) {
+                    nfl = compact_cb(s, q, lane);
+                } else {
+                    nfl = partition_F(s, flen, lane, [&](int32_t x) {
+                        return (s.A[(int64_t)x * s.S + qw] & qb) != 0u;
+                    });
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                acc.wops += 2ull * (unsigned long long)wc + (unsigned long long)flen;
+                ext[qw] &= ~qb;
+                cand[qw] &= ~qb;
+                finic[qw] |= qb;
+                uint32_t *nm = fr_meta(s, d + 1);
+                nm[0] = (uint32_t)nfl;
+                nm[1] = (uint32_t)q;
+                meta_set_hsum(nm, meta_hsum(meta) + vertex_hash(s.gid[q], P.seed));
+            }
+            __syncwarp();
+            ++d;
+            enter = true;
+            continue;
+        }
+    pop:
+        if (d == 0) return 0;
+        if (P.mode == BK_MCE && !(T.kdepth == 0 && d == 1)) {
+            const int a = (int)fr_meta(s, d)[0], len = (int)fr_meta(s, d - 1)[0];
+            if (a > 0 && a < len) merge_F(s, a, len, lane);
+        }
+        --d;
+        enter = false;
+    }
+}
+
 // Run one task to completion.  Returns false when the launch must stop.
 __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigned long long *shist,
                          uint32_t *ws_smem, uint32_t *ws_glob, const uint32_t *taskbuf, int lane,
@@ -969,7 +1120,7 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
     }
     const int64_t need = bk_ws_words(w, c, P.mode);
     uint32_t *base = (need <= P.smem_words) ? ws_smem : ws_glob;
-    if (need > P.gws_words && base == ws_glob) {
+    if (bk_private_words(w, c, P.mode) > P.gws_words && base == ws_glob) {
         if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 4ULL);
         return false;
     }
@@ -1013,6 +1164,10 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
         }
     }
     if (!ready) {
+        if (need > P.gws_words && base == ws_glob) {   // no cache room and no room for a private build
+            if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 4ULL);
+            return false;
+        }
         if (P.mode == BK_MCE) ws_layout_split(s, base, base + bk_shared_words(w, c), w, c);
         else ws_layout(s, base, w, c, P.mode);
         if (built != root || P.mode == BK_IMCE) {   // same pointers as the last build of `root`: f and W kept
@@ -1085,8 +1240,9 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
     __syncwarp();
 
     __syncwarp();
-    const int code = s.wc <= 32 ? search<1>(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter)
-                                : search<2>(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter);
+    const int code = s.wc <= 32   ? search<1>(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter)
+                     : s.wc <= 64 ? search<2>(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter)
+                                  : search_mem(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter);
     return code != 1;
 }
 

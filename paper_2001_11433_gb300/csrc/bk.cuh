@@ -111,13 +111,17 @@ __host__ __device__ inline int64_t bk_shared_words(int64_t w, int64_t c) {
     return (words + 31) & ~int64_t(31);
 }
 
+// Frames of the explicit stack: one per clique vertex beyond the seeds,
+// at most 511 (a deeper search stops with an error instead of overrunning).
+__host__ __device__ inline int64_t bk_depth_cap(int64_t c) { return (c < 511 ? c : 511) + 2; }
+
 // Words of the per-warp search state: F and its scratch, frames, K path,
 // and (incremental mode) the exclusion rows.
 __host__ __device__ inline int64_t bk_private_words(int64_t w, int64_t c, int32_t mode) {
     const int64_t wc = (c + 31) / 32;
     const int64_t S = (wc & 1) ? wc : wc + 1;
     const int64_t fr = 4 * wc + 4;                  // cand, finic, ext, conf + meta
-    int64_t words = 2 * (w - c) + (c + 2) * fr + (c + 2) + 8;
+    int64_t words = 2 * (w - c) + bk_depth_cap(c) * fr + (c + 2) + 8;
     if (mode == BK_IMCE) words += (c + 2) * S;
     return (words + 31) & ~int64_t(31);
 }

@@ -71,28 +71,46 @@ __global__ void k_degree_i32(const int32_t *row_ptr, int32_t n, int32_t *d) {
 // every alive vertex whose remaining degree is <= k is removed with core
 // number k; removing a vertex decrements its alive neighbours, and those that
 // fall to <= k are removed at the same level (claimed once by CAS).
-// ctl[0] = removed so far, ctl[1], ctl[2] = lengths of the two frontiers.
+// The seeding scan of a level visits only the vertices still alive after the
+// previous one (a compacted list), so a level costs its alive count, not n.
+// ctl[0] = removed so far, ctl[1], ctl[2] = lengths of the two frontiers,
+// ctl[3], ctl[4] = lengths of the two alive lists.
 // Every read of a control word is followed by a grid barrier before any
 // thread may change that word, so all threads take the same branches.
 __global__ void k_core_peel(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
-                            int32_t *d, int32_t *core, int32_t *fa, int32_t *fb, int32_t *ctl) {
+                            int32_t *d, int32_t *core, int32_t *fa, int32_t *fb, int32_t *la, int32_t *lb,
+                            int32_t *ctl) {
     cg::grid_group grid = cg::this_grid();
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    int32_t *cur = fa, *nxt = fb;
-    int ci = 1, ni = 2;
+    int32_t *cur = fa, *nxt = fb, *alive = la, *alive2 = lb;
+    int ci = 1, ni = 2, ai = 3, bi = 4;
     for (int32_t k = 0; k <= n; ++k) {   // a core number never exceeds n - 1
         grid.sync();
         const int32_t removed = *(volatile int32_t *)&ctl[0];
+        const int32_t na = *(volatile int32_t *)&ctl[ai];
         grid.sync();
         if (removed >= n) break;
-        for (int64_t v = tid; v < n; v += nth) {
-            if (core[v] < 0 && d[v] <= k) {
+        for (int64_t i = tid; i < na; i += nth) {
+            const int32_t v = alive[i];
+            if (*(volatile int32_t *)&core[v] >= 0) continue;   // removed at an earlier level
+            if (d[v] <= k) {
                 core[v] = k;
-                cur[atomicAdd(&ctl[ci], 1)] = (int32_t)v;
+                cur[atomicAdd(&ctl[ci], 1)] = v;
+            } else {
+                alive2[atomicAdd(&ctl[bi], 1)] = v;
             }
         }
         grid.sync();
+        if (tid == 0) ctl[ai] = 0;   // read by everyone before the last barrier
+        {
+            int32_t *t = alive;
+            alive = alive2;
+            alive2 = t;
+            const int ti = ai;
+            ai = bi;
+            bi = ti;
+        }
         for (;;) {
             const int32_t len = *(volatile int32_t *)&ctl[ci];
             grid.sync();
@@ -119,6 +137,11 @@ __global__ void k_core_peel(const int32_t *__restrict__ row_ptr, const int32_t *
             grid.sync();
         }
     }
+}
+
+__global__ void k_iota(int32_t *a, int32_t n) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        a[v] = (int32_t)v;
 }
 
 __global__ void k_i32_to_i64(const int32_t *a, int32_t n, int64_t *b) {
@@ -287,15 +310,20 @@ mce_status build_csr(const int32_t *u, const int32_t *v, int64_t m, int32_t n, c
 
 static mce_status core_numbers(const mce_graph *g, cudaStream_t s, int64_t *key) {
     const int32_t n = g->n;
-    DevBuf d, core, fa, fb, ctl;
+    DevBuf d, core, fa, fb, la, lb, ctl;
     MCE_TRY(d.alloc((size_t)n * sizeof(int32_t), s));
     MCE_TRY(core.alloc((size_t)n * sizeof(int32_t), s));
     MCE_TRY(fa.alloc((size_t)n * sizeof(int32_t), s));
     MCE_TRY(fb.alloc((size_t)n * sizeof(int32_t), s));
-    MCE_TRY(ctl.alloc(4 * sizeof(int32_t), s));
+    MCE_TRY(la.alloc((size_t)n * sizeof(int32_t), s));
+    MCE_TRY(lb.alloc((size_t)n * sizeof(int32_t), s));
+    MCE_TRY(ctl.alloc(8 * sizeof(int32_t), s));
     MCE_LAUNCH(k_degree_i32, grid_for(n, 256), 256, 0, s, g->row_ptr, n, d.as<int32_t>());
+    MCE_LAUNCH(k_iota, grid_for(n, 256), 256, 0, s, la.as<int32_t>(), n);
     MCE_CUDA(cudaMemsetAsync(core.p, 0xff, (size_t)n * sizeof(int32_t), s));
-    MCE_CUDA(cudaMemsetAsync(ctl.p, 0, 4 * sizeof(int32_t), s));
+    MCE_CUDA(cudaMemsetAsync(ctl.p, 0, 8 * sizeof(int32_t), s));
+    const int32_t n0 = n;
+    MCE_CUDA(cudaMemcpyAsync(ctl.as<int32_t>() + 3, &n0, sizeof(int32_t), cudaMemcpyHostToDevice, s));
     int dev = 0, per_sm = 0;
     MCE_CUDA(cudaGetDevice(&dev));
     MCE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_core_peel, 256, 0));
@@ -306,10 +334,10 @@ static mce_status core_numbers(const mce_graph *g, cudaStream_t s, int64_t *key)
     unsigned blocks = (unsigned)(num_sms() * per_sm);
     const int32_t *rp = g->row_ptr, *cl = g->col;
     int32_t *pd = d.as<int32_t>(), *pc = core.as<int32_t>(), *pa = fa.as<int32_t>(), *pb = fb.as<int32_t>(),
-            *pt = ctl.as<int32_t>();
+            *pla = la.as<int32_t>(), *plb = lb.as<int32_t>(), *pt = ctl.as<int32_t>();
     int32_t nn = n;
     void *args[] = {(void *)&rp, (void *)&cl, (void *)&nn, (void *)&pd, (void *)&pc, (void *)&pa, (void *)&pb,
-                    (void *)&pt};
+                    (void *)&pla, (void *)&plb, (void *)&pt};
     g_launches.fetch_add(1, std::memory_order_relaxed);
     MCE_CUDA(cudaLaunchCooperativeKernel((const void *)k_core_peel, dim3(blocks), dim3(256), args, 0, s));
     MCE_LAUNCH(k_i32_to_i64, grid_for(n, 256), 256, 0, s, core.as<int32_t>(), n, key);

@@ -22,7 +22,7 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
                               unsigned long long *req_max, const int32_t *graph_of, unsigned long long *g_count,
                               unsigned long long *g_hash, int64_t *list_off, int32_t *list_vtx,
                               int64_t list_max_cliques, int64_t list_max_words, const uint8_t *in_subset) {
-    unsigned long long cnt = 0, hsh = 0, nodes = 0, req = 0, cmax = 0, shw = 0;
+    unsigned long long cnt = 0, hsh = 0, nodes = 0, req = 0, cmax = 0, shw = 0, prv = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         if (in_subset && !in_subset[v]) {
             flag[v] = 0;
@@ -77,6 +77,7 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
             req = max(req, (unsigned long long)bk_ws_words(w, c, BK_MCE));
             cmax = max(cmax, (unsigned long long)c);
             shw += (unsigned long long)bk_shared_words(w, c);
+            prv = max(prv, (unsigned long long)bk_private_words(w, c, BK_MCE));
         }
         flag[v] = f;
     }
@@ -87,6 +88,7 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
         req = max(req, __shfl_xor_sync(0xffffffffu, req, o));
         cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
         shw += __shfl_xor_sync(0xffffffffu, shw, o);
+        prv = max(prv, __shfl_xor_sync(0xffffffffu, prv, o));
     }
     if ((threadIdx.x & 31) == 0) {
         if (cnt) {
@@ -99,6 +101,7 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
         if (req) atomicMax(req_max, req);
         if (cmax) atomicMax(req_max + 1, cmax);
         if (shw) atomicAdd(req_max + 2, shw);
+        if (prv) atomicMax(req_max + 3, prv);
     }
 }
 
@@ -308,8 +311,8 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
     MCE_TRY(flag.alloc((size_t)(n + 1) * 4, s));
     MCE_TRY(keys.alloc((size_t)(n + 1) * 8, s));
     DevBuf reqb, mask;
-    MCE_TRY(reqb.alloc(24, s));
-    MCE_CUDA(cudaMemsetAsync(reqb.p, 0, 24, s));
+    MCE_TRY(reqb.alloc(32, s));
+    MCE_CUDA(cudaMemsetAsync(reqb.p, 0, 32, s));
     const uint8_t *maskp = nullptr;
     DevBuf hsub;
     const int32_t *subp = o->subset;
@@ -349,9 +352,9 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
                    o->list_vtx, o->list_max_cliques, o->list_max_words, maskp);
     MCE_TRY(exclusive_scan_i32(flag.as<int32_t>(), flag.as<int32_t>(), n, s));
     int32_t n_act = 0;
-    unsigned long long reqc[3] = {0, 0, 0};
+    unsigned long long reqc[4] = {0, 0, 0, 0};
     MCE_CUDA(cudaMemcpyAsync(&n_act, flag.as<int32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
-    MCE_CUDA(cudaMemcpyAsync(reqc, reqb.p, 24, cudaMemcpyDeviceToHost, s));
+    MCE_CUDA(cudaMemcpyAsync(reqc, reqb.p, 32, cudaMemcpyDeviceToHost, s));
     MCE_CUDA(cudaStreamSynchronize(s));
     res->subproblems = n_act;
     BkBuffers bb;
@@ -396,9 +399,14 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         P.split = o->split;
         P.split_nodes = o->split ? (o->split_nodes ? o->split_nodes : 2048u) : 0u;
         P.max_run_ns = (uint64_t)o->time_limit_ms * 1000000ULL;
-        // build cache for every subproblem (up to 2^29 words)
+        // build cache for every subproblem (up to 2^30 words); when it holds them
+        // all, a warp's own workspace only needs the private search state
         DevBuf cache, coff;
-        const int64_t cw = (int64_t)reqc[2] < ((int64_t)1 << 29) ? (int64_t)reqc[2] : ((int64_t)1 << 29);
+        const int64_t cw = (int64_t)reqc[2] < ((int64_t)1 << 30) ? (int64_t)reqc[2] : ((int64_t)1 << 30);
+        int64_t per_warp = (int64_t)reqc[0];
+        if (cw == (int64_t)reqc[2]) per_warp = (int64_t)reqc[3];
+        else if (per_warp > ((int64_t)1 << 24)) per_warp = (int64_t)reqc[3] > ((int64_t)1 << 24) ? (int64_t)reqc[3]
+                                                                                                 : ((int64_t)1 << 24);
         if (cw > 0) {
             MCE_TRY(cache.alloc((size_t)cw * 4 + 512, s));
             MCE_TRY(coff.alloc((size_t)n * 8, s));
@@ -414,7 +422,7 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         MCE_CUDA(cudaEventCreate(&k1));
         EvPair kg{k0, k1};
         MCE_CUDA(cudaEventRecord(k0, s));
-        MCE_TRY(run_bk(P, ls, (int64_t)reqc[0], (int64_t)reqc[1], s, bb));
+        MCE_TRY(run_bk(P, ls, per_warp, (int64_t)reqc[1], s, bb));
         MCE_CUDA(cudaEventRecord(k1, s));
         MCE_CUDA(cudaEventSynchronize(k1));
         float ks = 0;

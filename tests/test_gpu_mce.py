@@ -266,3 +266,30 @@ def test_subset_and_subproblem_budget(gpu_lib):
     o2 = O.parmce(og, rk, subset=sub, threads=4)
     assert_same_summary(r2, o2)
     assert r2.tree_nodes == o2.nodes and r2.incomplete == 0
+
+
+@pytest.mark.parametrize("hub_degree", [2100, 5000])
+def test_wide_candidate_sets(gpu_lib, hub_degree):
+    """A rank that puts a hub lowest gives its subproblem every neighbour as a
+    candidate (more than 2048 here); the result must not depend on the rank."""
+    mce = gpu_lib
+    rng = np.random.default_rng(hub_degree)
+    n = hub_degree + 1
+    leaves = np.arange(1, n, dtype=np.int32)
+    u = [np.zeros(hub_degree, np.int32)]
+    v = [leaves]
+    # sparse random structure among the leaves: triangles and small cliques through the hub
+    a = rng.integers(1, n, 3 * hub_degree).astype(np.int32)
+    b = rng.integers(1, n, 3 * hub_degree).astype(np.int32)
+    u.append(a)
+    v.append(b)
+    u, v = np.concatenate(u), np.concatenate(v)
+    og = O.Graph(n, u, v)
+    rk = np.arange(n, dtype=np.int32)      # hub (vertex 0) ranked lowest
+    o = O.parmce(og, rk, per_vertex=True, threads=4)
+    g = gpu_graph(mce, n, u, v)
+    pv = per_vertex_bufs(n)
+    r = mce.enumerate_cliques(g, rank="user", user_rank=_t(rk), per_vertex=pv)
+    assert_same_summary(r, o)
+    assert r.tree_nodes == o.nodes
+    assert np.array_equal(u64(pv[2]), o.per_vertex["nodes"])
