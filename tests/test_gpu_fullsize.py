@@ -58,3 +58,24 @@ def test_rmat18_sampled_subproblems(gpu_lib):
     assert r2.hash == int(hsh[keep].astype(object).sum()) % (1 << 64)
     assert r2.tree_nodes == int(nodes[keep].sum())
     assert r2.incomplete == 0 and r2.complete
+
+
+def test_chung_lu_planted_full_enumeration(gpu_lib):
+    """The whole Chung-Lu graph (1.7M vertices, ~11M edges, 200 planted
+    cliques): count, set hash and size histogram equal the oracle's stored
+    summary (tests/golden/chung_lu_planted.json, written by make_golden.py
+    from oracle.parmce), for every Section 4.2 rank."""
+    import json
+    import os
+    mce = gpu_lib
+    with open(os.path.join(os.path.dirname(__file__), "golden", "chung_lu_planted.json")) as f:
+        gold = json.load(f)
+    w = graphgen.chung_lu_planted()
+    assert w.name == gold["workload"] and w.n == gold["n"]
+    g = mce.Graph(w.n, _t(w.u), _t(w.v))
+    assert g.nnz // 2 == gold["edges"]
+    for kind in ("degen", "degree", "triangle"):
+        r = mce.enumerate_cliques(g, rank=kind)
+        assert r.count == gold["count"], kind
+        assert r.hash == int(gold["hash"]), kind
+        assert list(r.hist) == gold["hist"], kind
