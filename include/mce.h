@@ -236,6 +236,30 @@ mce_status mce_enumerate_batched(const mce_graph *g, const int32_t *graph_ptr, i
                                  const mce_opts *opts, uint64_t *counts, uint64_t *hashes,
                                  int32_t *status, mce_result *total);
 
+/* A reusable batched plan: everything that does not change between runs
+ * (graph ids, rank, Γ+ lists, trivial subproblems, subproblem order, all
+ * device buffers) is prepared once by mce_batched_create; graph_ptr is host
+ * int32[k+1] as for mce_enumerate_batched and opts->node_budget is the
+ * per-graph budget.  The plan keeps pointers into g, which must outlive it. */
+typedef struct mce_batched mce_batched;
+mce_status mce_batched_create(const mce_graph *g, const int32_t *graph_ptr, int32_t k, const mce_opts *opts,
+                              mce_batched **b);
+/* One asynchronous run on `stream` (no host synchronisation, no
+ * allocation).  The first run after creation or tuning is captured into a
+ * CUDA graph; later runs replay it. */
+mce_status mce_batched_run(mce_batched *b, void *stream);
+/* Wait for the last run and copy its per-graph results to host arrays
+ * (counts uint64[k], hashes uint64[k], status int32[k]; each may be NULL)
+ * and the summary over all graphs to *total. */
+mce_status mce_batched_read(mce_batched *b, void *stream, uint64_t *counts, uint64_t *hashes, int32_t *status,
+                            mce_result *total);
+/* Autotuner: times `repeats` runs of each launch shape (resident blocks per
+ * SM x hand-over interval) with the per-graph budget lowered to tune_budget
+ * (0 = keep it) and keeps the fastest; the choice is returned. */
+mce_status mce_batched_tune(mce_batched *b, void *stream, uint64_t tune_budget, int32_t repeats,
+                            int32_t *best_blocks_per_sm, uint32_t *best_split_nodes);
+void mce_batched_free(mce_batched *b);
+
 /* ---------------------------------------------------------------- incremental MCE */
 
 typedef struct {
@@ -266,6 +290,74 @@ const mce_graph *imce_graph(const imce_state *s);
 mce_status imce_cliques(const imce_state *s, int64_t *list_off, int32_t *list_vtx,
                         int64_t max_cliques, int64_t max_words, int64_t *n_cliques, int64_t *n_words);
 void imce_close(imce_state *s);
+
+/* ---------------------------------------------------------------- serving loop */
+
+/* Continuous batching of edge batches over device-resident graphs (tenants),
+ * each with its clique index.  Section 5 defines one step for G and a batch
+ * H, so a tenant runs one batch at a time in submission order; batches of
+ * different tenants run concurrently, one per slot (a worker thread with its
+ * own CUDA stream).  A batch is admitted when it has arrived, its tenant is
+ * idle, a slot is free and its projected device memory (mem_fixed + 16(n+1)
+ * + 8(nnz+2k) + 96k bytes) fits mem_budget next to the batches in flight;
+ * the oldest arrived batch that does not fit holds back later ones, and a
+ * batch is always admitted when nothing is in flight.  Latency is measured
+ * from arrival to completion on a host steady clock. */
+typedef struct imce_server imce_server;
+/* Test hook: when set, the server calls it in place of imce_add_edges (host
+ * arrays u, v of k pairs) and tenants carry no device state. */
+typedef mce_status (*imce_server_exec_fn)(void *ctx, int32_t tenant, const int32_t *u, const int32_t *v, int64_t k,
+                                          imce_delta *out);
+typedef struct {
+    int32_t slots;             /* concurrent batches, 1..64 (default 4) */
+    uint64_t mem_budget;       /* bytes; 0 = 80% of free device memory at create */
+    uint64_t mem_fixed;        /* per-batch fixed part of the projection; 0 = 384 MiB */
+    imce_server_exec_fn execute;
+    void *execute_ctx;
+} imce_server_opts;
+
+typedef struct {
+    int64_t id;
+    int32_t tenant;
+    mce_status status;         /* of imce_add_edges for this batch */
+    int64_t edges;             /* raw pairs submitted */
+    double arrival_ms, admit_ms, done_ms;   /* server clock */
+    uint64_t reserved;         /* projected bytes held while in flight */
+    imce_delta delta;
+} imce_request_info;
+
+typedef struct {
+    int64_t completed, failed, edges, applied;
+    uint64_t new_cliques, subsumed_cliques;
+    double p50_ms, p99_ms, max_ms;          /* latency: arrival -> completion */
+    double wait_p50_ms, wait_p99_ms;        /* arrival -> admission */
+    double span_ms;                         /* first arrival -> last completion */
+    double edges_per_s;                     /* edges / span */
+    int32_t max_in_flight;
+    uint64_t peak_reserved, mem_budget;
+} imce_server_stats;
+
+void imce_server_opts_init(imce_server_opts *o);
+mce_status imce_server_create(const imce_server_opts *o, imce_server **s);
+/* imce_open(g, opts) into a new tenant; g is copied; *tenant = its index. */
+mce_status imce_server_add_tenant(imce_server *s, const mce_graph *g, const mce_opts *opts, int32_t *tenant);
+/* Queue k raw pairs (host arrays, copied before return) for a tenant.  The
+ * batch arrives at arrival_ms on the server clock (ms since create or the
+ * last reset; negative or past = now).  Returns at once; *id names it. */
+mce_status imce_server_submit(imce_server *s, int32_t tenant, const int32_t *u, const int32_t *v, int64_t k,
+                              double arrival_ms, int64_t *id);
+/* Block until batch `id` has finished; returns its status. */
+mce_status imce_server_wait(imce_server *s, int64_t id, imce_request_info *info);
+/* Block until every submitted batch has finished. */
+mce_status imce_server_drain(imce_server *s);
+/* Drain, then restart the clock at 0 and the statistics. */
+mce_status imce_server_reset_clock(imce_server *s);
+/* Statistics over the batches finished since create or the last reset. */
+mce_status imce_server_stats_get(imce_server *s, imce_server_stats *st);
+/* The tenant's state (owned by the server; use only while it is idle). */
+imce_state *imce_server_tenant(imce_server *s, int32_t tenant);
+/* Drain, stop the workers and close every tenant. */
+void imce_server_free(imce_server *s);
 
 /* ---------------------------------------------------------------- no-allocation entry point */
 

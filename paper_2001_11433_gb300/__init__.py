@@ -99,6 +99,55 @@ class DeltaC(ctypes.Structure):
     ]
 
 
+EXEC_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_int64, ctypes.POINTER(DeltaC))
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [
+        ("slots", ctypes.c_int32),
+        ("mem_budget", ctypes.c_uint64),
+        ("mem_fixed", ctypes.c_uint64),
+        ("execute", EXEC_FN),
+        ("execute_ctx", ctypes.c_void_p),
+    ]
+
+
+class RequestInfoC(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_int64),
+        ("tenant", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("edges", ctypes.c_int64),
+        ("arrival_ms", ctypes.c_double),
+        ("admit_ms", ctypes.c_double),
+        ("done_ms", ctypes.c_double),
+        ("reserved", ctypes.c_uint64),
+        ("delta", DeltaC),
+    ]
+
+
+class ServerStatsC(ctypes.Structure):
+    _fields_ = [
+        ("completed", ctypes.c_int64),
+        ("failed", ctypes.c_int64),
+        ("edges", ctypes.c_int64),
+        ("applied", ctypes.c_int64),
+        ("new_cliques", ctypes.c_uint64),
+        ("subsumed_cliques", ctypes.c_uint64),
+        ("p50_ms", ctypes.c_double),
+        ("p99_ms", ctypes.c_double),
+        ("max_ms", ctypes.c_double),
+        ("wait_p50_ms", ctypes.c_double),
+        ("wait_p99_ms", ctypes.c_double),
+        ("span_ms", ctypes.c_double),
+        ("edges_per_s", ctypes.c_double),
+        ("max_in_flight", ctypes.c_int32),
+        ("peak_reserved", ctypes.c_uint64),
+        ("mem_budget", ctypes.c_uint64),
+    ]
+
+
 # (name, argtypes, restype) of every exported symbol of include/mce.h
 _vp, _i32, _i64, _u64, _f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float
 _P = ctypes.POINTER
@@ -124,7 +173,22 @@ SIGNATURES = {
     "mce_model_train": ([_vp, _vp, _vp, _i32, _i32, _i32, _f32, _u64, _vp, _P(_f32)], _i32),
     "mce_model_predict": ([_vp, _vp, _i32, _i32, _vp, _vp], _i32),
     "mce_enumerate_batched": ([_vp, _vp, _i32, _P(Opts), _vp, _vp, _vp, _P(ResultC)], _i32),
+    "mce_batched_create": ([_vp, _vp, _i32, _P(Opts), _P(_vp)], _i32),
+    "mce_batched_run": ([_vp, _vp], _i32),
+    "mce_batched_read": ([_vp, _vp, _vp, _vp, _vp, _P(ResultC)], _i32),
+    "mce_batched_tune": ([_vp, _vp, _u64, _i32, _P(_i32), _P(ctypes.c_uint32)], _i32),
+    "mce_batched_free": ([_vp], None),
     "imce_open": ([_vp, _P(Opts), _P(_vp)], _i32),
+    "imce_server_opts_init": ([_P(ServerOpts)], None),
+    "imce_server_create": ([_P(ServerOpts), _P(_vp)], _i32),
+    "imce_server_add_tenant": ([_vp, _vp, _P(Opts), _P(_i32)], _i32),
+    "imce_server_submit": ([_vp, _i32, _vp, _vp, _i64, ctypes.c_double, _P(_i64)], _i32),
+    "imce_server_wait": ([_vp, _i64, _P(RequestInfoC)], _i32),
+    "imce_server_drain": ([_vp], _i32),
+    "imce_server_reset_clock": ([_vp], _i32),
+    "imce_server_stats_get": ([_vp, _P(ServerStatsC)], _i32),
+    "imce_server_tenant": ([_vp, _i32], _vp),
+    "imce_server_free": ([_vp], None),
     "imce_add_edges": ([_vp, _vp, _vp, _i64, _i32, _P(DeltaC)], _i32),
     "imce_graph": ([_vp], _vp),
     "imce_cliques": ([_vp, _vp, _vp, _i64, _i64, _P(_i64), _P(_i64)], _i32),
@@ -427,6 +491,52 @@ def enumerate_batched(g: Graph, graph_ptr, allow=(MCE_OK, MCE_EBUDGET), **kw):
     return u64(counts), u64(hashes), status[:k].cpu().numpy(), _result(r, st)
 
 
+class BatchedPlan:
+    """mce_batched_*: prepared once, each run captured into / replayed from a CUDA graph."""
+
+    def __init__(self, g: Graph, graph_ptr, **kw):
+        self.k = len(graph_ptr) - 1
+        self._gptr = np.ascontiguousarray(graph_ptr, dtype=np.int32)
+        self._g = g                               # the plan points into g
+        o = make_opts(**kw)
+        h = ctypes.c_void_p()
+        _check(load().mce_batched_create(g._h, self._gptr.ctypes.data, self.k, ctypes.byref(o), ctypes.byref(h)),
+               "mce_batched_create")
+        self._h = h
+        self._stream = kw.get("stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mce_batched_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self):
+        _check(load().mce_batched_run(self._h, _stream_ptr(self._stream)), "mce_batched_run")
+
+    def read(self):
+        counts = np.zeros(self.k, np.uint64)
+        hashes = np.zeros(self.k, np.uint64)
+        status = np.zeros(self.k, np.int32)
+        r = ResultC()
+        st = load().mce_batched_read(self._h, _stream_ptr(self._stream), counts.ctypes.data, hashes.ctypes.data,
+                                     status.ctypes.data, ctypes.byref(r))
+        if st not in (MCE_OK, MCE_EBUDGET):
+            _check(st, "mce_batched_read")
+        return counts, hashes, status, _result(r, st)
+
+    def tune(self, tune_budget=0, repeats=1):
+        bps, sp = ctypes.c_int32(), ctypes.c_uint32()
+        _check(load().mce_batched_tune(self._h, _stream_ptr(self._stream), tune_budget, repeats, ctypes.byref(bps),
+                                       ctypes.byref(sp)), "mce_batched_tune")
+        return int(bps.value), int(sp.value)
+
+
 @dataclass
 class Delta:
     applied: int
@@ -439,6 +549,12 @@ class Delta:
     sub_hist: np.ndarray
     alive: int
     ms: float
+
+
+def _delta(d: DeltaC) -> Delta:
+    return Delta(int(d.applied), int(d.dropped), int(d.new_count), int(d.new_hash), int(d.sub_count),
+                 int(d.sub_hash), np.array(d.new_hist[: d.new_hist_len], dtype=np.uint64),
+                 np.array(d.sub_hist[: d.sub_hist_len], dtype=np.uint64), int(d.alive), float(d.ms))
 
 
 class Imce:
@@ -470,9 +586,7 @@ class Imce:
         d = DeltaC()
         _check(load().imce_add_edges(self._h, _ptr(u), _ptr(v), len(u), int(on_dev), ctypes.byref(d)),
                "imce_add_edges")
-        return Delta(int(d.applied), int(d.dropped), int(d.new_count), int(d.new_hash), int(d.sub_count),
-                     int(d.sub_hash), np.array(d.new_hist[: d.new_hist_len], dtype=np.uint64),
-                     np.array(d.sub_hist[: d.sub_hist_len], dtype=np.uint64), int(d.alive), float(d.ms))
+        return _delta(d)
 
     def graph(self) -> Graph:
         return Graph._borrow(load().imce_graph(self._h), self.n)
@@ -483,5 +597,111 @@ class Imce:
         vtx = torch.empty(max(max_words, 1), dtype=torch.int32, device="cuda")
         nc, nw = ctypes.c_int64(), ctypes.c_int64()
         _check(load().imce_cliques(self._h, _ptr(off), _ptr(vtx), max_cliques, max_words, ctypes.byref(nc),
+                                   ctypes.byref(nw)), "imce_cliques")
+        return decode_list(off, vtx, nc.value)
+
+
+@dataclass
+class RequestInfo:
+    id: int
+    tenant: int
+    status: int
+    edges: int
+    arrival_ms: float
+    admit_ms: float
+    done_ms: float
+    reserved: int
+    delta: Delta
+
+
+class Server:
+    """imce_server_*: continuous batching of edge batches over tenants.
+
+    `execute` (tests only) replaces imce_add_edges by a Python callable
+    f(tenant, u, v) -> Delta-like tuple, so the scheduler runs without a GPU."""
+
+    def __init__(self, slots=4, mem_budget=0, mem_fixed=0, execute=None):
+        lib = load()
+        o = ServerOpts()
+        lib.imce_server_opts_init(ctypes.byref(o))
+        o.slots, o.mem_budget, o.mem_fixed = slots, mem_budget, mem_fixed
+        self._cb = None
+        if execute is not None:
+            def tramp(_ctx, tenant, u, v, k, out):
+                try:
+                    ua = np.ctypeslib.as_array(ctypes.cast(u, ctypes.POINTER(ctypes.c_int32)), (k,)).copy() if k else \
+                        np.zeros(0, np.int32)
+                    va = np.ctypeslib.as_array(ctypes.cast(v, ctypes.POINTER(ctypes.c_int32)), (k,)).copy() if k else \
+                        np.zeros(0, np.int32)
+                    st, applied, new_count = execute(tenant, ua, va)
+                    out.contents.applied = applied
+                    out.contents.dropped = k - applied
+                    out.contents.new_count = new_count
+                    return st
+                except Exception:                 # noqa: BLE001 - reported as a failed batch
+                    return MCE_ESTATE
+            self._cb = EXEC_FN(tramp)
+            o.execute = self._cb
+        h = ctypes.c_void_p()
+        _check(lib.imce_server_create(ctypes.byref(o), ctypes.byref(h)), "imce_server_create")
+        self._h = h
+        self._n = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().imce_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_tenant(self, g: Graph | None = None, seed: int = 0, rank="degen") -> int:
+        t = ctypes.c_int32()
+        o = make_opts(rank=rank, seed=seed)
+        _check(load().imce_server_add_tenant(self._h, g._h if g is not None else None, ctypes.byref(o),
+                                             ctypes.byref(t)), "imce_server_add_tenant")
+        self._n.append(g.n if g is not None else 0)
+        return int(t.value)
+
+    def submit(self, tenant: int, u, v, arrival_ms: float = -1.0) -> int:
+        u = np.ascontiguousarray(u, dtype=np.int32)
+        v = np.ascontiguousarray(v, dtype=np.int32)
+        rid = ctypes.c_int64()
+        _check(load().imce_server_submit(self._h, tenant, u.ctypes.data, v.ctypes.data, len(u), float(arrival_ms),
+                                         ctypes.byref(rid)), "imce_server_submit")
+        return int(rid.value)
+
+    def wait(self, rid: int) -> RequestInfo:
+        info = RequestInfoC()
+        st = load().imce_server_wait(self._h, rid, ctypes.byref(info))
+        if st == MCE_EINVAL and info.id != rid:
+            _check(st, "imce_server_wait")
+        return RequestInfo(int(info.id), int(info.tenant), int(info.status), int(info.edges), info.arrival_ms,
+                           info.admit_ms, info.done_ms, int(info.reserved), _delta(info.delta))
+
+    def drain(self):
+        _check(load().imce_server_drain(self._h), "imce_server_drain")
+
+    def reset_clock(self):
+        _check(load().imce_server_reset_clock(self._h), "imce_server_reset_clock")
+
+    def stats(self) -> dict:
+        st = ServerStatsC()
+        _check(load().imce_server_stats_get(self._h, ctypes.byref(st)), "imce_server_stats_get")
+        return {name: getattr(st, name) for name, _ in ServerStatsC._fields_}
+
+    def cliques(self, tenant: int, max_cliques: int, max_words: int):
+        """Alive cliques of an idle tenant (imce_cliques on its state)."""
+        import torch
+        h = load().imce_server_tenant(self._h, tenant)
+        if not h:
+            raise MceError(MCE_EINVAL, "imce_server_tenant: no device state")
+        off = torch.empty(max(max_cliques, 1), dtype=torch.int64, device="cuda")
+        vtx = torch.empty(max(max_words, 1), dtype=torch.int32, device="cuda")
+        nc, nw = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().imce_cliques(h, _ptr(off), _ptr(vtx), max_cliques, max_words, ctypes.byref(nc),
                                    ctypes.byref(nw)), "imce_cliques")
         return decode_list(off, vtx, nc.value)

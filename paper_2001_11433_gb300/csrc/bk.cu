@@ -1,3 +1,4 @@
+#include <atomic>
 // Persistent warp-cooperative Bron-Kerbosch (TTT) engine.
 //
 // One warp runs one search at a time.  A search is either a whole
@@ -1408,21 +1409,31 @@ mce_status init_queue_seq(unsigned long long *seq, int64_t n, cudaStream_t s) {
     return MCE_OK;
 }
 
+mce_status bk_prepare(int32_t warps_per_block, int32_t blocks_per_sm, int32_t smem_words) {
+    // dynamic shared memory above the 48 KB default must be opted into once
+    // per kernel, outside any stream capture
+    static std::atomic<int> granted[3] = {48 * 1024, 48 * 1024, 48 * 1024};
+    const int smem = 512 * 4 + warps_per_block * smem_words * 4;
+    const int t = blocks_per_sm >= 4 ? 2 : (blocks_per_sm == 3 ? 1 : 0);
+    if (smem <= granted[t].load()) return MCE_OK;
+    if (t == 2) MCE_CUDA(cudaFuncSetAttribute(k_bk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    else if (t == 1) MCE_CUDA(cudaFuncSetAttribute(k_bk<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    else MCE_CUDA(cudaFuncSetAttribute(k_bk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int cur = granted[t].load();
+    while (smem > cur && !granted[t].compare_exchange_weak(cur, smem)) {
+    }
+    return MCE_OK;
+}
+
 mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s) {
     const size_t smem = (size_t)512 * 4 + (size_t)warps_per_block * p.smem_words * 4;
     const unsigned blocks = (unsigned)(num_sms() * blocks_per_sm);
+    MCE_TRY(bk_prepare(warps_per_block, blocks_per_sm, p.smem_words));
     // 4 resident blocks of 256 threads leave 64 registers a thread; fewer
     // blocks let the compiler keep the search state in more registers
-    if (blocks_per_sm >= 4) {
-        MCE_CUDA(cudaFuncSetAttribute(k_bk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MCE_LAUNCH(k_bk<4>, blocks, warps_per_block * 32, smem, s, p);
-    } else if (blocks_per_sm == 3) {
-        MCE_CUDA(cudaFuncSetAttribute(k_bk<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MCE_LAUNCH(k_bk<3>, blocks, warps_per_block * 32, smem, s, p);
-    } else {
-        MCE_CUDA(cudaFuncSetAttribute(k_bk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MCE_LAUNCH(k_bk<2>, blocks, warps_per_block * 32, smem, s, p);
-    }
+    if (blocks_per_sm >= 4) MCE_LAUNCH(k_bk<4>, blocks, warps_per_block * 32, smem, s, p);
+    else if (blocks_per_sm == 3) MCE_LAUNCH(k_bk<3>, blocks, warps_per_block * 32, smem, s, p);
+    else MCE_LAUNCH(k_bk<2>, blocks, warps_per_block * 32, smem, s, p);
     return MCE_OK;
 }
 

@@ -131,6 +131,7 @@ __host__ __device__ inline int64_t bk_ws_words(int64_t w, int64_t c, int32_t mod
     return bk_shared_words(w, c) + bk_private_words(w, c, mode);
 }
 
+mce_status bk_prepare(int32_t warps_per_block, int32_t blocks_per_sm, int32_t smem_words);
 mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s);
 mce_status init_queue_seq(unsigned long long *seq, int64_t n, cudaStream_t s);
 

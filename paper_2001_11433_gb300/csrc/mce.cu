@@ -144,6 +144,27 @@ struct EvPair {
 
 }  // namespace
 
+mce_status launch_prepass(const mce_graph *g, const int32_t *up_ptr, uint64_t seed, const float *cost,
+                          unsigned long long *out, int32_t *flag, uint64_t *keys, unsigned long long *reqc,
+                          const int32_t *graph_of, unsigned long long *g_count, unsigned long long *g_hash,
+                          cudaStream_t s) {
+    if (g->n == 0) return MCE_OK;
+    MCE_LAUNCH(k_mce_prepass, grid_for(g->n, 256), 256, 0, s, g->row_ptr, up_ptr, g->n, g->id_bits, seed, cost, out,
+               (unsigned long long *)nullptr, (unsigned long long *)nullptr, (unsigned long long *)nullptr, flag, keys,
+               reqc, graph_of, g_count, g_hash, (int64_t *)nullptr, (int32_t *)nullptr, (int64_t)0, (int64_t)0,
+               (const uint8_t *)nullptr);
+    return MCE_OK;
+}
+
+mce_status launch_order(const int32_t *flag_scan, const uint64_t *keys, int32_t n, int32_t n_act, int32_t idb,
+                        uint64_t *tmp2, int32_t *order, cudaStream_t s) {
+    uint64_t *act = tmp2, *act_tmp = tmp2 + n_act;
+    MCE_LAUNCH(k_gather_active, grid_for(n, 256), 256, 0, s, flag_scan, keys, n, act);
+    MCE_TRY(radix_sort_u64(act, act_tmp, n_act, 64, s));
+    MCE_LAUNCH(k_order_from_keys, grid_for(n_act, 256), 256, 0, s, act, n_act, idb, order);
+    return MCE_OK;
+}
+
 LaunchShape launch_shape(const mce_opts *o) {
     LaunchShape ls;
     ls.warps_per_block = (o && o->warps_per_block > 0) ? o->warps_per_block : 8;

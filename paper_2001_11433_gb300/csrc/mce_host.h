@@ -21,6 +21,16 @@ mce_status read_result(const DevBuf &out, const DevBuf &ctl, cudaStream_t s, mce
 mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, const int32_t *graph_of,
                      unsigned long long *graph_nodes, uint64_t graph_budget, unsigned long long *g_count,
                      unsigned long long *g_hash);
+// prepass of the per-vertex decomposition (trivial subproblems, sizes, order keys)
+mce_status launch_prepass(const mce_graph *g, const int32_t *up_ptr, uint64_t seed, const float *cost,
+                          unsigned long long *out, int32_t *flag, uint64_t *keys, unsigned long long *reqc,
+                          const int32_t *graph_of, unsigned long long *g_count, unsigned long long *g_hash,
+                          cudaStream_t s);
+// order of the non-trivial subproblems from the scanned flags and their keys
+mce_status launch_order(const int32_t *flag_scan, const uint64_t *keys, int32_t n, int32_t n_act, int32_t idb,
+                        uint64_t *tmp2, int32_t *order, cudaStream_t s);
+// move an incremental state to another stream between batches (imce.cu)
+void imce_set_stream(imce_state *S, cudaStream_t s);
 // learned cost model (mlp.cu)
 mce_status model_predict(const mce_model *m, const float *feat, int32_t rows, int32_t bf16, cudaStream_t s,
                          float *out);

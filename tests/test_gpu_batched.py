@@ -58,3 +58,58 @@ def test_batched_rejects_crossing_edges(gpu_lib):
     g = mce.Graph(6, np.array([0, 2], np.int32), np.array([1, 4], np.int32))
     with pytest.raises(mce.MceError):
         mce.enumerate_batched(g, np.array([0, 3, 6], np.int32))
+
+
+def test_plan_replay_and_tune_keep_results(gpu_lib):
+    """mce_batched_*: the captured run and its replays give the oracle's
+    per-graph results; the tuner changes the launch shape, not the results."""
+    mce = gpu_lib
+    u, v, gptr, _ = graphgen.batched_er(300, 4, 120, 0.1, 0.6, 79)
+    g = mce.Graph(int(gptr[-1]), _t(u), _t(v))
+    plan = mce.BatchedPlan(g, gptr)
+    exp = oracle_per_graph(u, v, gptr, range(300))
+    before = mce.kernel_launches()
+    seen = []
+    for _ in range(3):
+        plan.run()
+        counts, hashes, status, tot = plan.read()
+        assert (status == 0).all() and tot.complete
+        for i in range(300):
+            assert (int(counts[i]), int(hashes[i])) == exp[i], i
+        seen.append((tot.count, tot.hash, tot.tree_nodes, list(tot.hist)))
+    assert seen[0] == seen[1] == seen[2]
+    assert mce.kernel_launches() - before == 9      # reset, search, status per run
+    bps, split = plan.tune(tune_budget=0, repeats=1)
+    assert bps in (2, 3, 4) and split in (512, 2048, 8192)
+    plan.run()
+    counts, hashes, status, tot = plan.read()
+    assert (tot.count, tot.hash, tot.tree_nodes, list(tot.hist)) == seen[0]
+    ref = mce.enumerate_batched(g, gptr)
+    assert np.array_equal(ref[0], counts) and np.array_equal(ref[1], hashes)
+    plan.close()
+
+
+def test_plan_budget_and_trivial_graphs(gpu_lib):
+    """Per-graph budget in a plan; a batch of edgeless graphs (no search
+    launch at all) still reports every isolated vertex."""
+    mce = gpu_lib
+    u, v, gptr, _ = graphgen.batched_er(64, 16, 400, 0.1, 0.6, 78)
+    g = mce.Graph(int(gptr[-1]), _t(u), _t(v))
+    plan = mce.BatchedPlan(g, gptr, node_budget=20000)
+    plan.tune(tune_budget=5000, repeats=1)
+    plan.run()
+    counts, hashes, status, tot = plan.read()
+    ref = mce.enumerate_batched(g, gptr, node_budget=20000)
+    assert np.array_equal(status, ref[2])
+    ok = status == 0
+    assert np.array_equal(counts[ok], ref[0][ok]) and np.array_equal(hashes[ok], ref[1][ok])
+    assert not tot.complete
+    plan.close()
+    e = np.zeros(0, np.int32)
+    g0 = mce.Graph(10, e, e)
+    plan0 = mce.BatchedPlan(g0, np.array([0, 3, 10], np.int32))
+    plan0.run()
+    counts, hashes, status, tot = plan0.read()
+    assert list(counts) == [3, 7] and tot.count == 10 and tot.complete
+    assert int(hashes[0]) == sum(O.clique_hash([x]) for x in range(3)) % (1 << 64)
+    plan0.close()
