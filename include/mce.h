@@ -163,6 +163,15 @@ uint64_t mce_kernel_launches(void);
 mce_status mce_graph_create(const int32_t *u, const int32_t *v, int64_t m, int32_t n,
                             int32_t on_device, void *stream, mce_graph **g);
 
+/* Graph from a caller CSR (host if on_device == 0, else device):
+ * row_ptr int32[n+1], col int32[nnz], copied into library memory.  It must
+ * already be a simple undirected graph (Section 3): row_ptr[0] = 0,
+ * row_ptr[n] = nnz, rows strictly increasing, ids in [0, n), no self loop,
+ * (x, y) present iff (y, x) is.  Anything else is MCE_EINVAL with the
+ * failed properties named in mce_last_error(); nothing is repaired. */
+mce_status mce_graph_from_csr(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,
+                              int32_t on_device, void *stream, mce_graph **g);
+
 /* Copy out the CSR: row_ptr int32[n+1] and col int32[nnz] (device
  * pointers owned by the graph, valid until mce_graph_free). */
 mce_status mce_graph_csr(const mce_graph *g, int32_t *n, int64_t *nnz,

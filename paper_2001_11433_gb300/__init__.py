@@ -157,6 +157,7 @@ SIGNATURES = {
     "mce_opts_init": ([_P(Opts)], None),
     "mce_kernel_launches": ([], _u64),
     "mce_graph_create": ([_vp, _vp, _i64, _i32, _i32, _vp, _P(_vp)], _i32),
+    "mce_graph_from_csr": ([_vp, _vp, _i32, _i64, _i32, _vp, _P(_vp)], _i32),
     "mce_graph_csr": ([_vp, _P(_i32), _P(_i64), _P(_vp), _P(_vp)], _i32),
     "mce_graph_copy_csr": ([_vp, _vp, _vp, _i32, _vp], _i32),
     "mce_graph_free": ([_vp], None),
@@ -294,6 +295,25 @@ class Graph:
                                     ctypes.byref(h)), "mce_graph_create")
         self._h, self.n = h, int(n)
         self._owned = True
+
+    @classmethod
+    def from_csr(cls, row_ptr, col, stream=None):
+        """mce_graph_from_csr: a validated copy of a simple undirected CSR."""
+        import torch
+        on_dev = isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda
+        if isinstance(row_ptr, torch.Tensor):
+            row_ptr, col = row_ptr.contiguous(), col.contiguous()
+            assert row_ptr.dtype == torch.int32 and col.dtype == torch.int32
+        else:
+            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+        n = len(row_ptr) - 1
+        h = ctypes.c_void_p()
+        _check(load().mce_graph_from_csr(_ptr(row_ptr), _ptr(col) if len(col) else None, n, len(col), int(on_dev),
+                                         _stream_ptr(stream), ctypes.byref(h)), "mce_graph_from_csr")
+        g = cls.__new__(cls)
+        g._h, g.n, g._owned = h, n, True
+        return g
 
     @classmethod
     def _borrow(cls, handle, n):
@@ -660,9 +680,10 @@ class Server:
 
     def add_tenant(self, g: Graph | None = None, seed: int = 0, rank="degen") -> int:
         t = ctypes.c_int32()
-        o = make_opts(rank=rank, seed=seed)
-        _check(load().imce_server_add_tenant(self._h, g._h if g is not None else None, ctypes.byref(o),
-                                             ctypes.byref(t)), "imce_server_add_tenant")
+        o = make_opts(rank=rank, seed=seed) if g is not None else None
+        _check(load().imce_server_add_tenant(self._h, g._h if g is not None else None,
+                                             ctypes.byref(o) if o is not None else None, ctypes.byref(t)),
+               "imce_server_add_tenant")
         self._n.append(g.n if g is not None else 0)
         return int(t.value)
 

@@ -81,6 +81,34 @@ mce_status mce_graph_create(const int32_t *u, const int32_t *v, int64_t m, int32
     return MCE_OK;
 }
 
+mce_status mce_graph_from_csr(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz, int32_t on_device,
+                              void *stream, mce_graph **g) {
+    if (!g || !row_ptr || n < 0 || n >= (1 << 30) || nnz < 0 || nnz >= ((int64_t)1 << 31) - 1 || (nnz > 0 && !col)) {
+        g_last_error = "mce_graph_from_csr: bad arguments";
+        return MCE_EINVAL;
+    }
+    init_pool_once();
+    cudaStream_t s = (cudaStream_t)stream;
+    mce_graph *gr = new mce_graph();
+    gr->n = n;
+    gr->nnz = nnz;
+    gr->id_bits = bits_for(n > 0 ? (uint64_t)(n - 1) : 0);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    mce_status st = cuda_status(cudaMallocAsync((void **)&gr->row_ptr, ((size_t)n + 1) * 4, s), "cudaMallocAsync");
+    if (st == MCE_OK) st = cuda_status(cudaMallocAsync((void **)&gr->col, ((size_t)nnz + 4) * 4, s), "cudaMallocAsync");
+    if (st == MCE_OK)
+        st = cuda_status(cudaMemcpyAsync(gr->row_ptr, row_ptr, ((size_t)n + 1) * 4, kind, s), "copy row_ptr");
+    if (st == MCE_OK && nnz > 0)
+        st = cuda_status(cudaMemcpyAsync(gr->col, col, (size_t)nnz * 4, kind, s), "copy col");
+    if (st == MCE_OK) st = check_csr(gr, s);
+    if (st != MCE_OK) {
+        mce_graph_free(gr);
+        return st;
+    }
+    *g = gr;
+    return MCE_OK;
+}
+
 mce_status mce_graph_csr(const mce_graph *g, int32_t *n, int64_t *nnz, const int32_t **row_ptr, const int32_t **col) {
     if (!g) return MCE_EINVAL;
     if (n) *n = g->n;

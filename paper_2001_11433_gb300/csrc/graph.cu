@@ -1,3 +1,4 @@
+#include <string>
 // Graph ingest and vertex ranking kernels.
 //
 //   build_csr       simple undirected graph from raw pairs (Section 3; inputs
@@ -261,6 +262,62 @@ __global__ void k_up_fill(const int32_t *__restrict__ row_ptr, const int32_t *__
 }  // namespace
 
 // ------------------------------------------------------------------ host side
+
+namespace {
+
+// Validation of a caller CSR (simple undirected graph): bit 1 row offsets,
+// 2 row not strictly increasing, 4 id outside [0, n), 8 self loop, 16 an
+// entry (x, y) without (y, x).
+__global__ void k_check_csr(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz, int32_t *bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz)) atomicOr(bad, 1);
+    for (int64_t x = t0; x < n; x += stride) {
+        const int32_t r0 = row_ptr[x], r1 = row_ptr[x + 1];
+        if (r0 < 0 || r1 < r0 || (int64_t)r1 > nnz) {
+            atomicOr(bad, 1);
+            continue;
+        }
+        for (int32_t e = r0; e < r1; ++e) {
+            const int32_t y = col[e];
+            if (y < 0 || y >= n) {
+                atomicOr(bad, 4);
+                continue;
+            }
+            if (y == x) atomicOr(bad, 8);
+            if (e > r0 && col[e - 1] >= y) atomicOr(bad, 2);
+            const int32_t q0 = row_ptr[y], q1 = row_ptr[y + 1];
+            if (q0 < 0 || q1 < q0 || (int64_t)q1 > nnz) continue;   // row y is reported itself
+            int32_t lo = q0, hi = q1;
+            while (lo < hi) {
+                const int32_t mid = lo + ((hi - lo) >> 1);
+                if (col[mid] < (int32_t)x) lo = mid + 1; else hi = mid;
+            }
+            if (!(lo < q1 && col[lo] == (int32_t)x)) atomicOr(bad, 16);
+        }
+    }
+}
+
+}  // namespace
+
+mce_status check_csr(const mce_graph *g, cudaStream_t s) {
+    DevBuf bad;
+    MCE_TRY(bad.alloc(4, s));
+    MCE_CUDA(cudaMemsetAsync(bad.p, 0, 4, s));
+    MCE_LAUNCH(k_check_csr, grid_for(g->n > 0 ? g->n : 1, 256), 256, 0, s, g->row_ptr, g->col, g->n, g->nnz,
+               bad.as<int32_t>());
+    int32_t hb = 0;
+    MCE_CUDA(cudaMemcpyAsync(&hb, bad.p, 4, cudaMemcpyDeviceToHost, s));
+    MCE_CUDA(cudaStreamSynchronize(s));
+    if (hb) {
+        g_last_error = std::string("mce_graph_from_csr: not a simple undirected CSR:") +
+                       ((hb & 1) ? " row offsets" : "") + ((hb & 2) ? " row not strictly increasing" : "") +
+                       ((hb & 4) ? " id outside [0, n)" : "") + ((hb & 8) ? " self loop" : "") +
+                       ((hb & 16) ? " not symmetric" : "");
+        return MCE_EINVAL;
+    }
+    return MCE_OK;
+}
 
 mce_status build_csr(const int32_t *u, const int32_t *v, int64_t m, int32_t n, cudaStream_t s, mce_graph *g) {
     g->n = n;

@@ -862,6 +862,8 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
 
 }  // namespace
 
+void imce_set_stream(imce_state *S, cudaStream_t s) { S->s = s; }
+
 }  // namespace mce
 
 using namespace mce;

@@ -29,6 +29,8 @@ mce_status launch_prepass(const mce_graph *g, const int32_t *up_ptr, uint64_t se
 // order of the non-trivial subproblems from the scanned flags and their keys
 mce_status launch_order(const int32_t *flag_scan, const uint64_t *keys, int32_t n, int32_t n_act, int32_t idb,
                         uint64_t *tmp2, int32_t *order, cudaStream_t s);
+// validate a graph built from a caller CSR (graph.cu)
+mce_status check_csr(const mce_graph *g, cudaStream_t s);
 // move an incremental state to another stream between batches (imce.cu)
 void imce_set_stream(imce_state *S, cudaStream_t s);
 // learned cost model (mlp.cu)

@@ -293,3 +293,33 @@ def test_wide_candidate_sets(gpu_lib, hub_degree):
     assert_same_summary(r, o)
     assert r.tree_nodes == o.nodes
     assert np.array_equal(u64(pv[2]), o.per_vertex["nodes"])
+
+
+def test_graph_from_csr_round_trip_and_validation(gpu_lib):
+    """mce_graph_from_csr accepts exactly the simple undirected CSRs (Section 3)."""
+    mce = gpu_lib
+    u, v = graphgen.er(300, 0.05, 31)
+    g = mce.Graph(300, u, v)
+    row, col = g.csr()
+    g2 = mce.Graph.from_csr(row, col)
+    import torch
+    g3 = mce.Graph.from_csr(torch.from_numpy(row).cuda(), torch.from_numpy(col).cuda())
+    r1, r2, r3 = (mce.enumerate_cliques(x, rank="degen") for x in (g, g2, g3))
+    assert (r1.count, r1.hash, r1.tree_nodes) == (r2.count, r2.hash, r2.tree_nodes) == (r3.count, r3.hash,
+                                                                                        r3.tree_nodes)
+    empty = mce.Graph.from_csr(np.zeros(6, np.int32), np.zeros(0, np.int32))
+    assert mce.enumerate_cliques(empty).count == 5
+    # path 0-1-2 as the reference CSR, then one defect at a time
+    ok_row, ok_col = np.array([0, 1, 3, 4], np.int32), np.array([1, 0, 2, 1], np.int32)
+    mce.Graph.from_csr(ok_row, ok_col)
+    bad = {
+        "row offsets": (np.array([0, 1, 3, 5], np.int32), ok_col),
+        "row not strictly increasing": (ok_row, np.array([1, 2, 0, 1], np.int32)),
+        "id outside": (ok_row, np.array([1, 0, 7, 1], np.int32)),
+        "self loop": (np.array([0, 1, 4, 5], np.int32), np.array([1, 0, 1, 2, 1], np.int32)),
+        "not symmetric": (np.array([0, 1, 3, 3], np.int32), np.array([1, 0, 2], np.int32)),
+    }
+    for what, (rp, cl) in bad.items():
+        with pytest.raises(mce.MceError) as e:
+            mce.Graph.from_csr(rp, cl)
+        assert e.value.status == mce.MCE_EINVAL and what in str(e.value), what
