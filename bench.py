@@ -112,6 +112,23 @@ def load_peaks():
 
 
 TREE_CAP = 1 << 24          # nodes per subproblem search tree in the benchmark set
+
+# DRAM bytes (read + write) of one k_bk launch from an ncu capture of this
+# workload (5 % sample, profiles/k_bk_rmat18_sample5pct_full.md), scaled by
+# tree nodes; valid only for the kernel sources it was taken with.
+K_BK_TRAFFIC = {"bytes": 168_209_408, "tree_nodes": 209_045_963,
+                "sha256": {"bk.cu": "14fb1cf01c444619ffd063ad8bdb8214a8df915eb47932690b0ee5231c7ceba0",
+                           "bk.cuh": "2d3e8c6e6f64a2521d9258d956def8cccd8db4f0648f99262ebca92e462d9917"}}
+
+
+def k_bk_traffic(tree_nodes: int):
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2001_11433_gb300", "csrc")
+    for name, digest in K_BK_TRAFFIC["sha256"].items():
+        with open(os.path.join(csrc, name), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None        # the kernel changed since the counters were taken
+    return K_BK_TRAFFIC["bytes"] * tree_nodes / K_BK_TRAFFIC["tree_nodes"]
 CPU_SAMPLE_MAX_CAND = 150    # the CPU baseline samples subproblems with |Γ+(v)| <= this
 
 
@@ -289,7 +306,8 @@ def run_ours(args):
                    "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
         "phases_ms": {"rank": res.ms_rank, "enumerate": res.ms_enum, "search_kernel": float(np.mean(search_ms))},
         "roofline": {"bound": "alu", "kernel": "k_bk (persistent search)", "achieved": achieved, "peak": peak_ops,
-                     "unit": "word-ops/s", "frac": achieved / peak_ops if peak_ops else None, "traffic": None,
+                     "unit": "word-ops/s", "frac": achieved / peak_ops if peak_ops else None,
+                     "traffic": k_bk_traffic(res.tree_nodes), "traffic_unit": "DRAM bytes per launch",
                      "peak_source": f"{POPC_PER_CLK_PER_SM} POPC/clk/SM x {props.multi_processor_count} SMs x "
                                     f"{sm_mhz:.0f} MHz (median SM clock sampled during the run)"},
         "e2e": {"value": world * count / (e2e_ms / 1000.0), "unit": UNIT,

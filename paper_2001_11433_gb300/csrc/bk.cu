@@ -474,7 +474,7 @@ struct Acc {
     unsigned long long wops;                 // per lane: algorithmic word operations
     unsigned long long count, hash, nodes;   // per warp, whole launch
     unsigned long long t_count, t_hash, t_nodes;   // per task
-    unsigned long long t_rep;                      // t_nodes already credited to sub_nodes
+    unsigned long long t_rep;                      // t_nodes already credited to sub_nodes / graph_nodes
     unsigned long long t_split;                    // t_nodes at the last hand-over
 };
 
@@ -612,15 +612,18 @@ __device__ int periodic(const BkParams &P, Ws &s, const Task &T, Acc &acc, int l
                 ab |= 1ULL;
             }
         }
+        // exact node counts per subproblem and per graph: the task's nodes
+        // since the last report (the rest is credited when the task ends), so
+        // "over budget" holds exactly when the whole tree exceeds the budget
+        const unsigned long long delta = acc.t_nodes - acc.t_rep;
+        acc.t_rep = acc.t_nodes;
         if (P.sub_nodes) {
-            const unsigned long long delta = acc.t_nodes - acc.t_rep;
-            acc.t_rep = acc.t_nodes;
             const unsigned long long tot = atomicAdd(&P.sub_nodes[root], delta) + delta;
             if (tot > P.sub_budget) ab |= 16ULL;
         }
         if (P.graph_nodes) {
             const int32_t gg = P.graph_of[P.mode == BK_MCE ? root : P.eu[root]];
-            const unsigned long long tot = atomicAdd(&P.graph_nodes[gg], 64ULL) + 64ULL;
+            const unsigned long long tot = atomicAdd(&P.graph_nodes[gg], delta) + delta;
             if (P.graph_budget && tot > P.graph_budget) ab |= 16ULL;
         }
         if (P.split) {
@@ -1358,6 +1361,8 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
         acc.max_busy += globaltimer_ns() - t0;
         if (lane == 0) {
             if (P.sub_nodes && acc.t_nodes > acc.t_rep) atomicAdd(&P.sub_nodes[T.root], acc.t_nodes - acc.t_rep);
+            if (P.graph_nodes && acc.t_nodes > acc.t_rep)
+                atomicAdd(&P.graph_nodes[P.graph_of[P.mode == BK_MCE ? T.root : P.eu[T.root]]], acc.t_nodes - acc.t_rep);
             if (P.pv_count && P.mode == BK_MCE) {
                 atomicAdd(&P.pv_count[T.root], acc.t_count);
                 atomicAdd(&P.pv_hash[T.root], acc.t_hash);

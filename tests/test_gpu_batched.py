@@ -51,6 +51,17 @@ def test_batched_budget_marks_large_graphs(gpu_lib):
     for i in small:
         assert (int(counts[i]), int(hashes[i])) == exp[i]
     assert not tot.complete
+    # the budget is exact: a graph is over it iff its search trees are larger
+    import torch
+    pv = tuple(torch.zeros(g.n, dtype=torch.int64, device="cuda") for _ in range(3))
+    mce.enumerate_cliques(g, rank="degen", per_vertex=pv)
+    nodes = pv[2].cpu().numpy().view(np.uint64).astype(np.int64)
+    tree = np.array([nodes[gptr[i]:gptr[i + 1]].sum() for i in range(64)])
+    sizes = np.diff(gptr)
+    assert (status[tree <= 20000] == 0).all()
+    assert (status[tree > 20000 + sizes] == mce.MCE_EBUDGET).all()
+    again = mce.enumerate_batched(g, gptr, node_budget=20000)
+    assert np.array_equal(again[2], status)
 
 
 def test_batched_rejects_crossing_edges(gpu_lib):
