@@ -56,6 +56,7 @@ struct Ws {
     int32_t *kpath;               // K path of the current task (local ids)
     int32_t frw;                  // words per frame
     int32_t dcap;                 // frames available
+    uint32_t *piv;                // this warp's pivot scratch in shared memory
 };
 
 __device__ __forceinline__ uint32_t *fr_cand(const Ws &s, int d) { return s.fr + (int64_t)d * s.frw; }
@@ -75,13 +76,13 @@ __device__ __forceinline__ void ws_layout(Ws &s, uint32_t *base, int32_t w, int3
     s.w = w;
     s.c = c;
     s.wc = (c + 31) >> 5;
-    s.S = (s.wc & 1) ? s.wc : s.wc + 1;
+    s.S = (int32_t)bk_row_stride(s.wc);
     s.frw = 4 * s.wc + 4;
     uint32_t *p = base;
     s.gid = reinterpret_cast<int32_t *>(p);
     p += w;
     s.bnd = reinterpret_cast<int32_t *>(p);
-    p += w;
+    p = base + bk_align4(2 * (int64_t)w);
     s.A = p;
     p += (int64_t)w * s.S;
     s.F0 = reinterpret_cast<int32_t *>(p);
@@ -106,13 +107,13 @@ __device__ __forceinline__ void ws_layout_split(Ws &s, uint32_t *shared, uint32_
     s.w = w;
     s.c = c;
     s.wc = (c + 31) >> 5;
-    s.S = (s.wc & 1) ? s.wc : s.wc + 1;
+    s.S = (int32_t)bk_row_stride(s.wc);
     s.frw = 4 * s.wc + 4;
     uint32_t *p = shared + 32;
     s.gid = reinterpret_cast<int32_t *>(p);
     p += w;
     s.bnd = reinterpret_cast<int32_t *>(p);
-    p += w;
+    p = shared + bk_align4(32 + 2 * (int64_t)w);
     s.A = p;
     p += (int64_t)w * s.S;
     s.F0 = reinterpret_cast<int32_t *>(p);
@@ -405,7 +406,7 @@ __device__ void build_imce(const BkParams &P, Ws &s, int32_t i, int lane) {
     // the layout was sized for the bound min(deg); re-derive it for the actual c
     s.c = c;
     s.wc = (c + 31) >> 5;
-    s.S = (s.wc & 1) ? s.wc : s.wc + 1;
+    s.S = (int32_t)bk_row_stride(s.wc);
     s.frw = 4 * s.wc + 4;
     s.w = c;
     s.W = c;
@@ -413,7 +414,7 @@ __device__ void build_imce(const BkParams &P, Ws &s, int32_t i, int lane) {
     {
         uint32_t *p = reinterpret_cast<uint32_t *>(s.gid) + c;
         s.bnd = reinterpret_cast<int32_t *>(p);
-        p += c;
+        p = reinterpret_cast<uint32_t *>(s.gid) + bk_align4(2 * (int64_t)c);
         s.A = p;
         p += (int64_t)c * s.S;
         s.F0 = reinterpret_cast<int32_t *>(p);
@@ -719,10 +720,11 @@ __device__ __forceinline__ uint32_t bcast(const uint32_t (&r)[NR], int k) {
     return __shfl_sync(FULL, (NR == 1 || k < 32) ? r[0] : r[NR - 1], k & 31);
 }
 
+// conf is only live in incremental mode (always empty in static MCE)
 template <int NR>
 __device__ __forceinline__ void frame_store(const Ws &s, int d, int lane, const uint32_t (&rc)[NR],
                                             const uint32_t (&rf)[NR], const uint32_t (&re)[NR],
-                                            const uint32_t (&rx)[NR]) {
+                                            const uint32_t (&rx)[NR], bool with_conf) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int k = lane + 32 * r;
@@ -730,14 +732,14 @@ __device__ __forceinline__ void frame_store(const Ws &s, int d, int lane, const 
             fr_cand(s, d)[k] = rc[r];
             fr_finic(s, d)[k] = rf[r];
             fr_ext(s, d)[k] = re[r];
-            fr_conf(s, d)[k] = rx[r];
+            if (with_conf) fr_conf(s, d)[k] = rx[r];
         }
     }
 }
 
 template <int NR>
 __device__ __forceinline__ void frame_load(const Ws &s, int d, int lane, uint32_t (&rc)[NR], uint32_t (&rf)[NR],
-                                           uint32_t (&re)[NR], uint32_t (&rx)[NR]) {
+                                           uint32_t (&re)[NR], uint32_t (&rx)[NR], bool with_conf) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int k = lane + 32 * r;
@@ -745,7 +747,7 @@ __device__ __forceinline__ void frame_load(const Ws &s, int d, int lane, uint32_
         rc[r] = in ? fr_cand(s, d)[k] : 0u;
         rf[r] = in ? fr_finic(s, d)[k] : 0u;
         re[r] = in ? fr_ext(s, d)[k] : 0u;
-        rx[r] = in ? fr_conf(s, d)[k] : 0u;
+        rx[r] = (in && with_conf) ? fr_conf(s, d)[k] : 0u;
     }
 }
 
@@ -758,9 +760,10 @@ template <int NR>
 __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigned long long *shist, int lane,
                       int &node_tick, uint64_t t_start, int32_t root, int k0, bool enter) {
     const int wc = s.wc;
+    const bool imce = P.mode == BK_IMCE;
     uint32_t rc[NR], rf[NR], re[NR], rx[NR];
     int d = 0;
-    frame_load<NR>(s, 0, lane, rc, rf, re, rx);
+    frame_load<NR>(s, 0, lane, rc, rf, re, rx, imce);
     uint32_t flen = fr_meta(s, 0)[0];
     uint64_t hsum = meta_hsum(fr_meta(s, 0));
     for (;;) {
@@ -790,30 +793,59 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
             {
                 uint32_t best_cnt = 0;
                 int32_t best_gid = 0x7fffffff, best_loc = -1;
-                uint32_t cf[NR];
+                // cand to this warp's shared scratch, read back as 16-byte vectors
+                // beside the 16-byte aligned rows (words wc..S-1 are zero)
+                uint32_t *scand = s.piv;
+                uint16_t *ul = reinterpret_cast<uint16_t *>(s.piv + 64);
 #pragma unroll
-                for (int r = 0; r < NR; ++r) cf[r] = rc[r] | rf[r];
-                for (int k = 0; k < wc; ++k) {
-                    const uint32_t mword = bcast<NR>(cf, k);
-                    if (mword == 0u) continue;
-                    const bool mine = (mword >> lane) & 1u;
-                    const uint32_t *row = s.A + (int64_t)((k << 5) + lane) * s.S;
-                    uint32_t cnt = 0;
-                    for (int t = 0; t < wc; ++t) {
-                        const uint32_t cw = bcast<NR>(rc, t);
-                        if (mine) cnt += __popc(cw & row[t]);
+                for (int r = 0; r < NR; ++r) {
+                    const int k = lane + 32 * r;
+                    if (k < s.S) scand[k] = k < wc ? rc[r] : 0u;
+                }
+                const int S4 = s.S >> 2;
+                const uint4 *cv = reinterpret_cast<const uint4 *>(scand);
+                __syncwarp();
+                // members of cand ∪ finic in increasing local id, listed 16 words
+                // (512 vertices) at a time and counted one member per lane
+                for (int ch = 0; ch < ((wc + 15) >> 4); ++ch) {
+                    const int wi = (ch << 4) + (lane & 15);
+                    const uint32_t src = (NR == 1 || ch < 2) ? (rc[0] | rf[0]) : (rc[NR - 1] | rf[NR - 1]);
+                    uint32_t word = __shfl_sync(FULL, src, wi & 31);
+                    if (lane >= 16 || wi >= wc) word = 0u;
+                    const int pc = __popc(word);
+                    int incl = pc;
+#pragma unroll
+                    for (int o = 1; o < 16; o <<= 1) {
+                        const int y = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= o) incl += y;
                     }
-                    if (mine) {
+                    const int tot = __shfl_sync(FULL, incl, 15);
+                    if (tot == 0) continue;
+                    int pos = incl - pc;
+                    while (word) {
+                        ul[pos++] = (uint16_t)((wi << 5) + __ffs(word) - 1);
+                        word &= word - 1;
+                    }
+                    __syncwarp();
+                    for (int i = lane; i < tot; i += 32) {
+                        const int u = ul[i];
+                        const uint4 *row = reinterpret_cast<const uint4 *>(s.A + (int64_t)u * s.S);
+                        uint32_t cnt = 0;
+                        for (int g = 0; g < S4; ++g) {
+                            const uint4 x = row[g], y = cv[g];
+                            cnt += __popc(x.x & y.x) + __popc(x.y & y.y) + __popc(x.z & y.z) + __popc(x.w & y.w);
+                        }
                         acc.wops += (unsigned long long)wc;
-                        const int u = (k << 5) + lane;
-                        const int32_t g = s.gid[u];
-                        if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
+                        // local ids below c follow the global ids, and a lane meets its
+                        // members in increasing local id: a tie never replaces the best
+                        if (best_loc < 0 || cnt > best_cnt) {
                             best_cnt = cnt;
-                            best_gid = g;
                             best_loc = u;
                         }
                     }
+                    __syncwarp();
                 }
+                if (best_loc >= 0) best_gid = s.gid[best_loc];
                 // F is ordered by bnd = popc(A[u]) >= |cand ∩ A[u]|; once the bound
                 // of the next entries drops below the best count none of them can
                 // win (a tie needs count == best), so the scan stops there.
@@ -829,11 +861,14 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                             take = (uint32_t)s.bnd[u] + 1u >= thr;
                         }
                         if (__any_sync(FULL, take)) {
-                            const uint32_t *row = s.A + (int64_t)u * s.S;
                             uint32_t cnt = 0;
-                            for (int t = 0; t < wc; ++t) {
-                                const uint32_t cw = bcast<NR>(rc, t);
-                                if (take) cnt += __popc(cw & row[t]);
+                            if (take) {
+                                const uint4 *row = reinterpret_cast<const uint4 *>(s.A + (int64_t)u * s.S);
+                                for (int g = 0; g < S4; ++g) {
+                                    const uint4 x = row[g], y = cv[g];
+                                    cnt += __popc(x.x & y.x) + __popc(x.y & y.y) + __popc(x.z & y.z) +
+                                           __popc(x.w & y.w);
+                                }
                             }
                             if (take) {
                                 acc.wops += (unsigned long long)wc;
@@ -866,7 +901,7 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
             enter = false;
             if (++node_tick >= 64) {
                 node_tick = 0;
-                frame_store<NR>(s, d, lane, rc, rf, re, rx);
+                frame_store<NR>(s, d, lane, rc, rf, re, rx, imce);
                 __syncwarp();
                 const int act = periodic(P, s, T, acc, lane, d, root, t_start);
                 if (act) return act;
@@ -891,6 +926,7 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                 }
             }
             if (q < 0) goto pop;
+            const int32_t gq = s.gid[q];   // its latency overlaps the child build
             const int qw = q >> 5;
             const uint32_t qb = 1u << (q & 31);
             const uint32_t *qrow = s.A + (int64_t)q * s.S;
@@ -924,8 +960,8 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                 return 1;
             }
             // parent frame to memory (its meta is unchanged), child meta
-            frame_store<NR>(s, d, lane, rc, rf, re, rx);
-            const uint64_t nh = hsum + vertex_hash(s.gid[q], P.seed);
+            frame_store<NR>(s, d, lane, rc, rf, re, rx, imce);
+            const uint64_t nh = hsum + vertex_hash(gq, P.seed);
             if (lane == 0) {
                 acc.wops += 2ull * (unsigned long long)wc + (unsigned long long)flen;
                 uint32_t *nm = fr_meta(s, d + 1);
@@ -956,7 +992,7 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
             if (a > 0 && a < len) merge_F(s, a, len, lane);
         }
         --d;
-        frame_load<NR>(s, d, lane, rc, rf, re, rx);
+        frame_load<NR>(s, d, lane, rc, rf, re, rx, imce);
         flen = fr_meta(s, d)[0];
         hsum = meta_hsum(fr_meta(s, d));
         enter = false;
@@ -1263,12 +1299,13 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
     const int nw_block = blockDim.x >> 5;
     for (int i = threadIdx.x; i < 256; i += blockDim.x) shist[i] = 0ULL;
     __syncthreads();
-    uint32_t *ws_smem = smem + 512 + (int64_t)wib * P.smem_words;
+    uint32_t *ws_smem = smem + 512 + (int64_t)nw_block * BK_PIV_WORDS + (int64_t)wib * P.smem_words;
     const int64_t gwarp = (int64_t)blockIdx.x * nw_block + wib;
     uint32_t *ws_glob = P.gws + gwarp * P.gws_words;
     uint32_t *taskbuf = P.taskbuf + gwarp * P.slot_words;
     Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     Ws s;
+    s.piv = smem + 512 + (int64_t)wib * BK_PIV_WORDS;
     int32_t built = -1;
     int node_tick = 0;
     bool hungry = false;
@@ -1418,7 +1455,7 @@ mce_status bk_prepare(int32_t warps_per_block, int32_t blocks_per_sm, int32_t sm
     // dynamic shared memory above the 48 KB default must be opted into once
     // per kernel, outside any stream capture
     static std::atomic<int> granted[3] = {48 * 1024, 48 * 1024, 48 * 1024};
-    const int smem = 512 * 4 + warps_per_block * smem_words * 4;
+    const int smem = (int)bk_block_smem_bytes(warps_per_block, smem_words);
     const int t = blocks_per_sm >= 4 ? 2 : (blocks_per_sm == 3 ? 1 : 0);
     if (smem <= granted[t].load()) return MCE_OK;
     if (t == 2) MCE_CUDA(cudaFuncSetAttribute(k_bk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -1431,7 +1468,7 @@ mce_status bk_prepare(int32_t warps_per_block, int32_t blocks_per_sm, int32_t sm
 }
 
 mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s) {
-    const size_t smem = (size_t)512 * 4 + (size_t)warps_per_block * p.smem_words * 4;
+    const size_t smem = (size_t)bk_block_smem_bytes(warps_per_block, p.smem_words);
     const unsigned blocks = (unsigned)(num_sms() * blocks_per_sm);
     MCE_TRY(bk_prepare(warps_per_block, blocks_per_sm, p.smem_words));
     // 4 resident blocks of 256 threads leave 64 registers a thread; fewer

@@ -103,12 +103,27 @@ struct BkParams {
 // then local ids, bounds, bitset rows, the bound-sorted fini list F0, and one
 // bitset over F0 positions per candidate (its lower-ranked neighbours).
 // Rounded to 32 words so that every part starts on a 128-byte line.
+// Bitset rows are ⌈c/32⌉ words padded to a multiple of 4, so that every row
+// starts on a 16-byte boundary and is read as 16-byte vectors.
+__host__ __device__ inline int64_t bk_row_stride(int64_t wc) { return (wc + 3) & ~int64_t(3); }
+__host__ __device__ inline int64_t bk_align4(int64_t x) { return (x + 3) & ~int64_t(3); }
+
 __host__ __device__ inline int64_t bk_shared_words(int64_t w, int64_t c) {
     const int64_t wc = (c + 31) / 32;
-    const int64_t S = (wc & 1) ? wc : wc + 1;
+    const int64_t S = bk_row_stride(wc);
     const int64_t wf = (w - c + 31) / 32;
-    const int64_t words = 32 + 2 * w + w * S + (w - c) + c * wf;
+    const int64_t words = bk_align4(32 + 2 * w) + w * S + (w - c) + c * wf;
     return (words + 31) & ~int64_t(31);
+}
+
+// Per-warp shared-memory scratch of the pivot step: cand (64 words) and
+// the member list of cand ∪ finic (512 16-bit local ids).
+constexpr int BK_PIV_WORDS = 64 + 256;
+
+// Dynamic shared memory of one search block: 256 histogram bins, the pivot
+// scratch of every warp, then the optional per-warp workspace slots.
+__host__ __device__ inline int64_t bk_block_smem_bytes(int32_t warps_per_block, int32_t smem_words) {
+    return (int64_t)512 * 4 + (int64_t)warps_per_block * (BK_PIV_WORDS + smem_words) * 4;
 }
 
 // Frames of the explicit stack: one per clique vertex beyond the seeds,
@@ -119,7 +134,7 @@ __host__ __device__ inline int64_t bk_depth_cap(int64_t c) { return (c < 511 ? c
 // and (incremental mode) the exclusion rows.
 __host__ __device__ inline int64_t bk_private_words(int64_t w, int64_t c, int32_t mode) {
     const int64_t wc = (c + 31) / 32;
-    const int64_t S = (wc & 1) ? wc : wc + 1;
+    const int64_t S = bk_row_stride(wc);
     const int64_t fr = 4 * wc + 4;                  // cand, finic, ext, conf + meta
     int64_t words = 2 * (w - c) + bk_depth_cap(c) * fr + (c + 2) + 8;
     if (mode == BK_IMCE) words += (c + 2) * S;

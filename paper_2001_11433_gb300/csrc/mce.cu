@@ -174,7 +174,7 @@ LaunchShape launch_shape(const mce_opts *o) {
     ls.blocks_per_sm = (o && o->blocks_per_sm > 0) ? o->blocks_per_sm : 2;
     // shared memory per SM is 228 KB with 1 KB reserved per block
     const int64_t per_block = (int64_t)228 * 1024 / ls.blocks_per_sm - 1024;
-    int64_t words = (per_block - 2048) / 4 / ls.warps_per_block;
+    int64_t words = (per_block - 2048) / 4 / ls.warps_per_block - BK_PIV_WORDS;
     words &= ~int64_t(3);
     if (words < 0) words = 0;
     // Measured on GB300: the per-warp workspaces hit L1 more often when no
