@@ -309,7 +309,9 @@ def run_ours(args):
                      "unit": "word-ops/s", "frac": achieved / peak_ops if peak_ops else None,
                      "traffic": k_bk_traffic(res.tree_nodes), "traffic_unit": "DRAM bytes per launch",
                      "peak_source": f"{POPC_PER_CLK_PER_SM} POPC/clk/SM x {props.multi_processor_count} SMs x "
-                                    f"{sm_mhz:.0f} MHz (median SM clock sampled during the run)"},
+                                    f"{sm_mhz:.0f} MHz (median SM clock sampled during the run)",
+                     "work": "per tree node (|cand|+|fini|)*ceil(|cand|/32) pivot AND+POPC words + "
+                             "2*ceil((|cand|+|fini|)/32) per child + |K| per clique, counted by the kernel"},
         "e2e": {"value": world * count / (e2e_ms / 1000.0), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * m + 4 * len(subset_host),
                 "d2h_bytes_per_step": 8 * (16 + 1024) + 8 * 8},

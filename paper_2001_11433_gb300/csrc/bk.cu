@@ -477,11 +477,23 @@ struct Acc {
     unsigned long long t_count, t_hash, t_nodes;   // per task
     unsigned long long t_rep;                      // t_nodes already credited to sub_nodes / graph_nodes
     unsigned long long t_split;                    // t_nodes at the last hand-over
+    unsigned long long maxsize;                    // largest clique emitted (folded in once per warp)
 };
+
+// Algorithmic word operations of one tree node with |cand| = cn and |fini| =
+// fn, `next` of whose children are searched: the pivot counts (cn + fn)
+// members against ⌈cn/32⌉ words, and each child intersects cand and fini
+// (2⌈(cn + fn)/32⌉ words).  Counted once per node, on lane 0.
+__device__ __forceinline__ void count_node_wops(Acc &acc, int lane, int cn, int fn, int next) {
+    if (lane == 0)
+        acc.wops += (unsigned long long)(cn + fn) * (unsigned long long)((cn + 31) >> 5) +
+                    2ull * (unsigned long long)next * (unsigned long long)((cn + fn + 31) >> 5);
+}
 
 __device__ void emit(const BkParams &P, const Ws &s, int32_t root, int32_t k0, int d, uint64_t hsum, Acc &acc,
                      unsigned long long *shist, int lane) {
     const uint32_t size = (uint32_t)(k0 + d);
+    if (lane == 0) acc.wops += size;   // |K| additions of the clique hash
     const uint64_t h = clique_hash_from_sum(hsum, size);
     acc.count++;
     acc.hash += h;
@@ -491,8 +503,8 @@ __device__ void emit(const BkParams &P, const Ws &s, int32_t root, int32_t k0, i
         if (size < 256) atomicAdd(&shist[size], 1ULL);
         else if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
         else atomicOr(&P.out[OUT_FLAGS], 2ULL);
-        atomicMax(&P.out[OUT_MAXSIZE], (unsigned long long)size);
     }
+    if (size > acc.maxsize) acc.maxsize = size;
     if (P.list_off) {
         unsigned long long pos = 0, idx = 0;
         if (lane == 0) {
@@ -600,8 +612,11 @@ struct Task {
 // Budget, abort and splitting checks, made every 64 nodes with the current
 // frame written back to memory.  Returns 0 = go on, 1 = stop the launch,
 // 2 = drop this task (its graph or subproblem is over budget).
-__device__ int periodic(const BkParams &P, Ws &s, const Task &T, Acc &acc, int lane, int d, int32_t root,
-                        uint64_t t_start) {
+// Lane 0 reads the control words and credits node counts; the result is
+// broadcast: returns 1 = stop the launch, 2 = drop this task, 0 = go on with
+// `hungry` = the number of hand-overs wanted (0 = none).
+__device__ int poll(const BkParams &P, Acc &acc, int lane, int32_t root, uint64_t t_start,
+                    unsigned long long &hungry_out) {
     unsigned long long ab = 0, hungry = 0;
     if (lane == 0) {
         if (globaltimer_ns() - t_start > P.max_run_ns) atomicOr(&P.ctl[CTL_ABORT], 2ULL);
@@ -640,20 +655,23 @@ __device__ int periodic(const BkParams &P, Ws &s, const Task &T, Acc &acc, int l
     }
     ab = __shfl_sync(FULL, ab, 0);
     hungry = __shfl_sync(FULL, hungry, 0);
+    hungry_out = hungry;
     if (ab & 3ULL) return 1;
     if (ab & 16ULL) return 2;
-    if (!hungry) return 0;
-    acc.t_split = acc.t_nodes;
-    // shallowest frames with at least two unexplored children; up to four
-    // hand-overs per check when many warps wait
-    int budget = hungry > 4 ? 4 : (int)hungry;
-    for (int dd = 0; dd <= d && budget > 0; ++dd) {
+    if (hungry) acc.t_split = acc.t_nodes;
+    return 0;
+}
+
+// Hand over pending children of the memory frames 0..dmax (shallowest
+// first): at most `budget` records.  Below frame `dcur` a single pending
+// sibling is a whole subtree worth handing over (this warp stays busy in the
+// child it is in); at frame dcur itself at least one child stays here.
+__device__ void donate_mem(const BkParams &P, Ws &s, const Task &T, int lane, int dmax, int dcur, int32_t root,
+                           int &budget) {
+    for (int dd = 0; dd <= dmax && budget > 0; ++dd) {
         const uint32_t *ext = fr_ext(s, dd);
         const int rem = warp_popc(ext, s.wc, lane);
-        // below the current frame a single pending sibling is a whole subtree
-        // worth handing over (this warp stays busy in the child it is in);
-        // at the current frame keep at least one child for this warp
-        if (rem < (dd < d ? 1 : 2)) continue;
+        if (rem < (dd < dcur ? 1 : 2)) continue;
         const int kd = T.kdepth + dd;
         int64_t pos = -1;
         if (lane == 0) pos = queue_claim_push(P);
@@ -696,7 +714,7 @@ __device__ int periodic(const BkParams &P, Ws &s, const Task &T, Acc &acc, int l
                 rb[k] = cand[k] & ~lo;               // cand \ ext_lo
                 rb[s.wc + k] = finic[k] | lo;        // fini ∪ ext_lo
                 rb[2 * s.wc + k] = e & ~lo;          // ext_hi
-                rb[3 * s.wc + k] = conf[k];
+                rb[3 * s.wc + k] = P.mode == BK_IMCE ? conf[k] : 0u;
                 ext2[k] = lo;
             }
             seen += __shfl_sync(FULL, incl, 31);
@@ -711,10 +729,393 @@ __device__ int periodic(const BkParams &P, Ws &s, const Task &T, Acc &acc, int l
         --dd;   // the same frame may still hold two or more children
     }
     __syncwarp();
+}
+
+// Checks made every 64 nodes with the current frame written back to memory.
+// Returns 0 = go on, 1 = stop the launch, 2 = drop this task.
+__device__ int periodic(const BkParams &P, Ws &s, const Task &T, Acc &acc, int lane, int d, int32_t root,
+                        uint64_t t_start) {
+    unsigned long long hungry = 0;
+    const int code = poll(P, acc, lane, root, t_start, hungry);
+    if (code || !hungry) return code;
+    // up to four hand-overs per check when many warps wait
+    int budget = hungry > 4 ? 4 : (int)hungry;
+    donate_mem(P, s, T, lane, d, d, root, budget);
     return 0;
 }
 
 // word k of a set lives in register k / 32 of lane k % 32
+// ------------------------------------------------------------------ small universe in registers
+//
+// Below a node whose candidates number at most 32 and whose fini (finic plus
+// the F list) at most 32, the whole subtree runs on 32-bit masks (the same
+// TTT steps on a relabelled universe):
+//   C = the node's candidates, ascending local id (so ascending global id);
+//   X = its fini vertices (finic members, then the F list).
+// Lane l holds adjC = {k : C_l ~ C_k}, adjX = {k : X_l ~ C_k}, and in
+// incremental mode exclC = {k : (C_l, C_k) is an excluded earlier edge}.
+// A frame is (cand, finc ⊆ C, ext, xs ⊆ X, conf); frame j of the stack is
+// kept in the registers of lane j, with the C index q that created it.
+// Hand-overs turn a mask frame back into a task record over the
+// subproblem's columns (the receiver rebuilds F from the path).
+
+struct SmallU {
+    int32_t cidC, cidX;      // local ids of C_lane, X_lane
+    uint32_t adjC, adjX, exclC;
+    int32_t gC, gX;          // global ids (pivot ties)
+    uint64_t hC;             // h(C_lane)
+    int cn, xn;
+};
+
+struct SmallF {              // this lane's stack slot
+    uint32_t c, f, e, x, k;
+    int32_t q;
+};
+
+// C-index mask -> the lane's words of a bitset over the subproblem's
+// candidate columns (or-ed into w); X members that are columns go to wf
+template <int NR>
+__device__ __forceinline__ void small_to_words(const SmallU &u, uint32_t m, int lane, uint32_t (&w)[NR]) {
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        const int32_t cid = __shfl_sync(FULL, u.cidC, b);
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (lane + 32 * r == (cid >> 5)) w[r] |= 1u << (cid & 31);
+    }
+}
+
+// record of small frame fd (its masks given) with ext split: ext_lo stays
+template <int NR>
+__device__ bool small_donate(const BkParams &P, const Ws &s, const Task &T, const SmallU &u, int lane, int d,
+                             int fd, int ds, const SmallF &mine, int32_t qcur, uint32_t mc, uint32_t mf,
+                             uint32_t mx, uint32_t mk, uint32_t ext, uint32_t &ext_lo, int32_t root) {
+    const int rem = __popc(ext);
+    const int keep = rem / 2;
+    uint32_t lo = 0u, x = ext;
+    for (int t = 0; t < keep; ++t) {
+        const uint32_t bit = x & (0u - x);
+        lo |= bit;
+        x ^= bit;
+    }
+    const int kd = T.kdepth + d + fd;
+    int64_t pos = -1;
+    if (lane == 0) pos = queue_claim_push(P);
+    pos = __shfl_sync(FULL, pos, 0);
+    if (pos < 0) return false;
+    uint32_t *rec = P.arena + (int64_t)((unsigned long long)pos % (unsigned long long)P.qcap) * P.slot_words;
+    if (lane == 0) {
+        rec[0] = (uint32_t)root;
+        rec[1] = (uint32_t)kd;
+    }
+    const int k_out = T.kdepth + d;
+    for (int j0 = 0; j0 < kd; j0 += 32) {
+        const int j = j0 + lane;
+        // small frame m = j - k_out + 1 was created by C index q_m
+        const int m = j - k_out + 1;
+        const int32_t qm_lane = __shfl_sync(FULL, mine.q, m > 0 && m < 32 ? m : 0);
+        const int32_t qm = (m == ds) ? qcur : qm_lane;
+        const int32_t loc_small = __shfl_sync(FULL, u.cidC, (qm >= 0 ? qm : 0) & 31);
+        if (j < kd) {
+            int32_t loc;
+            if (j < T.kdepth) loc = s.kpath[j];
+            else if (j < k_out) loc = (int32_t)fr_meta(s, j - T.kdepth + 1)[1];
+            else loc = loc_small;
+            rec[2 + j] = (uint32_t)loc;
+        }
+    }
+    uint32_t wcand[NR], wfin[NR], wext[NR], wconf[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) wcand[r] = wfin[r] = wext[r] = wconf[r] = 0u;
+    small_to_words<NR>(u, mc & ~lo, lane, wcand);
+    small_to_words<NR>(u, mf | lo, lane, wfin);
+    small_to_words<NR>(u, ext & ~lo, lane, wext);
+    if (P.mode == BK_IMCE) small_to_words<NR>(u, mk, lane, wconf);
+    // X members that are candidate columns (finic of the small root) stay fini
+    uint32_t xm = mx;
+    while (xm) {
+        const int b = __ffs(xm) - 1;
+        xm &= xm - 1;
+        const int32_t cid = __shfl_sync(FULL, u.cidX, b);
+        if (cid < s.c) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                if (lane + 32 * r == (cid >> 5)) wfin[r] |= 1u << (cid & 31);
+        }
+    }
+    uint32_t *rb = rec + 2 + kd;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int k = lane + 32 * r;
+        if (k < s.wc) {
+            rb[k] = wcand[r];
+            rb[s.wc + k] = wfin[r];
+            rb[2 * s.wc + k] = wext[r];
+            rb[3 * s.wc + k] = wconf[r];
+        }
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
+        queue_publish(P, pos);
+        atomicAdd(&P.out[OUT_SPLITS], 1ULL);
+    }
+    ext_lo = lo;
+    return true;
+}
+
+// The subtree of the node at memory depth d (its cand/finic in rc/rf, conf
+// in rx, F list Fd[0..flen)), already counted, with cand not empty.
+// Frames 0..d-1 are in memory.  Returns as search<NR>.
+template <int NR>
+__device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigned long long *shist, int lane,
+                            int &node_tick, uint64_t t_start, int32_t root, int k0, int d, uint64_t hsum,
+                            const uint32_t (&rc)[NR], const uint32_t (&rf)[NR], const uint32_t (&rx)[NR],
+                            const int32_t *Fd, int flen) {
+    const bool imce = P.mode == BK_IMCE;
+    const int wc = s.wc;
+    // ---- relabel: C and X lists in the pivot scratch
+    int32_t *Cl = reinterpret_cast<int32_t *>(s.piv + 64);
+    int32_t *Xl = Cl + 32;
+    SmallU u;
+    {
+        int base_c = 0, base_f = 0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const uint32_t wcw = rc[r], wfw = rf[r];
+            const int pc = __popc(wcw), pf = __popc(wfw);
+            int ic = pc, jf = pf;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, ic, o);
+                const int z = __shfl_up_sync(FULL, jf, o);
+                if (lane >= o) {
+                    ic += y;
+                    jf += z;
+                }
+            }
+            int pcs = base_c + ic - pc, pfs = base_f + jf - pf;
+            uint32_t m = wcw;
+            while (m) {
+                Cl[pcs++] = ((lane + 32 * r) << 5) + __ffs(m) - 1;
+                m &= m - 1;
+            }
+            m = wfw;
+            while (m) {
+                Xl[pfs++] = ((lane + 32 * r) << 5) + __ffs(m) - 1;
+                m &= m - 1;
+            }
+            base_c += __shfl_sync(FULL, ic, 31);
+            base_f += __shfl_sync(FULL, jf, 31);
+        }
+        u.cn = base_c;
+        u.xn = base_f + flen;
+        if (lane < flen) Xl[base_f + lane] = Fd[lane];
+    }
+    __syncwarp();
+    u.cidC = lane < u.cn ? Cl[lane] : 0;
+    u.cidX = lane < u.xn ? Xl[lane] : 0;
+    u.adjC = u.adjX = u.exclC = 0u;
+    {
+        const uint32_t *rowC = s.A + (int64_t)u.cidC * s.S;
+        const uint32_t *rowX = s.A + (int64_t)u.cidX * s.S;
+        const uint32_t *xrow = imce ? s.X + (int64_t)u.cidC * s.S : nullptr;
+        for (int k = 0; k < u.cn; ++k) {
+            const int32_t ck = Cl[k];
+            const int wd = ck >> 5;
+            const uint32_t bit = 1u << (ck & 31);
+            if (lane < u.cn && (rowC[wd] & bit)) u.adjC |= 1u << k;
+            if (lane < u.xn && (rowX[wd] & bit)) u.adjX |= 1u << k;
+            if (imce && lane < u.cn && (xrow[wd] & bit)) u.exclC |= 1u << k;
+        }
+    }
+    u.gC = lane < u.cn ? s.gid[u.cidC] : 0x7fffffff;
+    u.gX = lane < u.xn ? s.gid[u.cidX] : 0x7fffffff;
+    u.hC = lane < u.cn ? vertex_hash(u.gC, P.seed) : 0ULL;
+    uint32_t conf = 0u;
+    if (imce) {
+        const int wd = u.cidC >> 5;
+        uint32_t wv = __shfl_sync(FULL, rx[0], wd & 31);
+        if (NR > 1) {
+            const uint32_t w1 = __shfl_sync(FULL, rx[NR - 1], wd & 31);
+            if (wd >= 32) wv = w1;
+        }
+        conf = __ballot_sync(FULL, lane < u.cn && ((wv >> (u.cidC & 31)) & 1u));
+    }
+    __syncwarp();   // Cl / Xl are scratch again after this point
+    // ---- the search
+    uint32_t cand = u.cn == 32 ? FULL : ((1u << u.cn) - 1u);
+    uint32_t finc = 0u, ext = 0u;
+    uint32_t xs = u.xn == 32 ? FULL : ((1u << u.xn) - 1u);
+    int32_t qcur = -1;
+    uint64_t hs = 0;
+    int ds = 0;
+    SmallF mine = {0u, 0u, 0u, 0u, 0u, -1};
+    bool enter = true, first = true;
+    for (;;) {
+        if (enter) {
+            if (!first) {
+                acc.nodes++;
+                acc.t_nodes++;
+            }
+            first = false;
+            if (imce) {
+                const uint32_t xx = cand & conf;
+                finc |= xx;
+                cand &= ~xx;
+            }
+            if (cand == 0u) {
+                if (finc == 0u && xs == 0u) {
+                    // emit K = seeds + task path + memory path + small path
+                    const uint32_t size = (uint32_t)(k0 + d + ds);
+                    const uint64_t h = clique_hash_from_sum(hsum + hs, size);
+                    if (lane == 0) acc.wops += size;
+                    acc.count++;
+                    acc.hash += h;
+                    acc.t_count++;
+                    acc.t_hash += h;
+                    if (lane == 0) {
+                        if (size < 256) atomicAdd(&shist[size], 1ULL);
+                        else if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
+                        else atomicOr(&P.out[OUT_FLAGS], 2ULL);
+                    }
+                    if (size > acc.maxsize) acc.maxsize = size;
+                    if (P.list_off) {
+                        unsigned long long pos = 0, idx = 0;
+                        if (lane == 0) {
+                            pos = atomicAdd(&P.out[OUT_LIST_WORDS], (unsigned long long)(size + 1));
+                            idx = atomicAdd(&P.out[OUT_LIST_CLIQUES], 1ULL);
+                        }
+                        pos = __shfl_sync(FULL, pos, 0);
+                        idx = __shfl_sync(FULL, idx, 0);
+                        if (idx >= (unsigned long long)P.list_max_cliques ||
+                            pos + size + 1 > (unsigned long long)P.list_max_words) {
+                            if (lane == 0) atomicOr(&P.out[OUT_FLAGS], 1ULL);
+                        } else {
+                            int32_t *dst = P.list_vtx + pos;
+                            const int nseed = P.mode == BK_MCE ? 1 : 2;
+                            if (lane == 0) {
+                                dst[0] = (int32_t)size;
+                                P.list_off[idx] = (int64_t)pos;
+                                if (P.mode == BK_MCE) {
+                                    dst[1] = root;
+                                } else {
+                                    dst[1] = P.eu[root];
+                                    dst[2] = P.ev[root];
+                                }
+                            }
+                            const int npath = k0 - nseed;
+                            for (int j = lane; j < npath + d; j += 32) {
+                                const int32_t loc = j < npath ? s.kpath[j] : (int32_t)fr_meta(s, j - npath + 1)[1];
+                                dst[1 + nseed + j] = s.gid[loc];
+                            }
+                            // small frame fj (1..ds, up to 32) was created by C index q_fj;
+                            // lane fj-1 writes it
+                            const int fj = lane + 1;
+                            const int32_t qn = __shfl_sync(FULL, mine.q, fj & 31);
+                            const int32_t qj = (fj == ds) ? qcur : qn;
+                            const int32_t gq = __shfl_sync(FULL, u.gC, (qj >= 0 ? qj : 0) & 31);
+                            if (fj <= ds) dst[nseed + npath + d + fj] = gq;
+                        }
+                    }
+                }
+                goto pop;
+            }
+            // ---- pivot over cand ∪ finc (C) and xs (X), ties to the smallest global id
+            {
+                const bool inC = lane < u.cn && (((cand | finc) >> lane) & 1u);
+                const bool inX = lane < u.xn && ((xs >> lane) & 1u);
+                const uint32_t kc = inC ? __popc(cand & u.adjC) + 1u : 0u;
+                const uint32_t kx = inX ? __popc(cand & u.adjX) + 1u : 0u;
+                const bool useX = kx > kc || (kx == kc && kx != 0u && u.gX < u.gC);
+                const uint32_t key = useX ? kx : kc;
+                const int32_t g = useX ? u.gX : u.gC;
+                const uint32_t mx = __reduce_max_sync(FULL, key);
+                const uint32_t mg = __reduce_min_sync(FULL, key == mx ? (uint32_t)g : 0xffffffffu);
+                const uint32_t who = __ballot_sync(FULL, key == mx && (uint32_t)g == mg);
+                const uint32_t adjp = __shfl_sync(FULL, useX ? u.adjX : u.adjC, __ffs(who) - 1);
+                ext = cand & ~adjp;
+                count_node_wops(acc, lane, __popc(cand), __popc(finc) + __popc(xs), __popc(ext));
+            }
+            enter = false;
+            if (++node_tick >= 64) {
+                node_tick = 0;
+                unsigned long long hungry = 0;
+                const int code = poll(P, acc, lane, root, t_start, hungry);
+                if (code) return code;
+                if (hungry) {
+                    int budget = hungry > 4 ? 4 : (int)hungry;
+                    // memory frames above the small root first, then small frames
+                    if (d > 0) donate_mem(P, s, T, lane, d - 1, d, root, budget);
+                    for (int fd = 0; fd <= ds && budget > 0; ++fd) {
+                        const uint32_t fe = fd < ds ? __shfl_sync(FULL, mine.e, fd) : ext;
+                        if (__popc(fe) < (fd < ds ? 1 : 2)) continue;
+                        const uint32_t fc = fd < ds ? __shfl_sync(FULL, mine.c, fd) : cand;
+                        const uint32_t ff = fd < ds ? __shfl_sync(FULL, mine.f, fd) : finc;
+                        const uint32_t fx = fd < ds ? __shfl_sync(FULL, mine.x, fd) : xs;
+                        const uint32_t fk = fd < ds ? __shfl_sync(FULL, mine.k, fd) : conf;
+                        uint32_t lo = fe;
+                        if (!small_donate<NR>(P, s, T, u, lane, d, fd, ds, mine, qcur, fc, ff, fx, fk, fe, lo, root))
+                            break;
+                        if (fd < ds) {
+                            if (lane == fd) mine.e = lo;
+                        } else {
+                            ext = lo;
+                        }
+                        --budget;
+                        --fd;   // the same frame may still hold pending children
+                    }
+                }
+            }
+        }
+        // ---- next child of the current frame
+        {
+            if (ext == 0u) goto pop;
+            const int q = __ffs(ext) - 1;
+            const uint32_t qb = 1u << q;
+            ext &= ~qb;
+            cand &= ~qb;
+            finc |= qb;
+            if (ds >= 32) {   // cannot happen: every frame adds a distinct member of C
+                if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 4ULL);
+                return 1;
+            }
+            if (lane == ds) {
+                mine.c = cand;
+                mine.f = finc;
+                mine.e = ext;
+                mine.x = xs;
+                mine.k = conf;
+                mine.q = qcur;
+            }
+            const uint32_t aq = __shfl_sync(FULL, u.adjC, q);
+            const uint32_t xq = __ballot_sync(FULL, (u.adjX >> q) & 1u);
+            const uint64_t hq = __shfl_sync(FULL, u.hC, q);
+            if (imce) conf |= __shfl_sync(FULL, u.exclC, q);
+            cand &= aq;
+            finc &= aq;
+            xs &= xq;
+            hs += hq;
+            qcur = q;
+            ++ds;
+            enter = true;
+            continue;
+        }
+    pop:
+        if (ds == 0) return 0;
+        hs -= __shfl_sync(FULL, u.hC, qcur);
+        --ds;
+        cand = __shfl_sync(FULL, mine.c, ds);
+        finc = __shfl_sync(FULL, mine.f, ds);
+        ext = __shfl_sync(FULL, mine.e, ds);
+        xs = __shfl_sync(FULL, mine.x, ds);
+        conf = __shfl_sync(FULL, mine.k, ds);
+        qcur = __shfl_sync(FULL, mine.q, ds);
+        enter = false;
+    }
+}
+
 template <int NR>
 __device__ __forceinline__ uint32_t bcast(const uint32_t (&r)[NR], int k) {
     return __shfl_sync(FULL, (NR == 1 || k < 32) ? r[0] : r[NR - 1], k & 31);
@@ -789,6 +1190,27 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                 if (!__any_sync(FULL, anyf) && flen == 0u) emit(P, s, root, k0, d, hsum, acc, shist, lane);
                 goto pop;
             }
+            // ---- at most 32 candidates and 32 fini vertices: the whole subtree in registers
+            int node_cn, node_fn;
+            {
+                int cn = 0, fcn = 0;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    cn += __popc(rc[r]);
+                    fcn += __popc(rf[r]);
+                }
+                cn = __reduce_add_sync(FULL, cn);
+                fcn = __reduce_add_sync(FULL, fcn);
+                node_cn = cn;
+                node_fn = fcn + (int)flen;
+                if (cn <= 32 && fcn + (int)flen <= 32) {
+                    const int32_t *Fd = (T.kdepth == 0 && d == 0) ? s.F0 : s.F;
+                    const int code = search_small<NR>(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, d,
+                                                      hsum, rc, rf, rx, Fd, (int)flen);
+                    if (code) return code;
+                    goto pop;
+                }
+            }
             // ---- pivot: argmax over cand ∪ finic ∪ F of |cand ∩ A[u]|, ties to the smallest id
             {
                 uint32_t best_cnt = 0;
@@ -835,7 +1257,6 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                             const uint4 x = row[g], y = cv[g];
                             cnt += __popc(x.x & y.x) + __popc(x.y & y.y) + __popc(x.z & y.z) + __popc(x.w & y.w);
                         }
-                        acc.wops += (unsigned long long)wc;
                         // local ids below c follow the global ids, and a lane meets its
                         // members in increasing local id: a tie never replaces the best
                         if (best_loc < 0 || cnt > best_cnt) {
@@ -871,7 +1292,6 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                                 }
                             }
                             if (take) {
-                                acc.wops += (unsigned long long)wc;
                                 const int32_t g = s.gid[u];
                                 if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
                                     best_cnt = cnt;
@@ -892,11 +1312,14 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                 const uint32_t who = __ballot_sync(FULL, key_cnt == mx && (uint32_t)best_gid == mg);
                 const int p = __shfl_sync(FULL, best_loc, __ffs(who) - 1);
                 const uint32_t *prow = s.A + (int64_t)p * s.S;
+                int ne = 0;
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     const int k = lane + 32 * r;
                     re[r] = k < wc ? (rc[r] & ~prow[k]) : 0u;
+                    ne += __popc(re[r]);
                 }
+                count_node_wops(acc, lane, node_cn, node_fn, __reduce_add_sync(FULL, ne));
             }
             enter = false;
             if (++node_tick >= 64) {
@@ -963,7 +1386,6 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
             frame_store<NR>(s, d, lane, rc, rf, re, rx, imce);
             const uint64_t nh = hsum + vertex_hash(gq, P.seed);
             if (lane == 0) {
-                acc.wops += 2ull * (unsigned long long)wc + (unsigned long long)flen;
                 uint32_t *nm = fr_meta(s, d + 1);
                 nm[0] = (uint32_t)nfl;
                 nm[1] = (uint32_t)q;
@@ -1032,7 +1454,6 @@ __device__ int search_mem(const BkParams &P, Ws &s, const Task &T, Acc &acc, uns
                 for (int k = 0; k < wc; ++k) {
                     const uint32_t mword = cand[k] | finic[k];
                     if ((mword >> lane) & 1u) {
-                        acc.wops += (unsigned long long)wc;
                         const int u = (k << 5) + lane;
                         const uint32_t *row = s.A + (int64_t)u * s.S;
                         uint32_t cnt = 0;
@@ -1057,7 +1478,6 @@ __device__ int search_mem(const BkParams &P, Ws &s, const Task &T, Acc &acc, uns
                                 const uint32_t *row = s.A + (int64_t)u * s.S;
                                 uint32_t cnt = 0;
                                 for (int t = 0; t < wc; ++t) cnt += __popc(cand[t] & row[t]);
-                                acc.wops += (unsigned long long)wc;
                                 const int32_t g = s.gid[u];
                                 if (best_loc < 0 || cnt > best_cnt || (cnt == best_cnt && g < best_gid)) {
                                     best_cnt = cnt;
@@ -1079,6 +1499,8 @@ __device__ int search_mem(const BkParams &P, Ws &s, const Task &T, Acc &acc, uns
                 const uint32_t *prow = s.A + (int64_t)p * s.S;
                 for (int k = lane; k < wc; k += 32) ext[k] = cand[k] & ~prow[k];
                 __syncwarp();
+                count_node_wops(acc, lane, warp_popc(cand, wc, lane), warp_popc(finic, wc, lane) + flen,
+                                warp_popc(ext, wc, lane));
             }
             enter = false;
             if (++node_tick >= 64) {
@@ -1117,7 +1539,6 @@ __device__ int search_mem(const BkParams &P, Ws &s, const Task &T, Acc &acc, uns
             }
             __syncwarp();
             if (lane == 0) {
-                acc.wops += 2ull * (unsigned long long)wc + (unsigned long long)flen;
                 ext[qw] &= ~qb;
                 cand[qw] &= ~qb;
                 finic[qw] |= qb;
@@ -1303,7 +1724,7 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
     const int64_t gwarp = (int64_t)blockIdx.x * nw_block + wib;
     uint32_t *ws_glob = P.gws + gwarp * P.gws_words;
     uint32_t *taskbuf = P.taskbuf + gwarp * P.slot_words;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     Ws s;
     s.piv = smem + 512 + (int64_t)wib * BK_PIV_WORDS;
     int32_t built = -1;
@@ -1435,6 +1856,7 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
         if (lane == 0) atomicAdd(&P.out[OUT_WORDOPS], w);
     }
     if (lane == 0) {
+        if (acc.maxsize) atomicMax(&P.out[OUT_MAXSIZE], acc.maxsize);
         atomicAdd(&P.out[OUT_COUNT], acc.count);
         atomicAdd(&P.out[OUT_HASH], acc.hash);
         atomicAdd(&P.out[OUT_NODES], acc.nodes);
