@@ -478,6 +478,8 @@ struct Acc {
     unsigned long long t_rep;                      // t_nodes already credited to sub_nodes / graph_nodes
     unsigned long long t_split;                    // t_nodes at the last hand-over
     unsigned long long maxsize;                    // largest clique emitted (folded in once per warp)
+    int tick;                                      // nodes between checks (shorter in the endgame)
+    int give;                                      // hand-overs per check at most
 };
 
 // Algorithmic word operations of one tree node with |cand| = cn and |fini| =
@@ -495,8 +497,6 @@ __device__ void emit(const BkParams &P, const Ws &s, int32_t root, int32_t k0, i
     const uint32_t size = (uint32_t)(k0 + d);
     if (lane == 0) acc.wops += size;   // |K| additions of the clique hash
     const uint64_t h = clique_hash_from_sum(hsum, size);
-    acc.count++;
-    acc.hash += h;
     acc.t_count++;
     acc.t_hash += h;
     if (lane == 0) {
@@ -653,6 +653,17 @@ __device__ int poll(const BkParams &P, Acc &acc, int lane, int32_t root, uint64_
                 qlen < (unsigned long long)P.qcap / 2) hungry = 1;
         }
     }
+    // endgame: every subproblem has been taken and warps wait for pieces; the
+    // busy warps check four times as often and hand over up to 8 per check
+    {
+        bool endgame = false;
+        if (lane == 0 && P.split)
+            endgame = *(volatile unsigned long long *)&P.ctl[CTL_NEXT] >= (unsigned long long)P.n_sub &&
+                      *(volatile unsigned long long *)&P.ctl[CTL_HUNGRY] > 0ULL;
+        endgame = __shfl_sync(FULL, endgame, 0);
+        acc.tick = endgame ? 16 : 64;
+        acc.give = endgame ? 8 : 4;
+    }
     ab = __shfl_sync(FULL, ab, 0);
     hungry = __shfl_sync(FULL, hungry, 0);
     hungry_out = hungry;
@@ -739,7 +750,7 @@ __device__ int periodic(const BkParams &P, Ws &s, const Task &T, Acc &acc, int l
     const int code = poll(P, acc, lane, root, t_start, hungry);
     if (code || !hungry) return code;
     // up to four hand-overs per check when many warps wait
-    int budget = hungry > 4 ? 4 : (int)hungry;
+    int budget = hungry > (unsigned long long)acc.give ? acc.give : (int)hungry;
     donate_mem(P, s, T, lane, d, d, root, budget);
     return 0;
 }
@@ -952,74 +963,74 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
     uint64_t hs = 0;
     int ds = 0;
     SmallF mine = {0u, 0u, 0u, 0u, 0u, -1};
-    bool enter = true, first = true;
+    // nodes and word-ops since the last flush into acc (32-bit, warp-uniform)
+    uint32_t n32 = 0, w32 = 0;
+    auto flush = [&]() {
+        acc.t_nodes += n32;
+        if (lane == 0) acc.wops += w32;
+        n32 = w32 = 0;
+    };
+    // emit K = seeds + task path + memory path + small frames 1..ds + qa + qb
+    auto small_emit = [&](uint32_t size, uint64_t hsm, int qa, int qb) {
+        const uint64_t h = clique_hash_from_sum(hsum + hsm, size);
+        w32 += size;
+        acc.t_count++;
+        acc.t_hash += h;
+        if (lane == 0) {
+            if (size < 256) atomicAdd(&shist[size], 1ULL);
+            else if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
+            else atomicOr(&P.out[OUT_FLAGS], 2ULL);
+        }
+        if (size > acc.maxsize) acc.maxsize = size;
+        if (P.list_off) {
+            unsigned long long pos = 0, idx = 0;
+            if (lane == 0) {
+                pos = atomicAdd(&P.out[OUT_LIST_WORDS], (unsigned long long)(size + 1));
+                idx = atomicAdd(&P.out[OUT_LIST_CLIQUES], 1ULL);
+            }
+            pos = __shfl_sync(FULL, pos, 0);
+            idx = __shfl_sync(FULL, idx, 0);
+            if (idx >= (unsigned long long)P.list_max_cliques || pos + size + 1 > (unsigned long long)P.list_max_words) {
+                if (lane == 0) atomicOr(&P.out[OUT_FLAGS], 1ULL);
+                return;
+            }
+            int32_t *dst = P.list_vtx + pos;
+            const int nseed = P.mode == BK_MCE ? 1 : 2;
+            if (lane == 0) {
+                dst[0] = (int32_t)size;
+                P.list_off[idx] = (int64_t)pos;
+                if (P.mode == BK_MCE) {
+                    dst[1] = root;
+                } else {
+                    dst[1] = P.eu[root];
+                    dst[2] = P.ev[root];
+                }
+            }
+            const int npath = k0 - nseed;
+            for (int j = lane; j < npath + d; j += 32) {
+                const int32_t loc = j < npath ? s.kpath[j] : (int32_t)fr_meta(s, j - npath + 1)[1];
+                dst[1 + nseed + j] = s.gid[loc];
+            }
+            // small frame fj (1..ds, up to 32) was created by C index q_fj; lane fj-1 writes it
+            const int fj = lane + 1;
+            const int32_t qn = __shfl_sync(FULL, mine.q, fj & 31);
+            const int32_t qj = (fj == ds) ? qcur : qn;
+            const int32_t gq = __shfl_sync(FULL, u.gC, (qj >= 0 ? qj : 0) & 31);
+            if (fj <= ds) dst[nseed + npath + d + fj] = gq;
+            const int32_t ga = __shfl_sync(FULL, u.gC, (qa >= 0 ? qa : 0) & 31);
+            const int32_t gb = __shfl_sync(FULL, u.gC, (qb >= 0 ? qb : 0) & 31);
+            if (lane == 0) {
+                if (qa >= 0) dst[nseed + npath + d + ds + 1] = ga;
+                if (qb >= 0) dst[nseed + npath + d + ds + 2] = gb;
+            }
+        }
+    };
+    bool enter = true;
     for (;;) {
         if (enter) {
-            if (!first) {
-                acc.nodes++;
-                acc.t_nodes++;
-            }
-            first = false;
-            if (imce) {
-                const uint32_t xx = cand & conf;
-                finc |= xx;
-                cand &= ~xx;
-            }
+            // (children arrive with the incremental-mode conflict move applied)
             if (cand == 0u) {
-                if (finc == 0u && xs == 0u) {
-                    // emit K = seeds + task path + memory path + small path
-                    const uint32_t size = (uint32_t)(k0 + d + ds);
-                    const uint64_t h = clique_hash_from_sum(hsum + hs, size);
-                    if (lane == 0) acc.wops += size;
-                    acc.count++;
-                    acc.hash += h;
-                    acc.t_count++;
-                    acc.t_hash += h;
-                    if (lane == 0) {
-                        if (size < 256) atomicAdd(&shist[size], 1ULL);
-                        else if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
-                        else atomicOr(&P.out[OUT_FLAGS], 2ULL);
-                    }
-                    if (size > acc.maxsize) acc.maxsize = size;
-                    if (P.list_off) {
-                        unsigned long long pos = 0, idx = 0;
-                        if (lane == 0) {
-                            pos = atomicAdd(&P.out[OUT_LIST_WORDS], (unsigned long long)(size + 1));
-                            idx = atomicAdd(&P.out[OUT_LIST_CLIQUES], 1ULL);
-                        }
-                        pos = __shfl_sync(FULL, pos, 0);
-                        idx = __shfl_sync(FULL, idx, 0);
-                        if (idx >= (unsigned long long)P.list_max_cliques ||
-                            pos + size + 1 > (unsigned long long)P.list_max_words) {
-                            if (lane == 0) atomicOr(&P.out[OUT_FLAGS], 1ULL);
-                        } else {
-                            int32_t *dst = P.list_vtx + pos;
-                            const int nseed = P.mode == BK_MCE ? 1 : 2;
-                            if (lane == 0) {
-                                dst[0] = (int32_t)size;
-                                P.list_off[idx] = (int64_t)pos;
-                                if (P.mode == BK_MCE) {
-                                    dst[1] = root;
-                                } else {
-                                    dst[1] = P.eu[root];
-                                    dst[2] = P.ev[root];
-                                }
-                            }
-                            const int npath = k0 - nseed;
-                            for (int j = lane; j < npath + d; j += 32) {
-                                const int32_t loc = j < npath ? s.kpath[j] : (int32_t)fr_meta(s, j - npath + 1)[1];
-                                dst[1 + nseed + j] = s.gid[loc];
-                            }
-                            // small frame fj (1..ds, up to 32) was created by C index q_fj;
-                            // lane fj-1 writes it
-                            const int fj = lane + 1;
-                            const int32_t qn = __shfl_sync(FULL, mine.q, fj & 31);
-                            const int32_t qj = (fj == ds) ? qcur : qn;
-                            const int32_t gq = __shfl_sync(FULL, u.gC, (qj >= 0 ? qj : 0) & 31);
-                            if (fj <= ds) dst[nseed + npath + d + fj] = gq;
-                        }
-                    }
-                }
+                if (finc == 0u && xs == 0u) small_emit((uint32_t)(k0 + d + ds), hs, -1, -1);
                 goto pop;
             }
             // ---- pivot over cand ∪ finc (C) and xs (X), ties to the smallest global id
@@ -1036,16 +1047,18 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
                 const uint32_t who = __ballot_sync(FULL, key == mx && (uint32_t)g == mg);
                 const uint32_t adjp = __shfl_sync(FULL, useX ? u.adjX : u.adjC, __ffs(who) - 1);
                 ext = cand & ~adjp;
-                count_node_wops(acc, lane, __popc(cand), __popc(finc) + __popc(xs), __popc(ext));
+                const uint32_t t = (uint32_t)(__popc(cand) + __popc(finc) + __popc(xs));
+                w32 += t + 2u * (uint32_t)__popc(ext) * ((t + 31u) >> 5);
             }
             enter = false;
-            if (++node_tick >= 64) {
+            if (++node_tick >= acc.tick) {
                 node_tick = 0;
+                flush();
                 unsigned long long hungry = 0;
                 const int code = poll(P, acc, lane, root, t_start, hungry);
                 if (code) return code;
                 if (hungry) {
-                    int budget = hungry > 4 ? 4 : (int)hungry;
+                    int budget = hungry > (unsigned long long)acc.give ? acc.give : (int)hungry;
                     // memory frames above the small root first, then small frames
                     if (d > 0) donate_mem(P, s, T, lane, d - 1, d, root, budget);
                     for (int fd = 0; fd <= ds && budget > 0; ++fd) {
@@ -1077,8 +1090,47 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
             ext &= ~qb;
             cand &= ~qb;
             finc |= qb;
+            const uint32_t aq = __shfl_sync(FULL, u.adjC, q);
+            const uint32_t xq = __ballot_sync(FULL, (u.adjX >> q) & 1u);
+            const uint64_t hq = __shfl_sync(FULL, u.hC, q);
+            uint32_t cc = cand & aq, cf = finc & aq, cx = xs & xq, ck = conf;
+            if (imce) {
+                // Algorithm 7: a candidate joined to K + q by an earlier new edge moves to fini
+                ck |= __shfl_sync(FULL, u.exclC, q);
+                const uint32_t mv = cc & ck;
+                cf |= mv;
+                cc &= ~mv;
+            }
+            if (cc == 0u) {
+                // the child is a leaf: a maximal clique unless fini is left
+                ++n32;
+                ++node_tick;
+                if (cf == 0u && cx == 0u) small_emit((uint32_t)(k0 + d + ds + 1), hs + hq, q, -1);
+                continue;
+            }
+            if ((cc & (cc - 1u)) == 0u) {
+                // one candidate c: every pivot count is 0 or 1, so the child has one
+                // child of its own ({c}, a maximal clique) unless a fini vertex is
+                // adjacent to c, in which case that vertex is the pivot and there is none
+                const int c = __ffs(cc) - 1;
+                const uint32_t ac = __shfl_sync(FULL, u.adjC, c);
+                const uint32_t xc = __ballot_sync(FULL, (u.adjX >> c) & 1u);
+                const uint32_t t = 1u + (uint32_t)(__popc(cf) + __popc(cx));
+                if ((cf & ac) != 0u || (cx & xc) != 0u) {
+                    ++n32;
+                    ++node_tick;
+                    w32 += t;
+                } else {
+                    n32 += 2;
+                    node_tick += 2;
+                    w32 += t + 2u * ((t + 31u) >> 5);
+                    small_emit((uint32_t)(k0 + d + ds + 2), hs + hq + __shfl_sync(FULL, u.hC, c), q, c);
+                }
+                continue;
+            }
             if (ds >= 32) {   // cannot happen: every frame adds a distinct member of C
                 if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 4ULL);
+                flush();
                 return 1;
             }
             if (lane == ds) {
@@ -1089,28 +1141,29 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
                 mine.k = conf;
                 mine.q = qcur;
             }
-            const uint32_t aq = __shfl_sync(FULL, u.adjC, q);
-            const uint32_t xq = __ballot_sync(FULL, (u.adjX >> q) & 1u);
-            const uint64_t hq = __shfl_sync(FULL, u.hC, q);
-            if (imce) conf |= __shfl_sync(FULL, u.exclC, q);
-            cand &= aq;
-            finc &= aq;
-            xs &= xq;
+            cand = cc;
+            finc = cf;
+            xs = cx;
+            conf = ck;
             hs += hq;
             qcur = q;
             ++ds;
+            ++n32;
             enter = true;
             continue;
         }
     pop:
-        if (ds == 0) return 0;
+        if (ds == 0) {
+            flush();
+            return 0;
+        }
         hs -= __shfl_sync(FULL, u.hC, qcur);
         --ds;
         cand = __shfl_sync(FULL, mine.c, ds);
         finc = __shfl_sync(FULL, mine.f, ds);
         ext = __shfl_sync(FULL, mine.e, ds);
         xs = __shfl_sync(FULL, mine.x, ds);
-        conf = __shfl_sync(FULL, mine.k, ds);
+        if (imce) conf = __shfl_sync(FULL, mine.k, ds);
         qcur = __shfl_sync(FULL, mine.q, ds);
         enter = false;
     }
@@ -1169,7 +1222,6 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
     uint64_t hsum = meta_hsum(fr_meta(s, 0));
     for (;;) {
         if (enter) {
-            acc.nodes++;
             acc.t_nodes++;
             if (P.mode == BK_IMCE) {
                 // Algorithm 7: a candidate joined to K by an earlier new edge cannot extend K
@@ -1322,7 +1374,7 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                 count_node_wops(acc, lane, node_cn, node_fn, __reduce_add_sync(FULL, ne));
             }
             enter = false;
-            if (++node_tick >= 64) {
+            if (++node_tick >= acc.tick) {
                 node_tick = 0;
                 frame_store<NR>(s, d, lane, rc, rf, re, rx, imce);
                 __syncwarp();
@@ -1432,7 +1484,6 @@ __device__ int search_mem(const BkParams &P, Ws &s, const Task &T, Acc &acc, uns
         uint32_t *cand = fr_cand(s, d), *finic = fr_finic(s, d), *ext = fr_ext(s, d);
         uint32_t *meta = fr_meta(s, d);
         if (enter) {
-            acc.nodes++;
             acc.t_nodes++;
             if (P.mode == BK_IMCE) {
                 const uint32_t *conf = fr_conf(s, d);
@@ -1503,7 +1554,7 @@ __device__ int search_mem(const BkParams &P, Ws &s, const Task &T, Acc &acc, uns
                                 warp_popc(ext, wc, lane));
             }
             enter = false;
-            if (++node_tick >= 64) {
+            if (++node_tick >= acc.tick) {
                 node_tick = 0;
                 const int act = periodic(P, s, T, acc, lane, d, root, t_start);
                 if (act) return act;
@@ -1724,13 +1775,14 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
     const int64_t gwarp = (int64_t)blockIdx.x * nw_block + wib;
     uint32_t *ws_glob = P.gws + gwarp * P.gws_words;
     uint32_t *taskbuf = P.taskbuf + gwarp * P.slot_words;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 64, 4};
     Ws s;
     s.piv = smem + 512 + (int64_t)wib * BK_PIV_WORDS;
     int32_t built = -1;
     int node_tick = 0;
     bool hungry = false;
     uint64_t idle_since = 0;
+    unsigned backoff = 500;   // ns between tries while waiting (doubles to 16 us)
     const uint64_t t_start = globaltimer_ns();
     for (;;) {
         // ---- acquire work: queued pieces first, then the next subproblem
@@ -1801,9 +1853,11 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
                 if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
                 break;
             }
-            __nanosleep(2000);
+            __nanosleep(backoff);
+            if (backoff < 16000u) backoff <<= 1;
             continue;
         }
+        backoff = 500;
         if (hungry) {
             hungry = false;
             acc.idle_ns += globaltimer_ns() - idle_since;
@@ -1817,6 +1871,9 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
         const uint64_t t0 = globaltimer_ns();
         const bool go_on = run_task(P, s, T, acc, shist, ws_smem, ws_glob, taskbuf, lane, built, node_tick, t_start);
         acc.max_busy += globaltimer_ns() - t0;
+        acc.count += acc.t_count;
+        acc.hash += acc.t_hash;
+        acc.nodes += acc.t_nodes;
         if (lane == 0) {
             if (P.sub_nodes && acc.t_nodes > acc.t_rep) atomicAdd(&P.sub_nodes[T.root], acc.t_nodes - acc.t_rep);
             if (P.graph_nodes && acc.t_nodes > acc.t_rep)

@@ -6,19 +6,21 @@
 
 namespace mce {
 
-// Control block of one persistent launch (uint64 words).
+// Control block of one persistent launch (uint64 words).  Each word sits on
+// its own 128-byte line: idle warps hammer the queue head while busy warps
+// poll the others.
 enum CtlWord {
-    CTL_NEXT = 0,      // next unclaimed subproblem index
-    CTL_QTAIL = 1,     // ring tickets taken by pushers
-    CTL_QHEAD = 2,     // ring tickets taken by poppers
-    CTL_PENDING = 3,   // subproblems + queued tasks not finished
-    CTL_HUNGRY = 4,    // warps waiting for work
-    CTL_CACHE_TOP = 5, // words of the build cache in use
-    CTL_NODES = 6,     // tree nodes, for the budget
-    CTL_ABORT = 7,     // 1 = budget, 2 = timeout, 4 = workspace too small, 8 = bad task
-    CTL_T_LAST = 8,    // globaltimer when the last subproblem was claimed
-    CTL_T_END = 9,     // latest globaltimer at which a warp left the launch
-    CTL_WORDS = 10
+    CTL_NEXT = 0 * 16,       // next unclaimed subproblem index
+    CTL_QTAIL = 1 * 16,      // ring tickets taken by pushers
+    CTL_QHEAD = 2 * 16,      // ring tickets taken by poppers
+    CTL_PENDING = 3 * 16,    // subproblems + queued tasks not finished
+    CTL_HUNGRY = 4 * 16,     // warps waiting for work
+    CTL_CACHE_TOP = 5 * 16,  // words of the build cache in use
+    CTL_NODES = 6 * 16,      // tree nodes, for the budget
+    CTL_ABORT = 7 * 16,      // 1 = budget, 2 = timeout, 4 = workspace too small, 8 = bad task
+    CTL_T_LAST = 8 * 16,     // globaltimer when the last subproblem was claimed
+    CTL_T_END = 9 * 16,      // latest globaltimer at which a warp left the launch
+    CTL_WORDS = 10 * 16
 };
 
 // Output block (uint64 words); the size histogram follows at OUT_HIST.
