@@ -292,7 +292,7 @@ mce_status mce_batched_create(const mce_graph *g, const int32_t *graph_ptr, int3
     P.seed = opts->hash_seed;
     P.out = b->out.as<unsigned long long>();
     P.split = opts->split;
-    P.split_nodes = opts->split ? (opts->split_nodes ? opts->split_nodes : 2048u) : 0u;
+    P.split_nodes = opts->split ? (opts->split_nodes ? opts->split_nodes : 4096u) : 0u;
     P.max_run_ns = (uint64_t)(opts->time_limit_ms ? opts->time_limit_ms : 600000u) * 1000000ULL;
     P.timeout_ns = 60ULL * 1000000000ULL;
     if (cw > 0) {
@@ -364,7 +364,7 @@ mce_status mce_batched_tune(mce_batched *b, void *stream, uint64_t tune_budget, 
         int32_t bps;
         uint32_t split;
     };
-    const Cand cands[] = {{2, 2048}, {3, 2048}, {4, 2048}, {2, 512}, {2, 8192}};
+    const Cand cands[] = {{3, 4096}, {2, 4096}, {4, 4096}, {3, 2048}, {3, 8192}};
     const uint64_t keep_budget = b->P.graph_budget;
     const LaunchShape keep_ls = b->ls;
     const uint32_t keep_split = b->P.split_nodes;

@@ -765,23 +765,24 @@ __device__ int periodic(const BkParams &P, Ws &s, const Task &T, Acc &acc, int l
 //   X = its fini vertices (finic members, then the F list).
 // Lane l holds adjC = {k : C_l ~ C_k}, adjX = {k : X_l ~ C_k}, and in
 // incremental mode exclC = {k : (C_l, C_k) is an excluded earlier edge}.
-// A frame is (cand, finc ⊆ C, ext, xs ⊆ X, conf); frame j of the stack is
-// kept in the registers of lane j, with the C index q that created it.
+// A frame is (cand, finc ⊆ C, ext, xs ⊆ X, conf); the stack of saved frames
+// lives in the warp's shared scratch.
 // Hand-overs turn a mask frame back into a task record over the
 // subproblem's columns (the receiver rebuilds F from the path).
 
 struct SmallU {
     int32_t cidC, cidX;      // local ids of C_lane, X_lane
     uint32_t adjC, adjX, exclC;
-    int32_t gC, gX;          // global ids (pivot ties)
+    int32_t gC, gX;          // global ids
+    uint32_t tC, tX;         // 127 - (position of the global id among C ∪ X): pivot tie keys
     uint64_t hC;             // h(C_lane)
     int cn, xn;
 };
 
-struct SmallF {              // this lane's stack slot
-    uint32_t c, f, e, x, k;
-    int32_t q;
-};
+// Stack frame j of the small search: 8 words in the warp's shared scratch,
+// [cand, finc, ext, xs, conf, q (C index that created frame j), hsum lo, hi].
+// Every lane stores the same words, so every lane reads back its own store.
+constexpr int SMALL_FRAME = 8;
 
 // C-index mask -> the lane's words of a bitset over the subproblem's
 // candidate columns (or-ed into w); X members that are columns go to wf
@@ -800,7 +801,7 @@ __device__ __forceinline__ void small_to_words(const SmallU &u, uint32_t m, int 
 // record of small frame fd (its masks given) with ext split: ext_lo stays
 template <int NR>
 __device__ bool small_donate(const BkParams &P, const Ws &s, const Task &T, const SmallU &u, int lane, int d,
-                             int fd, int ds, const SmallF &mine, int32_t qcur, uint32_t mc, uint32_t mf,
+                             int fd, int ds, const uint32_t *stk, int32_t qcur, uint32_t mc, uint32_t mf,
                              uint32_t mx, uint32_t mk, uint32_t ext, uint32_t &ext_lo, int32_t root) {
     const int rem = __popc(ext);
     const int keep = rem / 2;
@@ -825,8 +826,7 @@ __device__ bool small_donate(const BkParams &P, const Ws &s, const Task &T, cons
         const int j = j0 + lane;
         // small frame m = j - k_out + 1 was created by C index q_m
         const int m = j - k_out + 1;
-        const int32_t qm_lane = __shfl_sync(FULL, mine.q, m > 0 && m < 32 ? m : 0);
-        const int32_t qm = (m == ds) ? qcur : qm_lane;
+        const int32_t qm = (m == ds) ? qcur : (int32_t)stk[(m > 0 && m < 32 ? m : 0) * SMALL_FRAME + 5];
         const int32_t loc_small = __shfl_sync(FULL, u.cidC, (qm >= 0 ? qm : 0) & 31);
         if (j < kd) {
             int32_t loc;
@@ -944,6 +944,18 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
     u.gC = lane < u.cn ? s.gid[u.cidC] : 0x7fffffff;
     u.gX = lane < u.xn ? s.gid[u.cidX] : 0x7fffffff;
     u.hC = lane < u.cn ? vertex_hash(u.gC, P.seed) : 0ULL;
+    {
+        // C is in increasing global id, so C_l has l smaller ids in C
+        int oc = lane, ox = 0;
+        for (int k = 0; k < u.xn; ++k) {
+            const int32_t gk = __shfl_sync(FULL, u.gX, k);
+            oc += gk < u.gC;
+            ox += gk < u.gX;
+        }
+        for (int k = 0; k < u.cn; ++k) ox += __shfl_sync(FULL, u.gC, k) < u.gX;
+        u.tC = 127u - (uint32_t)oc;
+        u.tX = 127u - (uint32_t)ox;
+    }
     uint32_t conf = 0u;
     if (imce) {
         const int wd = u.cidC >> 5;
@@ -962,7 +974,7 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
     int32_t qcur = -1;
     uint64_t hs = 0;
     int ds = 0;
-    SmallF mine = {0u, 0u, 0u, 0u, 0u, -1};
+    uint32_t *stk = s.piv + 64;   // 32 frames; the relabel lists there are dead now
     // nodes and word-ops since the last flush into acc (32-bit, warp-uniform)
     uint32_t n32 = 0, w32 = 0;
     auto flush = [&]() {
@@ -1013,8 +1025,7 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
             }
             // small frame fj (1..ds, up to 32) was created by C index q_fj; lane fj-1 writes it
             const int fj = lane + 1;
-            const int32_t qn = __shfl_sync(FULL, mine.q, fj & 31);
-            const int32_t qj = (fj == ds) ? qcur : qn;
+            const int32_t qj = (fj == ds) ? qcur : (int32_t)stk[(fj & 31) * SMALL_FRAME + 5];
             const int32_t gq = __shfl_sync(FULL, u.gC, (qj >= 0 ? qj : 0) & 31);
             if (fj <= ds) dst[nseed + npath + d + fj] = gq;
             const int32_t ga = __shfl_sync(FULL, u.gC, (qa >= 0 ? qa : 0) & 31);
@@ -1035,19 +1046,17 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
             }
             // ---- pivot over cand ∪ finc (C) and xs (X), ties to the smallest global id
             {
-                const bool inC = lane < u.cn && (((cand | finc) >> lane) & 1u);
-                const bool inX = lane < u.xn && ((xs >> lane) & 1u);
-                const uint32_t kc = inC ? __popc(cand & u.adjC) + 1u : 0u;
-                const uint32_t kx = inX ? __popc(cand & u.adjX) + 1u : 0u;
-                const bool useX = kx > kc || (kx == kc && kx != 0u && u.gX < u.gC);
-                const uint32_t key = useX ? kx : kc;
-                const int32_t g = useX ? u.gX : u.gC;
+                // key = (count + 1, tie key): distinct for every member, so one
+                // reduction finds the pivot (largest count, then smallest id)
+                const uint32_t cf = cand | finc;
+                const uint32_t kc = ((cf >> lane) & 1u) ? ((__popc(cand & u.adjC) + 1u) << 7) | u.tC : 0u;
+                const uint32_t kx = ((xs >> lane) & 1u) ? ((__popc(cand & u.adjX) + 1u) << 7) | u.tX : 0u;
+                const uint32_t key = kx > kc ? kx : kc;
                 const uint32_t mx = __reduce_max_sync(FULL, key);
-                const uint32_t mg = __reduce_min_sync(FULL, key == mx ? (uint32_t)g : 0xffffffffu);
-                const uint32_t who = __ballot_sync(FULL, key == mx && (uint32_t)g == mg);
-                const uint32_t adjp = __shfl_sync(FULL, useX ? u.adjX : u.adjC, __ffs(who) - 1);
+                const uint32_t who = __ballot_sync(FULL, key == mx);
+                const uint32_t adjp = __shfl_sync(FULL, kx == mx ? u.adjX : u.adjC, __ffs(who) - 1);
                 ext = cand & ~adjp;
-                const uint32_t t = (uint32_t)(__popc(cand) + __popc(finc) + __popc(xs));
+                const uint32_t t = (uint32_t)(__popc(cf) + __popc(xs));
                 w32 += t + 2u * (uint32_t)__popc(ext) * ((t + 31u) >> 5);
             }
             enter = false;
@@ -1062,17 +1071,18 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
                     // memory frames above the small root first, then small frames
                     if (d > 0) donate_mem(P, s, T, lane, d - 1, d, root, budget);
                     for (int fd = 0; fd <= ds && budget > 0; ++fd) {
-                        const uint32_t fe = fd < ds ? __shfl_sync(FULL, mine.e, fd) : ext;
+                        const uint32_t *fr = stk + fd * SMALL_FRAME;
+                        const uint32_t fe = fd < ds ? fr[2] : ext;
                         if (__popc(fe) < (fd < ds ? 1 : 2)) continue;
-                        const uint32_t fc = fd < ds ? __shfl_sync(FULL, mine.c, fd) : cand;
-                        const uint32_t ff = fd < ds ? __shfl_sync(FULL, mine.f, fd) : finc;
-                        const uint32_t fx = fd < ds ? __shfl_sync(FULL, mine.x, fd) : xs;
-                        const uint32_t fk = fd < ds ? __shfl_sync(FULL, mine.k, fd) : conf;
+                        const uint32_t fc = fd < ds ? fr[0] : cand;
+                        const uint32_t ff = fd < ds ? fr[1] : finc;
+                        const uint32_t fx = fd < ds ? fr[3] : xs;
+                        const uint32_t fk = fd < ds ? fr[4] : conf;
                         uint32_t lo = fe;
-                        if (!small_donate<NR>(P, s, T, u, lane, d, fd, ds, mine, qcur, fc, ff, fx, fk, fe, lo, root))
+                        if (!small_donate<NR>(P, s, T, u, lane, d, fd, ds, stk, qcur, fc, ff, fx, fk, fe, lo, root))
                             break;
                         if (fd < ds) {
-                            if (lane == fd) mine.e = lo;
+                            stk[fd * SMALL_FRAME + 2] = lo;
                         } else {
                             ext = lo;
                         }
@@ -1133,13 +1143,10 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
                 flush();
                 return 1;
             }
-            if (lane == ds) {
-                mine.c = cand;
-                mine.f = finc;
-                mine.e = ext;
-                mine.x = xs;
-                mine.k = conf;
-                mine.q = qcur;
+            {
+                uint4 *fp = reinterpret_cast<uint4 *>(stk + ds * SMALL_FRAME);
+                fp[0] = make_uint4(cand, finc, ext, xs);
+                fp[1] = make_uint4(conf, (uint32_t)qcur, (uint32_t)hs, (uint32_t)(hs >> 32));
             }
             cand = cc;
             finc = cf;
@@ -1157,14 +1164,18 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
             flush();
             return 0;
         }
-        hs -= __shfl_sync(FULL, u.hC, qcur);
         --ds;
-        cand = __shfl_sync(FULL, mine.c, ds);
-        finc = __shfl_sync(FULL, mine.f, ds);
-        ext = __shfl_sync(FULL, mine.e, ds);
-        xs = __shfl_sync(FULL, mine.x, ds);
-        if (imce) conf = __shfl_sync(FULL, mine.k, ds);
-        qcur = __shfl_sync(FULL, mine.q, ds);
+        {
+            const uint4 *fp = reinterpret_cast<const uint4 *>(stk + ds * SMALL_FRAME);
+            const uint4 a = fp[0], b = fp[1];
+            cand = a.x;
+            finc = a.y;
+            ext = a.z;
+            xs = a.w;
+            conf = b.x;
+            qcur = (int32_t)b.y;
+            hs = (uint64_t)b.z | ((uint64_t)b.w << 32);
+        }
         enter = false;
     }
 }

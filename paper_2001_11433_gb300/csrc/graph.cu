@@ -74,8 +74,12 @@ __global__ void k_degree_i32(const int32_t *row_ptr, int32_t n, int32_t *d) {
 // fall to <= k are removed at the same level (claimed once by CAS).
 // The seeding scan of a level visits only the vertices still alive after the
 // previous one (a compacted list), so a level costs its alive count, not n.
+// The removal cascade gives each removed vertex a warp (hubs leave at the
+// high levels, where the frontier is short).  Levels that would remove
+// nothing are skipped: the next level is the smallest remaining degree.
 // ctl[0] = removed so far, ctl[1], ctl[2] = lengths of the two frontiers,
-// ctl[3], ctl[4] = lengths of the two alive lists.
+// ctl[3], ctl[4] = lengths of the two alive lists, ctl[5], ctl[6] = smallest
+// remaining degree (one slot per level parity).
 // Every read of a control word is followed by a grid barrier before any
 // thread may change that word, so all threads take the same branches.
 __global__ void k_core_peel(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
@@ -84,24 +88,34 @@ __global__ void k_core_peel(const int32_t *__restrict__ row_ptr, const int32_t *
     cg::grid_group grid = cg::this_grid();
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = tid >> 5, nwarp = nth >> 5;
     int32_t *cur = fa, *nxt = fb, *alive = la, *alive2 = lb;
     int ci = 1, ni = 2, ai = 3, bi = 4;
-    for (int32_t k = 0; k <= n; ++k) {   // a core number never exceeds n - 1
+    int par = 0;
+    for (int32_t k = 0; k <= n;) {   // a core number never exceeds n - 1
         grid.sync();
         const int32_t removed = *(volatile int32_t *)&ctl[0];
         const int32_t na = *(volatile int32_t *)&ctl[ai];
         grid.sync();
         if (removed >= n) break;
+        const int mi = 5 + par;
+        if (tid == 0) ctl[5 + (1 - par)] = 0x7fffffff;   // slot of the next level, untouched in this one
+        int32_t lmin = 0x7fffffff;
         for (int64_t i = tid; i < na; i += nth) {
             const int32_t v = alive[i];
             if (*(volatile int32_t *)&core[v] >= 0) continue;   // removed at an earlier level
-            if (d[v] <= k) {
+            const int32_t dv = d[v];
+            if (dv <= k) {
                 core[v] = k;
                 cur[atomicAdd(&ctl[ci], 1)] = v;
             } else {
                 alive2[atomicAdd(&ctl[bi], 1)] = v;
+                lmin = dv < lmin ? dv : lmin;
             }
         }
+        lmin = __reduce_min_sync(0xffffffffu, lmin);
+        if (lane == 0 && lmin != 0x7fffffff) atomicMin(&ctl[mi], lmin);
         grid.sync();
         if (tid == 0) ctl[ai] = 0;   // read by everyone before the last barrier
         {
@@ -116,15 +130,23 @@ __global__ void k_core_peel(const int32_t *__restrict__ row_ptr, const int32_t *
             const int32_t len = *(volatile int32_t *)&ctl[ci];
             grid.sync();
             if (len == 0) break;
-            for (int64_t i = tid; i < len; i += nth) {
+            int32_t cmin = 0x7fffffff;
+            for (int64_t i = wid; i < len; i += nwarp) {
                 const int32_t x = cur[i];
-                for (int32_t e = row_ptr[x]; e < row_ptr[x + 1]; ++e) {
+                const int32_t e1 = row_ptr[x + 1];
+                for (int32_t e = row_ptr[x] + lane; e < e1; e += 32) {
                     const int32_t w = col[e];
                     if (*(volatile int32_t *)&core[w] >= 0) continue;
                     const int32_t nd = atomicSub(&d[w], 1) - 1;
-                    if (nd <= k && atomicCAS(&core[w], -1, k) == -1) nxt[atomicAdd(&ctl[ni], 1)] = w;
+                    if (nd <= k) {
+                        if (atomicCAS(&core[w], -1, k) == -1) nxt[atomicAdd(&ctl[ni], 1)] = w;
+                    } else {
+                        cmin = nd < cmin ? nd : cmin;
+                    }
                 }
             }
+            cmin = __reduce_min_sync(0xffffffffu, cmin);
+            if (lane == 0 && cmin != 0x7fffffff) atomicMin(&ctl[mi], cmin);
             if (tid == 0) {
                 atomicAdd(&ctl[0], len);
                 ctl[ci] = 0;   // nobody reads ctl[ci] again before the next barrier
@@ -137,6 +159,12 @@ __global__ void k_core_peel(const int32_t *__restrict__ row_ptr, const int32_t *
             ni = ti;
             grid.sync();
         }
+        // every survivor now has a remaining degree > k; the smallest is the
+        // next level that removes anything (slot mi is not written again
+        // before everyone has read it: the next level uses the other slot)
+        const int32_t mn = *(volatile int32_t *)&ctl[mi];
+        k = mn > k + 1 ? mn : k + 1;
+        par ^= 1;
     }
 }
 
@@ -378,9 +406,9 @@ static mce_status core_numbers(const mce_graph *g, cudaStream_t s, int64_t *key)
     MCE_LAUNCH(k_degree_i32, grid_for(n, 256), 256, 0, s, g->row_ptr, n, d.as<int32_t>());
     MCE_LAUNCH(k_iota, grid_for(n, 256), 256, 0, s, la.as<int32_t>(), n);
     MCE_CUDA(cudaMemsetAsync(core.p, 0xff, (size_t)n * sizeof(int32_t), s));
-    MCE_CUDA(cudaMemsetAsync(ctl.p, 0, 8 * sizeof(int32_t), s));
-    const int32_t n0 = n;
-    MCE_CUDA(cudaMemcpyAsync(ctl.as<int32_t>() + 3, &n0, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    // ctl[3] = n alive, ctl[5] = no remaining degree seen yet
+    const int32_t ctl0[8] = {0, 0, 0, n, 0, 0x7fffffff, 0x7fffffff, 0};
+    MCE_CUDA(cudaMemcpyAsync(ctl.p, ctl0, sizeof(ctl0), cudaMemcpyHostToDevice, s));
     int dev = 0, per_sm = 0;
     MCE_CUDA(cudaGetDevice(&dev));
     MCE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_core_peel, 256, 0));
@@ -388,7 +416,8 @@ static mce_status core_numbers(const mce_graph *g, cudaStream_t s, int64_t *key)
         g_last_error = "core_numbers: cooperative kernel does not fit";
         return MCE_ECUDA;
     }
-    unsigned blocks = (unsigned)(num_sms() * per_sm);
+    // few blocks: the many grid barriers cost in proportion to the blocks
+    unsigned blocks = (unsigned)(num_sms() * (per_sm < 2 ? per_sm : 2));
     const int32_t *rp = g->row_ptr, *cl = g->col;
     int32_t *pd = d.as<int32_t>(), *pc = core.as<int32_t>(), *pa = fa.as<int32_t>(), *pb = fb.as<int32_t>(),
             *pla = la.as<int32_t>(), *plb = lb.as<int32_t>(), *pt = ctl.as<int32_t>();

@@ -169,9 +169,9 @@ LaunchShape launch_shape(const mce_opts *o) {
     LaunchShape ls;
     ls.warps_per_block = (o && o->warps_per_block > 0) ? o->warps_per_block : 8;
     if (ls.warps_per_block > 8) ls.warps_per_block = 8;
-    // measured on GB300 (R-MAT 14 and 18): two resident blocks of eight warps,
-    // with the 128-register build of the search kernel, beat three or four
-    ls.blocks_per_sm = (o && o->blocks_per_sm > 0) ? o->blocks_per_sm : 2;
+    // measured on GB300 (R-MAT 18 workload, hand-over every 4096 nodes):
+    // three resident blocks of eight warps (80 registers) beat two (128) and four
+    ls.blocks_per_sm = (o && o->blocks_per_sm > 0) ? o->blocks_per_sm : 3;
     // shared memory per SM is 228 KB with 1 KB reserved per block
     const int64_t per_block = (int64_t)228 * 1024 / ls.blocks_per_sm - 1024;
     int64_t words = (per_block - 2048) / 4 / ls.warps_per_block - BK_PIV_WORDS;
@@ -418,7 +418,7 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
             P.sub_budget = o->subproblem_budget;
         }
         P.split = o->split;
-        P.split_nodes = o->split ? (o->split_nodes ? o->split_nodes : 2048u) : 0u;
+        P.split_nodes = o->split ? (o->split_nodes ? o->split_nodes : 4096u) : 0u;
         P.max_run_ns = (uint64_t)o->time_limit_ms * 1000000ULL;
         // build cache for every subproblem (up to 2^30 words); when it holds them
         // all, a warp's own workspace only needs the private search state

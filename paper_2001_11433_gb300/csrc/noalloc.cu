@@ -246,7 +246,11 @@ extern "C" mce_status mce_enumerate_noalloc(const int32_t *row_ptr, const int32_
     }
     res->subproblems = n_act;
     if (n_act > 0) {
-        const LaunchShape ls = launch_shape(nullptr);
+        // two blocks of eight warps per SM: fewer per-warp workspaces in the fixed scratch
+        mce_opts shape;
+        mce_opts_init(&shape);
+        shape.blocks_per_sm = 2;
+        const LaunchShape ls = launch_shape(&shape);
         const int64_t nwarps = (int64_t)num_sms() * ls.blocks_per_sm * ls.warps_per_block;
         BkParams P{};
         P.mode = BK_MCE;
@@ -261,6 +265,7 @@ extern "C" mce_status mce_enumerate_noalloc(const int32_t *row_ptr, const int32_
         P.out = out;
         P.ctl = ctl;
         P.split = 1;
+        P.split_nodes = 4096;
         P.smem_words = ls.smem_words;
         P.gws_words = (int64_t)hreq[0] > ls.smem_words ? (int64_t)hreq[0] : 16;
         const int64_t cmax = (int64_t)hreq[1];
