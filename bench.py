@@ -17,6 +17,8 @@ ending with the summary (count, histogram, set hash) read back.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batched   # 4,096 disjoint G(n, p), batched plan
   python bench.py --workload serve     # IMCE serving loop, Chung-Lu 500k + 1M stream edges
+  python bench.py --workload ranks     # Chung-Lu 1.7M + planted cliques: rank and enumeration
+                                       # time per rank (degree, degeneracy, triangles, learned)
 
 Under torchrun every rank runs the same workload as an independent replica
 (the per-vertex subproblems need no exchange), the slowest
@@ -467,6 +469,100 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def neighbourhood_cost_labels(mce, g, rounds=4, seed=5):
+    """Training labels for the learned rank key: log(1 + TTT tree nodes) of
+    each sampled vertex's whole neighbourhood (cand = Γ(v), fini = ∅: the cost
+    of v's subproblem if v were ranked lowest).  Section 4.2 ranks a vertex
+    higher the costlier its neighbourhood, so that its own subproblem (the
+    higher-ranked neighbours only) stays small.  Each round takes an
+    independent set S (vertices whose random priority beats all neighbours'),
+    puts S below every other vertex in a user rank and runs the subproblems of
+    S only: each then has its whole neighbourhood as candidates."""
+    import torch
+    n = g.n
+    row, col = g.csr()
+    deg = np.diff(row)
+    rng = np.random.default_rng(seed)
+    done = np.zeros(n, bool)
+    vs, ls = [], []
+    for _ in range(rounds):
+        pri = rng.random(n)
+        pri[done] = 2.0                      # already labelled: never chosen
+        nb_min = np.full(n, 3.0)
+        has = deg > 0
+        nb_min[has] = np.minimum.reduceat(pri[col], row[:-1][has])
+        S = np.nonzero((pri < nb_min) & has & ~done)[0].astype(np.int32)
+        rank = np.empty(n, np.int32)
+        rest = np.setdiff1d(np.arange(n, dtype=np.int32), S, assume_unique=True)
+        rank[S] = np.arange(len(S), dtype=np.int32)
+        rank[rest] = np.arange(len(S), n, dtype=np.int32)
+        pv = tuple(torch.zeros(n, dtype=torch.int64, device="cuda") for _ in range(3))
+        mce.enumerate_cliques(g, rank="user", user_rank=torch.from_numpy(rank).cuda(),
+                              subset=torch.from_numpy(S).cuda(), per_vertex=pv)
+        nodes = pv[2].cpu().numpy()[S].astype(np.float64)
+        vs.append(S)
+        ls.append(np.log1p(nodes).astype(np.float32))
+        done[S] = True
+    return np.concatenate(vs), np.concatenate(ls)
+
+
+def run_ranks(args):
+    """Chung-Lu n = 1.7M (exponent 2.2, w_max 35,000, about 11M edges) plus
+    200 planted cliques of size U[20, 60].  Per rank: rank time (RT) and
+    enumeration time (ET), CUDA events inside the library, median of the timed
+    runs; every rank must give the same clique set (count, hash, histogram).
+    The learned rank uses an MLP 8-64-64-1 trained (FP32, on the GPU) on a
+    smaller Chung-Lu graph of the same family (n = 200,000, another seed) to
+    predict log(1 + search-tree nodes) of a vertex's whole neighbourhood
+    (neighbourhood_cost_labels); inference is BF16."""
+    import torch
+    import graphgen
+    import paper_2001_11433_gb300 as mce
+    mce.load(build_if_missing=False)
+    w = graphgen.chung_lu_planted()
+    g = mce.Graph(w.n, torch.from_numpy(w.u).cuda(), torch.from_numpy(w.v).cuda())
+    # training graph of the same family, another seed, n = 200,000
+    tu, tv, _ = graphgen.chung_lu(200_000, 2.2, 35_000.0 * (200_000 / 1_700_000) ** 0.5, 200_000 * 6.47,
+                                  graphgen.substream_seed(graphgen.BASE_SEED + 103, 0))
+    tg = mce.Graph(200_000, torch.from_numpy(tu).cuda(), torch.from_numpy(tv).cuda())
+    t0 = time.perf_counter()
+    lab_v, lab = neighbourhood_cost_labels(mce, tg, rounds=4, seed=5)
+    feat = mce.features(tg)[torch.from_numpy(lab_v).cuda().long()].contiguous()
+    model = mce.Model(64, seed=3)
+    loss = model.train(feat, torch.from_numpy(lab).cuda(), epochs=60, batch=2048, lr=3e-3, seed=4)
+    train_s = time.perf_counter() - t0
+    out, ref = {}, None
+    for kind in ("degree", "degen", "triangle", "learned"):
+        kw = {"rank": kind, "model": model} if kind == "learned" else {"rank": kind}
+        runs = []
+        for it in range(args.warmup + args.steps):
+            r = mce.enumerate_cliques(g, **kw)
+            if it >= args.warmup:
+                runs.append(r)
+        key = (runs[0].count, runs[0].hash, tuple(runs[0].hist))
+        ref = ref or key
+        assert key == ref, f"{kind}: clique set differs"
+        rt = float(np.median([x.ms_rank for x in runs]))
+        et = float(np.median([x.ms_enum for x in runs]))
+        out[kind] = {"rt_ms": rt, "et_ms": et, "total_ms": rt + et, "cliques_per_s": runs[0].count / ((rt + et) / 1e3),
+                     "tree_nodes": runs[0].tree_nodes, "splits": runs[0].tasks_split}
+    best = min(out, key=lambda k: out[k]["total_ms"])
+    line = {
+        "metric": "MCE wall time (RT + ET) and cliques/s per rank, learned vs degeneracy (bit-exact across ranks)",
+        "value": out["degen"]["cliques_per_s"], "unit": "cliques/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": out["degen"]["total_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32 (features FP32, inference BF16)", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "edge_samples": len(w.u), "cliques": ref[0], "hash": f"{ref[1]:#018x}",
+                   "max_clique": len(ref[2]) - 1, "learned_train": {"graph": "chung-lu n=200000, other seed",
+                                                                    "labels": int(len(lab)), "label": "log1p(tree nodes "
+                                                                    "of the whole neighbourhood)", "epochs": 60,
+                                                                    "final_mse": loss, "seconds": train_s},
+                   "fastest_rank": best},
+        "ranks": out,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -476,7 +572,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--sample", type=float, default=1.0, help="rmat18: timed fraction of the subproblem set")
-    ap.add_argument("--workload", choices=["rmat18", "batched", "serve"], default="rmat18")
+    ap.add_argument("--workload", choices=["rmat18", "batched", "serve", "ranks"], default="rmat18")
     ap.add_argument("--graph-budget", type=int, default=1 << 20, help="batched: tree nodes per graph")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent batches")
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load / saturation throughput")
@@ -485,6 +581,8 @@ def main():
         run_batched(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "ranks":
+        run_ranks(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

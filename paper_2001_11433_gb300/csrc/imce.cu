@@ -759,7 +759,12 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
         P.list_max_words = mw;
         P.split = S->opts.split;
         BkBuffers bb;
-        const LaunchShape ls = launch_shape(&S->opts);
+        // incremental searches start wide (|Γ'(u) ∩ Γ'(v)| candidates) and spend
+        // more of their time in the register-heavy wide search: two resident
+        // blocks per SM (128 registers) measured faster than three
+        mce_opts shape = S->opts;
+        if (shape.blocks_per_sm <= 0) shape.blocks_per_sm = 2;
+        const LaunchShape ls = launch_shape(&shape);
         MCE_TRY(run_bk(P, ls, (int64_t)reqc[0], (int64_t)reqc[1], s, bb));
         unsigned long long c[CTL_WORDS];
         MCE_CUDA(cudaMemcpyAsync(hn, nout.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
