@@ -114,6 +114,10 @@ def load_peaks():
 
 
 TREE_CAP = 1 << 24          # nodes per subproblem search tree in the benchmark set
+# launch shape for this workload, from a sweep on GB300 (2 or 3 resident
+# blocks of 8 warps per SM x hand-over every 2048..16384 nodes): 3 x 4096
+BLOCKS_PER_SM = 3
+SPLIT_NODES = 4096
 
 # DRAM bytes (read + write) of one k_bk launch from an ncu capture of this
 # workload (5 % sample, profiles/k_bk_rmat18_sample5pct_full.md), scaled by
@@ -234,7 +238,8 @@ def run_ours(args):
 
     def step_device():
         g = mce.Graph(w.n, dev_u, dev_v)
-        r = mce.enumerate_cliques(g, rank="degen", subset=dev_subset)
+        r = mce.enumerate_cliques(g, rank="degen", subset=dev_subset, blocks_per_sm=BLOCKS_PER_SM,
+                                  split_nodes=SPLIT_NODES)
         g.close()
         return r
 
@@ -271,7 +276,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g = mce.Graph(w.n, pin_u.numpy(), pin_v.numpy())
-        r2 = mce.enumerate_cliques(g, rank="degen", subset=pin_subset.numpy())
+        r2 = mce.enumerate_cliques(g, rank="degen", subset=pin_subset.numpy(), blocks_per_sm=BLOCKS_PER_SM,
+                                   split_nodes=SPLIT_NODES)
         g.close()
         e2e_times.append((time.perf_counter() - t0) * 1000.0)
     clocks = sampler.stop()
@@ -305,7 +311,8 @@ def run_ours(args):
                    "subproblems_excluded": excluded, "sample_fraction": args.sample, "cliques": count, "hash": f"{res.hash:#018x}",
                    "max_clique": len(res.hist) - 1, "tree_nodes": res.tree_nodes,
                    "tree_nodes_per_s": world * res.tree_nodes / (ms / 1000.0),
-                   "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
+                   "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{world}",
+                   "launch": {"blocks_per_sm": BLOCKS_PER_SM, "warps_per_block": 8, "split_nodes": SPLIT_NODES}},
         "phases_ms": {"rank": res.ms_rank, "enumerate": res.ms_enum, "search_kernel": float(np.mean(search_ms))},
         "roofline": {"bound": "alu", "kernel": "k_bk (persistent search)", "achieved": achieved, "peak": peak_ops,
                      "unit": "word-ops/s", "frac": achieved / peak_ops if peak_ops else None,

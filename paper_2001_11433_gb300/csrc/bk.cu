@@ -648,6 +648,9 @@ __device__ int poll(const BkParams &P, Acc &acc, int lane, int32_t root, uint64_
             const unsigned long long qt = *(volatile unsigned long long *)&P.ctl[CTL_QTAIL];
             const unsigned long long qlen = qt > qh ? qt - qh : 0ULL;
             if (qlen >= hungry) hungry = 0;
+            // a task hands over again only after 2048 more nodes of its own:
+            // pieces cut too small cost their receivers more than they hold
+            if (acc.t_nodes - acc.t_split < 2048ULL) hungry = 0;
             // a long-running task spreads its subtree before anybody waits
             if (!hungry && P.split_nodes && acc.t_nodes - acc.t_split >= P.split_nodes &&
                 qlen < (unsigned long long)P.qcap / 2) hungry = 1;
@@ -783,6 +786,8 @@ struct SmallU {
 // [cand, finc, ext, xs, conf, q (C index that created frame j), hsum lo, hi].
 // Every lane stores the same words, so every lane reads back its own store.
 constexpr int SMALL_FRAME = 8;
+// small frames with fewer candidates than this are not handed over
+constexpr int SMALL_DONATE_MIN_CAND = 8;
 
 // C-index mask -> the lane's words of a bitset over the subproblem's
 // candidate columns (or-ed into w); X members that are columns go to wf
@@ -1075,6 +1080,9 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
                         const uint32_t fe = fd < ds ? fr[2] : ext;
                         if (__popc(fe) < (fd < ds ? 1 : 2)) continue;
                         const uint32_t fc = fd < ds ? fr[0] : cand;
+                        // a piece costs its receiver a rebuild of F along the path and
+                        // a relabel; frames with few candidates hold too little work
+                        if (__popc(fc) < SMALL_DONATE_MIN_CAND) break;
                         const uint32_t ff = fd < ds ? fr[1] : finc;
                         const uint32_t fx = fd < ds ? fr[3] : xs;
                         const uint32_t fk = fd < ds ? fr[4] : conf;

@@ -169,9 +169,10 @@ LaunchShape launch_shape(const mce_opts *o) {
     LaunchShape ls;
     ls.warps_per_block = (o && o->warps_per_block > 0) ? o->warps_per_block : 8;
     if (ls.warps_per_block > 8) ls.warps_per_block = 8;
-    // measured on GB300 (R-MAT 18 workload, hand-over every 4096 nodes):
-    // three resident blocks of eight warps (80 registers) beat two (128) and four
-    ls.blocks_per_sm = (o && o->blocks_per_sm > 0) ? o->blocks_per_sm : 3;
+    // measured on GB300: two resident blocks of eight warps (128 registers)
+    // are the robust choice (Chung-Lu, incremental, sampled R-MAT sets); three
+    // (80 registers) win about 10 % on the full R-MAT 18 set only
+    ls.blocks_per_sm = (o && o->blocks_per_sm > 0) ? o->blocks_per_sm : 2;
     // shared memory per SM is 228 KB with 1 KB reserved per block
     const int64_t per_block = (int64_t)228 * 1024 / ls.blocks_per_sm - 1024;
     int64_t words = (per_block - 2048) / 4 / ls.warps_per_block - BK_PIV_WORDS;
