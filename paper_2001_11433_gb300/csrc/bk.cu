@@ -470,14 +470,20 @@ __device__ void build_imce(const BkParams &P, Ws &s, int32_t i, int lane) {
 
 // ------------------------------------------------------------------ output
 
+// Counters touched a few times per task live in shared memory, one set per
+// warp (lane 0 updates them), to keep registers for the search.
+struct AccCold {
+    unsigned long long build_ns, idle_ns, builds, pieces, max_busy, maxsize;
+};
+__shared__ AccCold g_cold[8];   // warps of one search block
+__device__ __forceinline__ AccCold &cold() { return g_cold[threadIdx.x >> 5]; }
+
 struct Acc {
-    unsigned long long build_ns, search_ns, idle_ns, builds, pieces, max_busy;
     unsigned long long wops;                 // per lane: algorithmic word operations
     unsigned long long count, hash, nodes;   // per warp, whole launch
     unsigned long long t_count, t_hash, t_nodes;   // per task
     unsigned long long t_rep;                      // t_nodes already credited to sub_nodes / graph_nodes
     unsigned long long t_split;                    // t_nodes at the last hand-over
-    unsigned long long maxsize;                    // largest clique emitted (folded in once per warp)
     int tick;                                      // nodes between checks (shorter in the endgame)
     int give;                                      // hand-overs per check at most
 };
@@ -504,7 +510,7 @@ __device__ void emit(const BkParams &P, const Ws &s, int32_t root, int32_t k0, i
         else if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
         else atomicOr(&P.out[OUT_FLAGS], 2ULL);
     }
-    if (size > acc.maxsize) acc.maxsize = size;
+    if (lane == 0 && size > cold().maxsize) cold().maxsize = size;
     if (P.list_off) {
         unsigned long long pos = 0, idx = 0;
         if (lane == 0) {
@@ -981,10 +987,13 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
     int ds = 0;
     uint32_t *stk = s.piv + 64;   // 32 frames; the relabel lists there are dead now
     // nodes and word-ops since the last flush into acc (32-bit, warp-uniform)
-    uint32_t n32 = 0, w32 = 0;
+    uint32_t n32 = 0, w32 = 0, smax = 0;
     auto flush = [&]() {
         acc.t_nodes += n32;
-        if (lane == 0) acc.wops += w32;
+        if (lane == 0) {
+            acc.wops += w32;
+            if (smax > cold().maxsize) cold().maxsize = smax;
+        }
         n32 = w32 = 0;
     };
     // emit K = seeds + task path + memory path + small frames 1..ds + qa + qb
@@ -998,7 +1007,7 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
             else if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
             else atomicOr(&P.out[OUT_FLAGS], 2ULL);
         }
-        if (size > acc.maxsize) acc.maxsize = size;
+        if (size > smax) smax = size;
         if (P.list_off) {
             unsigned long long pos = 0, idx = 0;
             if (lane == 0) {
@@ -1684,8 +1693,10 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
                 __syncwarp();
                 if (lane == 0) atomicExch(reinterpret_cast<unsigned long long *>(P.cache_off + root),
                                           (unsigned long long)off);
-                acc.builds++;
-                acc.build_ns += globaltimer_ns() - tb;
+                if (lane == 0) {
+                    cold().builds++;
+                    cold().build_ns += globaltimer_ns() - tb;
+                }
             } else {
                 s.W = (int32_t)__ldcg(sh);
                 s.f = (int32_t)__ldcg(sh + 1);
@@ -1708,8 +1719,10 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
                 build_imce(P, s, root, lane);
             }
             built = root;
-            acc.builds++;
-            acc.build_ns += globaltimer_ns() - tb;
+            if (lane == 0) {
+                cold().builds++;
+                cold().build_ns += globaltimer_ns() - tb;
+            }
         }
     }
     // ---- frame 0
@@ -1794,7 +1807,8 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
     const int64_t gwarp = (int64_t)blockIdx.x * nw_block + wib;
     uint32_t *ws_glob = P.gws + gwarp * P.gws_words;
     uint32_t *taskbuf = P.taskbuf + gwarp * P.slot_words;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 64, 4};
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 64, 4};
+    if (lane == 0) cold() = AccCold{0, 0, 0, 0, 0, 0};
     Ws s;
     s.piv = smem + 512 + (int64_t)wib * BK_PIV_WORDS;
     int32_t built = -1;
@@ -1867,7 +1881,7 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
                 if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], 1ULL);
             } else if (now - t_start > P.max_run_ns + P.timeout_ns) {
                 if (lane == 0) atomicOr(&P.ctl[CTL_ABORT], 2ULL);
-                acc.idle_ns += now - idle_since;
+                if (lane == 0) cold().idle_ns += now - idle_since;
                 hungry = false;
                 if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
                 break;
@@ -1879,17 +1893,19 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
         backoff = 500;
         if (hungry) {
             hungry = false;
-            acc.idle_ns += globaltimer_ns() - idle_since;
-            if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
+            if (lane == 0) {
+                cold().idle_ns += globaltimer_ns() - idle_since;
+                atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
+            }
         }
-        if (kind == 2) acc.pieces++;
+        if (kind == 2 && lane == 0) cold().pieces++;
         T.root = __shfl_sync(FULL, T.root, 0);
         T.kdepth = __shfl_sync(FULL, T.kdepth, 0);
         T.rec = __shfl_sync(FULL, T.rec, 0);
         acc.t_count = acc.t_hash = acc.t_nodes = acc.t_rep = acc.t_split = 0;
         const uint64_t t0 = globaltimer_ns();
         const bool go_on = run_task(P, s, T, acc, shist, ws_smem, ws_glob, taskbuf, lane, built, node_tick, t_start);
-        acc.max_busy += globaltimer_ns() - t0;
+        if (lane == 0) cold().max_busy += globaltimer_ns() - t0;
         acc.count += acc.t_count;
         acc.hash += acc.t_hash;
         acc.nodes += acc.t_nodes;
@@ -1913,17 +1929,20 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
         if (!go_on) break;
     }
     if (hungry) {
-        acc.idle_ns += globaltimer_ns() - idle_since;
-        if (lane == 0) atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
+        if (lane == 0) {
+            cold().idle_ns += globaltimer_ns() - idle_since;
+            atomicAdd(&P.ctl[CTL_HUNGRY], ~0ULL);
+        }
     }
     if (lane == 0) {
         atomicMax(&P.ctl[CTL_T_END], (unsigned long long)globaltimer_ns());
-        atomicAdd(&P.out[OUT_BUILD_NS], acc.build_ns);
-        atomicAdd(&P.out[OUT_SEARCH_NS], acc.max_busy - acc.build_ns);
-        atomicAdd(&P.out[OUT_IDLE_NS], acc.idle_ns);
-        atomicAdd(&P.out[OUT_BUILDS], acc.builds);
-        atomicAdd(&P.out[OUT_PIECES], acc.pieces);
-        atomicMax(&P.out[OUT_MAXBUSY_NS], acc.max_busy);
+        const AccCold &c = cold();
+        atomicAdd(&P.out[OUT_BUILD_NS], c.build_ns);
+        atomicAdd(&P.out[OUT_SEARCH_NS], c.max_busy - c.build_ns);
+        atomicAdd(&P.out[OUT_IDLE_NS], c.idle_ns);
+        atomicAdd(&P.out[OUT_BUILDS], c.builds);
+        atomicAdd(&P.out[OUT_PIECES], c.pieces);
+        atomicMax(&P.out[OUT_MAXBUSY_NS], c.max_busy);
         atomicAdd(&P.out[OUT_NWARPS], 1ULL);
     }
     {
@@ -1932,7 +1951,7 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
         if (lane == 0) atomicAdd(&P.out[OUT_WORDOPS], w);
     }
     if (lane == 0) {
-        if (acc.maxsize) atomicMax(&P.out[OUT_MAXSIZE], acc.maxsize);
+        if (cold().maxsize) atomicMax(&P.out[OUT_MAXSIZE], cold().maxsize);
         atomicAdd(&P.out[OUT_COUNT], acc.count);
         atomicAdd(&P.out[OUT_HASH], acc.hash);
         atomicAdd(&P.out[OUT_NODES], acc.nodes);
