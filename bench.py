@@ -120,11 +120,11 @@ BLOCKS_PER_SM = 3
 SPLIT_NODES = 4096
 
 # DRAM bytes (read + write) of one k_bk launch from an ncu capture of this
-# workload (5 % sample, profiles/k_bk_rmat18_sample5pct_full.md), scaled by
+# workload (10 % sample, profiles/k_bk_rmat18_sample10pct.md), scaled by
 # tree nodes; valid only for the kernel sources it was taken with.
-K_BK_TRAFFIC = {"bytes": 168_209_408, "tree_nodes": 209_045_963,
-                "sha256": {"bk.cu": "14fb1cf01c444619ffd063ad8bdb8214a8df915eb47932690b0ee5231c7ceba0",
-                           "bk.cuh": "2d3e8c6e6f64a2521d9258d956def8cccd8db4f0648f99262ebca92e462d9917"}}
+K_BK_TRAFFIC = {"bytes": 88_636_160 + 147_065_856, "tree_nodes": 437_700_333,
+                "sha256": {"bk.cu": "f522bee0624c52bdbf571e1646dc81336eefc58f45e14253b5000d0c9f52292d",
+                           "bk.cuh": "5ffddff991fc5dcc46cff8b8dca65fdff4207e5cb7a3e97f05d47969dcb5b0e6"}}
 
 
 def k_bk_traffic(tree_nodes: int):
