@@ -197,6 +197,32 @@ def test_rmat13_per_vertex_exact(gpu_lib, kind, split):
     assert np.array_equal(u64(pv[2]), o.per_vertex["nodes"])
 
 
+@pytest.mark.parametrize("shape", [(2, 16), (3, 64), (4, 256)])
+def test_handover_stress_keeps_every_subproblem(gpu_lib, shape):
+    """Hand-overs every few nodes (ParTTT prefix rule, Algorithm 3) from wide
+    frames, small mask frames and memory frames, under three launch shapes:
+    per-subproblem counts, hashes and tree nodes still equal the oracle's, and
+    the clique list equals the oracle's list."""
+    mce = gpu_lib
+    bps, split_nodes = shape
+    n, u, v = rmat(12, seed=21)
+    og = O.Graph(n, u, v)
+    rk = O.rank(og, "degen")
+    o = O.parmce(og, rk, per_vertex=True, threads=4)
+    g = gpu_graph(mce, n, u, v)
+    pv = per_vertex_bufs(n)
+    r = mce.enumerate_cliques(g, rank="degen", per_vertex=pv, blocks_per_sm=bps, split_nodes=split_nodes)
+    assert r.tasks_split > 0
+    assert_same_summary(r, o)
+    assert r.tree_nodes == o.nodes
+    assert np.array_equal(u64(pv[0]), o.per_vertex["count"])
+    assert np.array_equal(u64(pv[1]), o.per_vertex["hash"])
+    assert np.array_equal(u64(pv[2]), o.per_vertex["nodes"])
+    off, vtx = list_bufs(r.count + 16, r.count * 40 + 1024)
+    r2 = mce.enumerate_cliques(g, rank="degen", list_buf=(off, vtx), blocks_per_sm=bps, split_nodes=split_nodes)
+    assert mce.decode_list(off, vtx, r2.list_cliques) == O.ttt_whole(og, want_list=True).cliques
+
+
 def test_user_rank_random_permutation(gpu_lib):
     mce = gpu_lib
     n, u, v = rmat(12, seed=9)
