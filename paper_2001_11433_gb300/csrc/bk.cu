@@ -780,13 +780,16 @@ __device__ int periodic(const BkParams &P, Ws &s, const Task &T, Acc &acc, int l
 // subproblem's columns (the receiver rebuilds F from the path).
 
 struct SmallU {
-    int32_t cidC, cidX;      // local ids of C_lane, X_lane
     uint32_t adjC, adjX, exclC;
-    int32_t gC, gX;          // global ids
     uint32_t tC, tX;         // 127 - (position of the global id among C ∪ X): pivot tie keys
-    uint64_t hC;             // h(C_lane)
     int cn, xn;
 };
+
+// tables of the small search in the warp's shared scratch (read by broadcast)
+__device__ __forceinline__ uint64_t *small_h(const Ws &s) { return reinterpret_cast<uint64_t *>(s.piv); }
+__device__ __forceinline__ int32_t *small_gid(const Ws &s) { return reinterpret_cast<int32_t *>(s.piv + 320); }
+__device__ __forceinline__ int32_t *small_cidc(const Ws &s) { return reinterpret_cast<int32_t *>(s.piv + 352); }
+__device__ __forceinline__ int32_t *small_cidx(const Ws &s) { return reinterpret_cast<int32_t *>(s.piv + 384); }
 
 // Stack frame j of the small search: 8 words in the warp's shared scratch,
 // [cand, finc, ext, xs, conf, q (C index that created frame j), hsum lo, hi].
@@ -798,11 +801,12 @@ constexpr int SMALL_DONATE_MIN_CAND = 8;
 // C-index mask -> the lane's words of a bitset over the subproblem's
 // candidate columns (or-ed into w); X members that are columns go to wf
 template <int NR>
-__device__ __forceinline__ void small_to_words(const SmallU &u, uint32_t m, int lane, uint32_t (&w)[NR]) {
+__device__ __forceinline__ void small_to_words(const Ws &s, uint32_t m, int lane, uint32_t (&w)[NR]) {
+    const int32_t *cidc = small_cidc(s);
     while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
-        const int32_t cid = __shfl_sync(FULL, u.cidC, b);
+        const int32_t cid = cidc[b];
 #pragma unroll
         for (int r = 0; r < NR; ++r)
             if (lane + 32 * r == (cid >> 5)) w[r] |= 1u << (cid & 31);
@@ -838,7 +842,7 @@ __device__ bool small_donate(const BkParams &P, const Ws &s, const Task &T, cons
         // small frame m = j - k_out + 1 was created by C index q_m
         const int m = j - k_out + 1;
         const int32_t qm = (m == ds) ? qcur : (int32_t)stk[(m > 0 && m < 32 ? m : 0) * SMALL_FRAME + 5];
-        const int32_t loc_small = __shfl_sync(FULL, u.cidC, (qm >= 0 ? qm : 0) & 31);
+        const int32_t loc_small = small_cidc(s)[(qm >= 0 ? qm : 0) & 31];
         if (j < kd) {
             int32_t loc;
             if (j < T.kdepth) loc = s.kpath[j];
@@ -850,16 +854,16 @@ __device__ bool small_donate(const BkParams &P, const Ws &s, const Task &T, cons
     uint32_t wcand[NR], wfin[NR], wext[NR], wconf[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) wcand[r] = wfin[r] = wext[r] = wconf[r] = 0u;
-    small_to_words<NR>(u, mc & ~lo, lane, wcand);
-    small_to_words<NR>(u, mf | lo, lane, wfin);
-    small_to_words<NR>(u, ext & ~lo, lane, wext);
-    if (P.mode == BK_IMCE) small_to_words<NR>(u, mk, lane, wconf);
+    small_to_words<NR>(s, mc & ~lo, lane, wcand);
+    small_to_words<NR>(s, mf | lo, lane, wfin);
+    small_to_words<NR>(s, ext & ~lo, lane, wext);
+    if (P.mode == BK_IMCE) small_to_words<NR>(s, mk, lane, wconf);
     // X members that are candidate columns (finic of the small root) stay fini
     uint32_t xm = mx;
     while (xm) {
         const int b = __ffs(xm) - 1;
         xm &= xm - 1;
-        const int32_t cid = __shfl_sync(FULL, u.cidX, b);
+        const int32_t cid = small_cidx(s)[b];
         if (cid < s.c) {
 #pragma unroll
             for (int r = 0; r < NR; ++r)
@@ -936,13 +940,13 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
         if (lane < flen) Xl[base_f + lane] = Fd[lane];
     }
     __syncwarp();
-    u.cidC = lane < u.cn ? Cl[lane] : 0;
-    u.cidX = lane < u.xn ? Xl[lane] : 0;
+    const int32_t cidC = lane < u.cn ? Cl[lane] : 0;
+    const int32_t cidX = lane < u.xn ? Xl[lane] : 0;
     u.adjC = u.adjX = u.exclC = 0u;
     {
-        const uint32_t *rowC = s.A + (int64_t)u.cidC * s.S;
-        const uint32_t *rowX = s.A + (int64_t)u.cidX * s.S;
-        const uint32_t *xrow = imce ? s.X + (int64_t)u.cidC * s.S : nullptr;
+        const uint32_t *rowC = s.A + (int64_t)cidC * s.S;
+        const uint32_t *rowX = s.A + (int64_t)cidX * s.S;
+        const uint32_t *xrow = imce ? s.X + (int64_t)cidC * s.S : nullptr;
         for (int k = 0; k < u.cn; ++k) {
             const int32_t ck = Cl[k];
             const int wd = ck >> 5;
@@ -952,30 +956,37 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
             if (imce && lane < u.cn && (xrow[wd] & bit)) u.exclC |= 1u << k;
         }
     }
-    u.gC = lane < u.cn ? s.gid[u.cidC] : 0x7fffffff;
-    u.gX = lane < u.xn ? s.gid[u.cidX] : 0x7fffffff;
-    u.hC = lane < u.cn ? vertex_hash(u.gC, P.seed) : 0ULL;
     {
+        const int32_t gC = lane < u.cn ? s.gid[cidC] : 0x7fffffff;
+        const int32_t gX = lane < u.xn ? s.gid[cidX] : 0x7fffffff;
         // C is in increasing global id, so C_l has l smaller ids in C
         int oc = lane, ox = 0;
         for (int k = 0; k < u.xn; ++k) {
-            const int32_t gk = __shfl_sync(FULL, u.gX, k);
-            oc += gk < u.gC;
-            ox += gk < u.gX;
+            const int32_t gk = __shfl_sync(FULL, gX, k);
+            oc += gk < gC;
+            ox += gk < gX;
         }
-        for (int k = 0; k < u.cn; ++k) ox += __shfl_sync(FULL, u.gC, k) < u.gX;
+        for (int k = 0; k < u.cn; ++k) ox += __shfl_sync(FULL, gC, k) < gX;
         u.tC = 127u - (uint32_t)oc;
         u.tX = 127u - (uint32_t)ox;
+        // the tables live where the wide pivot keeps its cand and after the stack
+        // (Cl / Xl, read above, sit inside the stack area)
+        if (lane < u.cn) {
+            small_h(s)[lane] = vertex_hash(gC, P.seed);
+            small_gid(s)[lane] = gC;
+            small_cidc(s)[lane] = cidC;
+        }
+        if (lane < u.xn) small_cidx(s)[lane] = cidX;
     }
     uint32_t conf = 0u;
     if (imce) {
-        const int wd = u.cidC >> 5;
+        const int wd = cidC >> 5;
         uint32_t wv = __shfl_sync(FULL, rx[0], wd & 31);
         if (NR > 1) {
             const uint32_t w1 = __shfl_sync(FULL, rx[NR - 1], wd & 31);
             if (wd >= 32) wv = w1;
         }
-        conf = __ballot_sync(FULL, lane < u.cn && ((wv >> (u.cidC & 31)) & 1u));
+        conf = __ballot_sync(FULL, lane < u.cn && ((wv >> (cidC & 31)) & 1u));
     }
     __syncwarp();   // Cl / Xl are scratch again after this point
     // ---- the search
@@ -1040,10 +1051,10 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
             // small frame fj (1..ds, up to 32) was created by C index q_fj; lane fj-1 writes it
             const int fj = lane + 1;
             const int32_t qj = (fj == ds) ? qcur : (int32_t)stk[(fj & 31) * SMALL_FRAME + 5];
-            const int32_t gq = __shfl_sync(FULL, u.gC, (qj >= 0 ? qj : 0) & 31);
+            const int32_t gq = small_gid(s)[(qj >= 0 ? qj : 0) & 31];
             if (fj <= ds) dst[nseed + npath + d + fj] = gq;
-            const int32_t ga = __shfl_sync(FULL, u.gC, (qa >= 0 ? qa : 0) & 31);
-            const int32_t gb = __shfl_sync(FULL, u.gC, (qb >= 0 ? qb : 0) & 31);
+            const int32_t ga = small_gid(s)[(qa >= 0 ? qa : 0) & 31];
+            const int32_t gb = small_gid(s)[(qb >= 0 ? qb : 0) & 31];
             if (lane == 0) {
                 if (qa >= 0) dst[nseed + npath + d + ds + 1] = ga;
                 if (qb >= 0) dst[nseed + npath + d + ds + 2] = gb;
@@ -1119,7 +1130,7 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
             finc |= qb;
             const uint32_t aq = __shfl_sync(FULL, u.adjC, q);
             const uint32_t xq = __ballot_sync(FULL, (u.adjX >> q) & 1u);
-            const uint64_t hq = __shfl_sync(FULL, u.hC, q);
+            const uint64_t hq = small_h(s)[q];
             uint32_t cc = cand & aq, cf = finc & aq, cx = xs & xq, ck = conf;
             if (imce) {
                 // Algorithm 7: a candidate joined to K + q by an earlier new edge moves to fini
@@ -1151,7 +1162,7 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
                     n32 += 2;
                     node_tick += 2;
                     w32 += t + 2u * ((t + 31u) >> 5);
-                    small_emit((uint32_t)(k0 + d + ds + 2), hs + hq + __shfl_sync(FULL, u.hC, c), q, c);
+                    small_emit((uint32_t)(k0 + d + ds + 2), hs + hq + small_h(s)[c], q, c);
                 }
                 continue;
             }

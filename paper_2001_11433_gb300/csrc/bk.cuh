@@ -118,9 +118,11 @@ __host__ __device__ inline int64_t bk_shared_words(int64_t w, int64_t c) {
     return (words + 31) & ~int64_t(31);
 }
 
-// Per-warp shared-memory scratch of the pivot step: cand (64 words) and
-// the member list of cand ∪ finic (512 16-bit local ids).
-constexpr int BK_PIV_WORDS = 64 + 256;
+// Per-warp shared-memory scratch: the wide pivot's cand (64 words) and
+// member list of cand ∪ finic (512 16-bit local ids); in the small search
+// the same 320 words hold h(C_k) and the frame stack, and 96 more words the
+// global and local ids of C and the local ids of X.
+constexpr int BK_PIV_WORDS = 64 + 256 + 96;
 
 // Dynamic shared memory of one search block: 256 histogram bins, the pivot
 // scratch of every warp, then the optional per-warp workspace slots.
