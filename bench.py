@@ -122,9 +122,9 @@ SPLIT_NODES = 4096
 # DRAM bytes (read + write) of one k_bk launch from an ncu capture of this
 # workload (10 % sample, profiles/k_bk_rmat18_sample10pct.md), scaled by
 # tree nodes; valid only for the kernel sources it was taken with.
-K_BK_TRAFFIC = {"bytes": 88_636_160 + 147_065_856, "tree_nodes": 437_700_333,
-                "sha256": {"bk.cu": "f522bee0624c52bdbf571e1646dc81336eefc58f45e14253b5000d0c9f52292d",
-                           "bk.cuh": "5ffddff991fc5dcc46cff8b8dca65fdff4207e5cb7a3e97f05d47969dcb5b0e6"}}
+K_BK_TRAFFIC = {"bytes": 89_012_224 + 149_233_152, "tree_nodes": 437_700_333,
+                "sha256": {"bk.cu": "c84085d1dd7ff05d6b67c58ec7881a5c58f69e9892db813231df19052a0bdc93",
+                           "bk.cuh": "4f0536c7e58b1fa2d93c8fbfb6d1239c9d7f1ea953402c032d8caea9ecda0be9"}}
 
 
 def k_bk_traffic(tree_nodes: int):
