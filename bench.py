@@ -21,7 +21,7 @@ ending with the summary (count, histogram, set hash) read back.
                                        # time per rank (degree, degeneracy, triangles, learned)
 
 Under torchrun every rank runs the same workload as an independent replica
-(the per-vertex subproblems need no exchange; see DESIGN.md), the slowest
+(the per-vertex subproblems need no exchange), the slowest
 rank's time is used and value = cliques of all ranks / that time.
 `--impl reference` times the CPU oracle (the paper's algorithms as plain C on
 the host cores) on a bounded sample of the same workload.
@@ -120,7 +120,7 @@ BLOCKS_PER_SM = 3
 SPLIT_NODES = 4096
 
 # DRAM bytes (read + write) of one k_bk launch from an ncu capture of this
-# workload (10 % sample, profiles/k_bk_rmat18_sample10pct.md), scaled by
+# workload (a 10 % sample of its subproblems), scaled by
 # tree nodes; valid only for the kernel sources it was taken with.
 K_BK_TRAFFIC = {"bytes": 89_012_224 + 149_233_152, "tree_nodes": 437_700_333,
                 "sha256": {"bk.cu": "c84085d1dd7ff05d6b67c58ec7881a5c58f69e9892db813231df19052a0bdc93",
