@@ -476,40 +476,57 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def independent_sets(row, col, rounds=4, seed=5):
+    """`rounds` disjoint independent sets of a CSR graph (each vertex with a
+    neighbour at most once): a vertex joins when its random priority is below
+    all its neighbours' (vertices already taken never join again)."""
+    n = len(row) - 1
+    deg = np.diff(row)
+    has = deg > 0
+    rng = np.random.default_rng(seed)
+    done = np.zeros(n, bool)
+    out = []
+    for _ in range(rounds):
+        pri = rng.random(n)
+        pri[done] = 2.0                      # already taken: never chosen, never blocks
+        nb_min = np.full(n, 3.0)
+        nb_min[has] = np.minimum.reduceat(pri[col], row[:-1][has])
+        S = np.nonzero((pri < nb_min) & has & ~done)[0].astype(np.int32)
+        out.append(S)
+        done[S] = True
+    return out
+
+
+def lowest_first_rank(n, S):
+    """A total rank (permutation of [0, n)) with the vertices of S lowest, in
+    id order, then every other vertex in id order."""
+    rank = np.empty(n, np.int32)
+    rest = np.setdiff1d(np.arange(n, dtype=np.int32), S, assume_unique=True)
+    rank[S] = np.arange(len(S), dtype=np.int32)
+    rank[rest] = np.arange(len(S), n, dtype=np.int32)
+    return rank
+
+
 def neighbourhood_cost_labels(mce, g, rounds=4, seed=5):
     """Training labels for the learned rank key: log(1 + TTT tree nodes) of
     each sampled vertex's whole neighbourhood (cand = Γ(v), fini = ∅: the cost
     of v's subproblem if v were ranked lowest).  Section 4.2 ranks a vertex
     higher the costlier its neighbourhood, so that its own subproblem (the
-    higher-ranked neighbours only) stays small.  Each round takes an
-    independent set S (vertices whose random priority beats all neighbours'),
-    puts S below every other vertex in a user rank and runs the subproblems of
-    S only: each then has its whole neighbourhood as candidates."""
+    higher-ranked neighbours only) stays small.  For each independent set S,
+    a user rank puts S below every other vertex and only the subproblems of S
+    run: each then has its whole neighbourhood as candidates."""
     import torch
     n = g.n
     row, col = g.csr()
-    deg = np.diff(row)
-    rng = np.random.default_rng(seed)
-    done = np.zeros(n, bool)
     vs, ls = [], []
-    for _ in range(rounds):
-        pri = rng.random(n)
-        pri[done] = 2.0                      # already labelled: never chosen
-        nb_min = np.full(n, 3.0)
-        has = deg > 0
-        nb_min[has] = np.minimum.reduceat(pri[col], row[:-1][has])
-        S = np.nonzero((pri < nb_min) & has & ~done)[0].astype(np.int32)
-        rank = np.empty(n, np.int32)
-        rest = np.setdiff1d(np.arange(n, dtype=np.int32), S, assume_unique=True)
-        rank[S] = np.arange(len(S), dtype=np.int32)
-        rank[rest] = np.arange(len(S), n, dtype=np.int32)
+    for S in independent_sets(row, col, rounds, seed):
+        rank = lowest_first_rank(n, S)
         pv = tuple(torch.zeros(n, dtype=torch.int64, device="cuda") for _ in range(3))
         mce.enumerate_cliques(g, rank="user", user_rank=torch.from_numpy(rank).cuda(),
                               subset=torch.from_numpy(S).cuda(), per_vertex=pv)
         nodes = pv[2].cpu().numpy()[S].astype(np.float64)
         vs.append(S)
         ls.append(np.log1p(nodes).astype(np.float32))
-        done[S] = True
     return np.concatenate(vs), np.concatenate(ls)
 
 
