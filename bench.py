@@ -105,6 +105,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_max(values, device):
+    """Element-wise maximum of per-rank values over the process group (the
+    slowest replica's times)."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(units_per_replica, world, ms):
+    """Units all replicas processed per second of the slowest replica."""
+    return world * units_per_replica / (ms / 1000.0)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -284,15 +299,12 @@ def run_ours(args):
     ms = float(np.mean(times))
     e2e_ms = float(np.mean(e2e_times))
     if dist:
-        import torch.distributed as tdist
-        t = torch.tensor([ms, e2e_ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+        ms, e2e_ms = replica_max([ms, e2e_ms], "cuda")
     if rank != 0:
         return
     assert r2.count == res.count and r2.hash == res.hash
     count = res.count
-    value = world * count / (ms / 1000.0)
+    value = whole_job_rate(count, world, ms)
     peaks, peak_src = load_peaks()
     props = torch.cuda.get_device_properties(local)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
@@ -321,7 +333,7 @@ def run_ours(args):
                                     f"{sm_mhz:.0f} MHz (median SM clock sampled during the run)",
                      "work": "per tree node (|cand|+|fini|)*ceil(|cand|/32) pivot AND+POPC words + "
                              "2*ceil((|cand|+|fini|)/32) per child + |K| per clique, counted by the kernel"},
-        "e2e": {"value": world * count / (e2e_ms / 1000.0), "unit": UNIT,
+        "e2e": {"value": whole_job_rate(count, world, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * m + 4 * len(subset_host),
                 "d2h_bytes_per_step": 8 * (16 + 1024) + 8 * 8},
         "gpu_launches": int(launches),
