@@ -99,8 +99,9 @@ typedef struct {
     uint32_t split_nodes;         /* with split: a task hands over a piece every this many nodes even
                                      when no warp waits (0 = 4096); pieces also go to waiting warps */
     int32_t order_by_model;       /* 1 = schedule subproblems by the model's prediction */
-    int32_t warps_per_block;      /* 0 = automatic */
-    int32_t blocks_per_sm;        /* 0 = automatic */
+    int32_t warps_per_block;      /* search warps per block, 1..8 (0 = 8) */
+    int32_t blocks_per_sm;        /* resident search blocks per SM, 2..4 (0 = 2: 128 registers a
+                                     thread; 3 and 4 trade registers for warps) */
     int32_t shared_words;         /* per-warp shared-memory workspace words (0 = none, the default:
                                      the global workspaces then get the whole L1) */
     uint32_t time_limit_ms;       /* stop the search after this long (MCE_ETIMEOUT); 0 = 600 s */
