@@ -474,16 +474,16 @@ __device__ void build_imce(const BkParams &P, Ws &s, int32_t i, int lane) {
 // warp (lane 0 updates them), to keep registers for the search.
 struct AccCold {
     unsigned long long build_ns, idle_ns, builds, pieces, max_busy, maxsize;
+    unsigned long long count, hash, nodes;   // whole launch
+    unsigned long long t_rep;                // this task's nodes already credited to sub_nodes / graph_nodes
+    unsigned long long t_split;              // this task's nodes at its last hand-over
 };
 __shared__ AccCold g_cold[8];   // warps of one search block
 __device__ __forceinline__ AccCold &cold() { return g_cold[threadIdx.x >> 5]; }
 
 struct Acc {
     unsigned long long wops;                 // per lane: algorithmic word operations
-    unsigned long long count, hash, nodes;   // per warp, whole launch
     unsigned long long t_count, t_hash, t_nodes;   // per task
-    unsigned long long t_rep;                      // t_nodes already credited to sub_nodes / graph_nodes
-    unsigned long long t_split;                    // t_nodes at the last hand-over
     int tick;                                      // nodes between checks (shorter in the endgame)
     int give;                                      // hand-overs per check at most
 };
@@ -637,8 +637,8 @@ __device__ int poll(const BkParams &P, Acc &acc, int lane, int32_t root, uint64_
         // exact node counts per subproblem and per graph: the task's nodes
         // since the last report (the rest is credited when the task ends), so
         // "over budget" holds exactly when the whole tree exceeds the budget
-        const unsigned long long delta = acc.t_nodes - acc.t_rep;
-        acc.t_rep = acc.t_nodes;
+        const unsigned long long delta = acc.t_nodes - cold().t_rep;
+        cold().t_rep = acc.t_nodes;
         if (P.sub_nodes) {
             const unsigned long long tot = atomicAdd(&P.sub_nodes[root], delta) + delta;
             if (tot > P.sub_budget) ab |= 16ULL;
@@ -656,9 +656,9 @@ __device__ int poll(const BkParams &P, Acc &acc, int lane, int32_t root, uint64_
             if (qlen >= hungry) hungry = 0;
             // a task hands over again only after 2048 more nodes of its own:
             // pieces cut too small cost their receivers more than they hold
-            if (acc.t_nodes - acc.t_split < 2048ULL) hungry = 0;
+            if (acc.t_nodes - cold().t_split < 2048ULL) hungry = 0;
             // a long-running task spreads its subtree before anybody waits
-            if (!hungry && P.split_nodes && acc.t_nodes - acc.t_split >= P.split_nodes &&
+            if (!hungry && P.split_nodes && acc.t_nodes - cold().t_split >= P.split_nodes &&
                 qlen < (unsigned long long)P.qcap / 2) hungry = 1;
         }
     }
@@ -678,7 +678,7 @@ __device__ int poll(const BkParams &P, Acc &acc, int lane, int32_t root, uint64_
     hungry_out = hungry;
     if (ab & 3ULL) return 1;
     if (ab & 16ULL) return 2;
-    if (hungry) acc.t_split = acc.t_nodes;
+    if (hungry && lane == 0) cold().t_split = acc.t_nodes;
     return 0;
 }
 
@@ -1818,8 +1818,8 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
     const int64_t gwarp = (int64_t)blockIdx.x * nw_block + wib;
     uint32_t *ws_glob = P.gws + gwarp * P.gws_words;
     uint32_t *taskbuf = P.taskbuf + gwarp * P.slot_words;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 64, 4};
-    if (lane == 0) cold() = AccCold{0, 0, 0, 0, 0, 0};
+    Acc acc = {0, 0, 0, 0, 64, 4};
+    if (lane == 0) cold() = AccCold{0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     Ws s;
     s.piv = smem + 512 + (int64_t)wib * BK_PIV_WORDS;
     int32_t built = -1;
@@ -1913,17 +1913,19 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
         T.root = __shfl_sync(FULL, T.root, 0);
         T.kdepth = __shfl_sync(FULL, T.kdepth, 0);
         T.rec = __shfl_sync(FULL, T.rec, 0);
-        acc.t_count = acc.t_hash = acc.t_nodes = acc.t_rep = acc.t_split = 0;
+        acc.t_count = acc.t_hash = acc.t_nodes = 0;
+        if (lane == 0) cold().t_rep = cold().t_split = 0;
         const uint64_t t0 = globaltimer_ns();
         const bool go_on = run_task(P, s, T, acc, shist, ws_smem, ws_glob, taskbuf, lane, built, node_tick, t_start);
         if (lane == 0) cold().max_busy += globaltimer_ns() - t0;
-        acc.count += acc.t_count;
-        acc.hash += acc.t_hash;
-        acc.nodes += acc.t_nodes;
         if (lane == 0) {
-            if (P.sub_nodes && acc.t_nodes > acc.t_rep) atomicAdd(&P.sub_nodes[T.root], acc.t_nodes - acc.t_rep);
-            if (P.graph_nodes && acc.t_nodes > acc.t_rep)
-                atomicAdd(&P.graph_nodes[P.graph_of[P.mode == BK_MCE ? T.root : P.eu[T.root]]], acc.t_nodes - acc.t_rep);
+            AccCold &c = cold();
+            c.count += acc.t_count;
+            c.hash += acc.t_hash;
+            c.nodes += acc.t_nodes;
+            if (P.sub_nodes && acc.t_nodes > c.t_rep) atomicAdd(&P.sub_nodes[T.root], acc.t_nodes - c.t_rep);
+            if (P.graph_nodes && acc.t_nodes > c.t_rep)
+                atomicAdd(&P.graph_nodes[P.graph_of[P.mode == BK_MCE ? T.root : P.eu[T.root]]], acc.t_nodes - c.t_rep);
             if (P.pv_count && P.mode == BK_MCE) {
                 atomicAdd(&P.pv_count[T.root], acc.t_count);
                 atomicAdd(&P.pv_hash[T.root], acc.t_hash);
@@ -1963,9 +1965,9 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
     }
     if (lane == 0) {
         if (cold().maxsize) atomicMax(&P.out[OUT_MAXSIZE], cold().maxsize);
-        atomicAdd(&P.out[OUT_COUNT], acc.count);
-        atomicAdd(&P.out[OUT_HASH], acc.hash);
-        atomicAdd(&P.out[OUT_NODES], acc.nodes);
+        atomicAdd(&P.out[OUT_COUNT], cold().count);
+        atomicAdd(&P.out[OUT_HASH], cold().hash);
+        atomicAdd(&P.out[OUT_NODES], cold().nodes);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 256; i += blockDim.x)
