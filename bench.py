@@ -137,8 +137,8 @@ SPLIT_NODES = 4096
 # DRAM bytes (read + write) of one k_bk launch from an ncu capture of this
 # workload (a 10 % sample of its subproblems), scaled by
 # tree nodes; valid only for the kernel sources it was taken with.
-K_BK_TRAFFIC = {"bytes": 89_012_224 + 149_233_152, "tree_nodes": 437_700_333,
-                "sha256": {"bk.cu": "c84085d1dd7ff05d6b67c58ec7881a5c58f69e9892db813231df19052a0bdc93",
+K_BK_TRAFFIC = {"bytes": 80_302_848 + 119_014_400, "tree_nodes": 437_700_333,
+                "sha256": {"bk.cu": "06eab31bd1dcfa9afd27d1a9357e21c563df4902c7363ba689fa68622d0b5f61",
                            "bk.cuh": "4f0536c7e58b1fa2d93c8fbfb6d1239c9d7f1ea953402c032d8caea9ecda0be9"}}
 
 
