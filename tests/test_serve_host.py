@@ -48,7 +48,7 @@ def batch(tag, k=4):
 
 
 def test_tenant_order_and_cross_tenant_concurrency(lib):
-    rec = Recorder()
+    rec = Recorder(sleep_s=0.1)
     srv = lib.Server(slots=4, execute=rec)
     ts = [srv.add_tenant() for _ in range(4)]
     ids = []
@@ -69,7 +69,7 @@ def test_tenant_order_and_cross_tenant_concurrency(lib):
 def test_memory_admission(lib):
     # execute mode: tenants have n = nnz = 0, so a batch of k pairs projects
     # mem_fixed + 16 + 112 k bytes
-    rec = Recorder()
+    rec = Recorder(sleep_s=0.1)
     srv = lib.Server(slots=4, execute=rec, mem_fixed=1000, mem_budget=1600)
     ts = [srv.add_tenant() for _ in range(4)]
     for t in ts:
@@ -77,7 +77,7 @@ def test_memory_admission(lib):
     srv.drain()
     assert rec.max_active == 1 and srv.stats()["max_in_flight"] == 1
     srv.close()
-    rec = Recorder()
+    rec = Recorder(sleep_s=0.1)
     srv = lib.Server(slots=4, execute=rec, mem_fixed=1000, mem_budget=2600)
     ts = [srv.add_tenant() for _ in range(4)]
     for t in ts:
@@ -89,7 +89,7 @@ def test_memory_admission(lib):
 
 
 def test_oversized_batch_runs_alone_and_holds_later_ones(lib):
-    rec = Recorder(sleep_s=0.05)
+    rec = Recorder(sleep_s=0.2)
     srv = lib.Server(slots=4, execute=rec, mem_fixed=100, mem_budget=300)
     a, b, c = (srv.add_tenant() for _ in range(3))
     ra = srv.submit(a, *batch(1, k=1))            # 228 bytes, in flight first
