@@ -48,6 +48,11 @@ def _L():
                 "or_graph_n": ([vp], i32),
                 "or_graph_export": ([vp, vp, vp], None),
                 "or_graph_plus": ([vp, vp, vp, i64], vp),
+                "or_graph_minus": ([vp, vp, vp, i64], vp),
+                "or_canonical_deletion": ([vp, vp, vp, i64, vp, vp], i64),
+                "or_dmce_alg": ([vp, vp, vp, i64, vp, vp], None),
+                "or_dmce_diff": ([vp, vp, vp, i64, vp, vp], None),
+                "or_imce_remove": ([vp, vp, vp, i64, vp, vp], i64),
                 "or_out_new": ([ctypes.c_int, u64], vp),
                 "or_out_free": ([vp], None),
                 "or_out_count": ([vp], u64),
@@ -154,6 +159,10 @@ class Graph:
         hu, hv = _i32(hu), _i32(hv)
         return Graph._wrap(_L().or_graph_plus(self._h, hu.ctypes.data, hv.ctypes.data, len(hu)), self.n)
 
+    def minus(self, hu, hv) -> "Graph":
+        hu, hv = _i32(hu), _i32(hv)
+        return Graph._wrap(_L().or_graph_minus(self._h, hu.ctypes.data, hv.ctypes.data, len(hu)), self.n)
+
 
 def degree(g: Graph) -> np.ndarray:
     out = np.zeros(g.n, dtype=np.int64)
@@ -239,6 +248,17 @@ def canonical_batch(g: Graph, u, v):
     return hu[:k].copy(), hv[:k].copy()
 
 
+def canonical_deletion(g: Graph, u, v):
+    """Deletion batch in arrival order: pairs that are edges of g, each once."""
+    u, v = _i32(u), _i32(v)
+    hu = np.zeros(max(len(u), 1), dtype=np.int32)
+    hv = np.zeros(max(len(u), 1), dtype=np.int32)
+    k = _L().or_canonical_deletion(g._h, u.ctypes.data, v.ctypes.data, len(u), hu.ctypes.data, hv.ctypes.data)
+    if k < 0:
+        raise ValueError("vertex id outside [0, n)")
+    return hu[:k].copy(), hv[:k].copy()
+
+
 def _imce2(fn, g, hu, hv, seed):
     lib = _L()
     hu, hv = _i32(hu), _i32(hv)
@@ -261,6 +281,18 @@ def imce_diff(g: Graph, hu, hv, seed: int = 0):
     return _imce2(_L().or_imce_diff, g, hu, hv, seed)
 
 
+def dmce_alg(g: Graph, hu, hv, seed: int = 0):
+    """(removed, created) cliques of deleting a canonical batch from g, by the
+    reduction to the incremental case (Algorithms 6 + 9 on g, then Algorithm
+    8's splits kept when maximal in g - H)."""
+    return _imce2(_L().or_dmce_alg, g, hu, hv, seed)
+
+
+def dmce_diff(g: Graph, hu, hv, seed: int = 0):
+    """(C(g) \\ C(g - H), C(g - H) \\ C(g)) by the plain set differences."""
+    return _imce2(_L().or_dmce_diff, g, hu, hv, seed)
+
+
 class Imce:
     """Graph plus its maximal cliques, updated batch by batch (mode B)."""
 
@@ -281,6 +313,20 @@ class Imce:
         a, b = lib.or_out_new(int(want_list), self.seed), lib.or_out_new(int(want_list), self.seed)
         try:
             rho = lib.or_imce_add(self._h, u.ctypes.data, v.ctypes.data, len(u), a, b)
+            if rho < 0:
+                raise ValueError("vertex id outside [0, n)")
+            return int(rho), _result(a, want_list), _result(b, want_list)
+        finally:
+            lib.or_out_free(a)
+            lib.or_out_free(b)
+
+    def remove(self, u, v, want_list: bool = True):
+        """Delete a batch of edges: (deleted ρ, removed cliques, created cliques)."""
+        lib = _L()
+        u, v = _i32(u), _i32(v)
+        a, b = lib.or_out_new(int(want_list), self.seed), lib.or_out_new(int(want_list), self.seed)
+        try:
+            rho = lib.or_imce_remove(self._h, u.ctypes.data, v.ctypes.data, len(u), a, b)
             if rho < 0:
                 raise ValueError("vertex id outside [0, n)")
             return int(rho), _result(a, want_list), _result(b, want_list)

@@ -15,7 +15,10 @@
  *   - new cliques after an edge batch: Algorithm 6 with the sequential
  *     edge-excluding TTT of Algorithm 9 (Appendix A),
  *   - subsumed cliques: Algorithm 8,
- *   - the plain set differences C(G+H) \ C(G) and C(G) \ C(G+H).
+ *   - the plain set differences C(G+H) \ C(G) and C(G) \ C(G+H),
+ *   - edge deletions, by reduction to the incremental step (G = (G - H) + H):
+ *     removed = Algorithm 6 on G, created = Algorithm 8's splits of the
+ *     removed cliques that are maximal in G - H; and by the set differences.
  *
  * Sets are sorted int32 arrays.  Readings where the paper is silent:
  *   - rank(v) = position of (key(v), id(v)) in ascending lexicographic order;
@@ -941,4 +944,227 @@ void or_imce_diff(const or_graph *g, const int32_t *hu, const int32_t *hv, int64
 /* G+H as a new graph (for chaining batches in tests). */
 or_graph *or_graph_plus(const or_graph *g, const int32_t *hu, const int32_t *hv, int64_t rho) {
     return graph_plus(g, hu, hv, rho);
+}
+
+/* ------------------------------------------------------------------ */
+/* decremental maintenance: edge deletions by reduction to additions   */
+/* ------------------------------------------------------------------ */
+/*
+ * Deleting a batch H from G gives G' = G - H, and G = G' + H.  By Section 5
+ * applied to (G', H): C(G) = C(G') \ Λdel ∪ Λnew, with Λnew the maximal
+ * cliques of G containing an edge of H and Λdel the cliques of C(G') that are
+ * not maximal in G.  Hence the deletion removes Λnew and creates Λdel:
+ *   removed = Algorithm 6 (with Algorithm 9) run on G and H;
+ *   created = Algorithm 8's splits of every removed clique on its H edges,
+ *             keeping each split that is a maximal clique of G' (Algorithm 8
+ *             tests membership in C(G'); the reduction does not hold C(G'),
+ *             and for a clique of G' membership is maximality).
+ * Deletion batches keep pairs that are edges of G, in arrival order; self
+ * loops, non-edges and repeats are dropped.
+ */
+
+int64_t or_canonical_deletion(const or_graph *g, const int32_t *u, const int32_t *v, int64_t k,
+                              int32_t *hu, int32_t *hv) {
+    uint64_t cap = 16;
+    while (cap < (uint64_t)k * 2 + 16) cap <<= 1;
+    uint64_t *seen = (uint64_t *)malloc(cap * sizeof(uint64_t));
+    memset(seen, 0xff, cap * sizeof(uint64_t));
+    int64_t kept = 0;
+    for (int64_t i = 0; i < k; ++i) {
+        if (u[i] < 0 || u[i] >= g->n || v[i] < 0 || v[i] >= g->n) { free(seen); return -1; }
+        if (u[i] == v[i]) continue;
+        int32_t a = u[i] < v[i] ? u[i] : v[i], b = u[i] < v[i] ? v[i] : u[i];
+        if (!has_edge(g, a, b)) continue;
+        uint64_t key = ((uint64_t)(uint32_t)a << 32) | (uint32_t)b;
+        uint64_t h = fmix(key) & (cap - 1);
+        int dup = 0;
+        while (seen[h] != UINT64_MAX) {
+            if (seen[h] == key) { dup = 1; break; }
+            h = (h + 1) & (cap - 1);
+        }
+        if (dup) continue;
+        seen[h] = key;
+        hu[kept] = a;
+        hv[kept] = b;
+        kept++;
+    }
+    free(seen);
+    return kept;
+}
+
+static or_graph *graph_minus(const or_graph *g, const int32_t *hu, const int32_t *hv, int64_t rho) {
+    uint64_t *keys = (uint64_t *)malloc((size_t)(rho + 1) * sizeof(uint64_t));
+    for (int64_t i = 0; i < rho; ++i) keys[i] = ((uint64_t)(uint32_t)hu[i] << 32) | (uint32_t)hv[i];
+    qsort(keys, (size_t)rho, sizeof(uint64_t), cmp_u64);
+    int32_t *u = (int32_t *)malloc((size_t)(g->nnz + 1) * sizeof(int32_t));
+    int32_t *v = (int32_t *)malloc((size_t)(g->nnz + 1) * sizeof(int32_t));
+    int64_t k = 0;
+    for (int32_t a = 0; a < g->n; ++a)
+        for (int64_t e = g->row_ptr[a]; e < g->row_ptr[a + 1]; ++e) {
+            int32_t b = g->col[e];
+            int32_t x = a < b ? a : b, y = a < b ? b : a;
+            uint64_t key = ((uint64_t)(uint32_t)x << 32) | (uint32_t)y;
+            int64_t lo = 0, hi = rho;
+            while (lo < hi) { int64_t mid = lo + (hi - lo) / 2; if (keys[mid] < key) lo = mid + 1; else hi = mid; }
+            if (lo < rho && keys[lo] == key) continue;
+            u[k] = a;
+            v[k] = b;
+            k++;
+        }
+    or_graph *gm = or_graph_from_pairs(g->n, u, v, k);
+    free(u);
+    free(v);
+    free(keys);
+    return gm;
+}
+
+/* K (sorted, a clique of g) is maximal iff no vertex outside K is adjacent
+ * to all of K */
+static int is_maximal(const or_graph *g, const int32_t *k, int32_t len) {
+    int32_t best = 0;
+    for (int32_t i = 1; i < len; ++i) if (deg(g, k[i]) < deg(g, k[best])) best = i;
+    const int32_t *nb = nbr(g, k[best]);
+    int32_t d = deg(g, k[best]);
+    for (int32_t t = 0; t < d; ++t) {
+        int32_t w = nb[t];
+        if (contains(k, len, w)) continue;
+        int all = 1;
+        for (int32_t i = 0; i < len && all; ++i)
+            if (i != best && !has_edge(g, w, k[i])) all = 0;
+        if (all) return 0;
+    }
+    return 1;
+}
+
+/* Algorithm 8's splits of every removed clique on its H edges; the splits
+ * that are maximal in G' are the created cliques (each reported once). */
+static void dmce_created(const int32_t *hu, const int32_t *hv, int64_t rho, const or_graph *gm,
+                         const or_out *removed, or_out *out) {
+    uint64_t *keys = (uint64_t *)malloc((size_t)(rho + 1) * sizeof(uint64_t));
+    for (int64_t i = 0; i < rho; ++i) keys[i] = ((uint64_t)(uint32_t)hu[i] << 32) | (uint32_t)hv[i];
+    qsort(keys, (size_t)rho, sizeof(uint64_t), cmp_u64);
+    clset done;
+    cs_init(&done, removed->n_cl * 2 + 4);
+    int32_t *buf = NULL;
+    int32_t bufcap = 0;
+    for (int64_t c = 0; c < removed->n_cl; ++c) {
+        const int32_t *cv = removed->vtx + removed->off[c];
+        int32_t len = (int32_t)(removed->off[c + 1] - removed->off[c]);
+        if (len + 1 > bufcap) { bufcap = len + 1; buf = (int32_t *)realloc(buf, (size_t)bufcap * sizeof(int32_t)); }
+        clset S;
+        cs_init(&S, 4);
+        cs_insert(&S, cv, len);
+        for (int32_t a = 0; a < len; ++a)
+            for (int32_t b = a + 1; b < len; ++b) {
+                uint64_t key = ((uint64_t)(uint32_t)cv[a] << 32) | (uint32_t)cv[b];
+                int64_t lo = 0, hi = rho;
+                while (lo < hi) { int64_t mid = lo + (hi - lo) / 2; if (keys[mid] < key) lo = mid + 1; else hi = mid; }
+                if (!(lo < rho && keys[lo] == key)) continue;   /* (cv[a], cv[b]) is a deleted edge */
+                clset S2;
+                cs_init(&S2, S.n * 2);
+                for (int64_t t = 0; t < S.n; ++t) {
+                    const int32_t *sv = S.vtx + S.off[t];
+                    int32_t sl = (int32_t)(S.off[t + 1] - S.off[t]);
+                    if (contains(sv, sl, cv[a]) && contains(sv, sl, cv[b])) {
+                        int32_t n1 = 0, n2 = 0;
+                        for (int32_t x = 0; x < sl; ++x) if (sv[x] != cv[a]) buf[n1++] = sv[x];
+                        cs_insert(&S2, buf, n1);
+                        for (int32_t x = 0; x < sl; ++x) if (sv[x] != cv[b]) buf[n2++] = sv[x];
+                        cs_insert(&S2, buf, n2);
+                    } else {
+                        cs_insert(&S2, sv, sl);
+                    }
+                }
+                cs_free(&S);
+                S = S2;
+            }
+        for (int64_t t = 0; t < S.n; ++t) {
+            const int32_t *sv = S.vtx + S.off[t];
+            int32_t sl = (int32_t)(S.off[t + 1] - S.off[t]);
+            if (sl == 0 || cs_find(&done, sv, sl) >= 0) continue;
+            cs_insert(&done, sv, sl);
+            if (is_maximal(gm, sv, sl)) emit(out, sv, sl);
+        }
+        cs_free(&S);
+    }
+    cs_free(&done);
+    free(buf);
+    free(keys);
+}
+
+/* One-shot, algorithmic: (removed, created) for a canonical deletion batch. */
+void or_dmce_alg(const or_graph *g, const int32_t *hu, const int32_t *hv, int64_t rho,
+                 or_out *removed_out, or_out *created_out) {
+    or_out *rem = or_out_new(1, removed_out->seed);
+    imce_new(g, hu, hv, rho, rem);   /* maximal cliques of G = G' + H through an edge of H */
+    or_graph *gm = graph_minus(g, hu, hv, rho);
+    dmce_created(hu, hv, rho, gm, rem, created_out);
+    out_merge(removed_out, rem);
+    or_out_free(rem);
+    or_graph_free(gm);
+}
+
+/* One-shot, plain definition: removed = C(G) \ C(G - H), created = C(G - H) \ C(G). */
+void or_dmce_diff(const or_graph *g, const int32_t *hu, const int32_t *hv, int64_t rho,
+                  or_out *removed_out, or_out *created_out) {
+    or_graph *gm = graph_minus(g, hu, hv, rho);
+    or_out *a = or_out_new(1, removed_out->seed), *b = or_out_new(1, removed_out->seed);
+    or_ttt_whole(g, a);
+    or_ttt_whole(gm, b);
+    clset A, B;
+    cs_from_out(&A, a);
+    cs_from_out(&B, b);
+    for (int64_t c = 0; c < a->n_cl; ++c) {
+        const int32_t *k = a->vtx + a->off[c];
+        int32_t len = (int32_t)(a->off[c + 1] - a->off[c]);
+        if (cs_find(&B, k, len) < 0) emit(removed_out, k, len);
+    }
+    for (int64_t c = 0; c < b->n_cl; ++c) {
+        const int32_t *k = b->vtx + b->off[c];
+        int32_t len = (int32_t)(b->off[c + 1] - b->off[c]);
+        if (cs_find(&A, k, len) < 0) emit(created_out, k, len);
+    }
+    cs_free(&A);
+    cs_free(&B);
+    or_out_free(a);
+    or_out_free(b);
+    or_graph_free(gm);
+}
+
+/* Stateful deletion batch on the incremental state (C = C(G) kept): returns
+ * the number of edges deleted, or -1 on an invalid id (nothing changed). */
+int64_t or_imce_remove(or_imce *s, const int32_t *u, const int32_t *v, int64_t k, or_out *removed_out,
+                       or_out *created_out) {
+    int32_t *hu = (int32_t *)malloc((size_t)(k + 1) * sizeof(int32_t));
+    int32_t *hv = (int32_t *)malloc((size_t)(k + 1) * sizeof(int32_t));
+    int64_t rho = or_canonical_deletion(s->g, u, v, k, hu, hv);
+    if (rho < 0) { free(hu); free(hv); return -1; }
+    or_out *rem = or_out_new(1, s->seed);
+    imce_new(s->g, hu, hv, rho, rem);
+    or_graph *gm = graph_minus(s->g, hu, hv, rho);
+    or_out *cre = or_out_new(1, s->seed);
+    dmce_created(hu, hv, rho, gm, rem, cre);
+    for (int64_t c = 0; c < rem->n_cl; ++c) {
+        int64_t f = cs_find(&s->C, rem->vtx + rem->off[c], (int32_t)(rem->off[c + 1] - rem->off[c]));
+        if (f >= 0) s->C.dead[f] = 1;
+    }
+    for (int64_t c = 0; c < cre->n_cl; ++c) {
+        int64_t id = cs_insert(&s->C, cre->vtx + cre->off[c], (int32_t)(cre->off[c + 1] - cre->off[c]));
+        s->C.dead[id] = 0;
+    }
+    s->alive += cre->n_cl - rem->n_cl;
+    out_merge(removed_out, rem);
+    out_merge(created_out, cre);
+    or_out_free(rem);
+    or_out_free(cre);
+    or_graph_free(s->g);
+    s->g = gm;
+    free(hu);
+    free(hv);
+    return rho;
+}
+
+/* G - H as a new graph (for chaining batches in tests). */
+or_graph *or_graph_minus(const or_graph *g, const int32_t *hu, const int32_t *hv, int64_t rho) {
+    return graph_minus(g, hu, hv, rho);
 }
