@@ -133,9 +133,10 @@ typedef struct {
     float ms_rank;                /* ranking time (key + sort), device time */
     float ms_enum;                /* enumeration time, device time */
     float ms_search;              /* device time of the search kernel alone */
-    uint64_t word_ops;            /* 32-bit AND+POPC word operations of the search:
-                                     per node (|cand|+|fini|)*ceil(c/32) for the pivot,
-                                     per child 2*ceil(c/32) + |F| */
+    uint64_t word_ops;            /* algorithmic 32-bit word operations of the search: per
+                                     tree node (|cand|+|fini|)*ceil(|cand|/32) AND+POPC for
+                                     the pivot and 2*ceil((|cand|+|fini|)/32) per child
+                                     searched, plus |K| per clique emitted */
     int64_t incomplete;           /* subproblems abandoned by subproblem_budget */
     uint64_t stats[8];            /* search kernel, summed over warps: [0] ns building subproblems,
                                      [1] ns searching, [2] ns waiting for work, [3] builds,
@@ -239,8 +240,10 @@ mce_status mce_model_predict(const mce_model *m, const float *feat, int32_t rows
  * graphs are the vertex ranges [graph_ptr[i], graph_ptr[i+1]) of the
  * disjoint union described by (u, v, m, n); graph_ptr is host int32[k+1].
  * Per graph (device buffers, caller-owned): counts uint64[k], hashes
- * uint64[k], status int32[k] (MCE_OK, or MCE_EBUDGET when the graph used up
- * opts->node_budget nodes).  The budget applies per graph.  *total receives
+ * uint64[k], status int32[k] (MCE_OK, or MCE_EBUDGET when the graph's search
+ * trees have more than opts->node_budget nodes in all; node counts are
+ * exact, so the status does not depend on timing).  The budget applies per
+ * graph; counts and hashes of graphs over it are partial.  *total receives
  * the summary over all graphs. */
 mce_status mce_enumerate_batched(const mce_graph *g, const int32_t *graph_ptr, int32_t k,
                                  const mce_opts *opts, uint64_t *counts, uint64_t *hashes,
