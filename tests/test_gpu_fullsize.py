@@ -79,3 +79,29 @@ def test_chung_lu_planted_full_enumeration(gpu_lib):
         assert r.count == gold["count"], kind
         assert r.hash == int(gold["hash"]), kind
         assert list(r.hist) == gold["hist"], kind
+
+
+def test_batched_4096_sampled_graphs(gpu_lib):
+    """The batched workload as the benchmark runs it (4,096 G(n, p) in one
+    launch, a per-graph budget of 2^20 tree nodes): a seeded sample of the
+    graphs finished within the budget is recomputed by the oracle, on global
+    vertex ids, and compared graph by graph."""
+    mce = gpu_lib
+    w = graphgen.batched_er_4096()
+    gptr = w.extra["graph_ptr"]
+    g = mce.Graph(w.n, _t(w.u), _t(w.v))
+    counts, hashes, status, tot = mce.enumerate_batched(g, gptr, node_budget=1 << 20)
+    ok = np.nonzero(status == 0)[0]
+    assert 0 < len(ok) < len(gptr) - 1 and not tot.complete
+    assert (np.diff(w.u) >= 0).all()            # edges come graph by graph, in increasing u
+    bounds = np.searchsorted(w.u, gptr)
+    cand = [i for i in ok if gptr[i + 1] - gptr[i] <= 400]
+    sample = np.random.default_rng(77).choice(cand, min(16, len(cand)), replace=False)
+    for i in sample:
+        a, b = int(gptr[i]), int(gptr[i + 1])
+        e0, e1 = int(bounds[i]), int(bounds[i + 1])
+        og = O.Graph(b, w.u[e0:e1], w.v[e0:e1])      # vertices below a are isolated and left out
+        sub = np.arange(a, b, dtype=np.int32)
+        o = O.parmce(og, O.rank(og, "degen"), subset=sub, per_vertex=True, threads=8)
+        assert int(counts[i]) == int(o.per_vertex["count"].sum()), i      # per-vertex arrays follow `sub`
+        assert int(hashes[i]) == int(o.per_vertex["hash"].astype(object).sum()) % (1 << 64), i
