@@ -377,3 +377,104 @@ def test_incremental_medium_graph():
     new_b, del_b = O.imce_alg(g, hu, hv)
     assert new_a.cliques == new_b.cliques and del_a.cliques == del_b.cliques
     assert new_a.count > 0 and del_a.count > 0
+
+
+# ---------------------------------------------------------------- search-tree node counts
+#
+# Every GPU parity test compares tree-node counts with the oracle's, and the
+# learned cost model is trained on them, so the oracle's tree (Algorithm 1:
+# pivot over cand ∪ fini maximising |cand ∩ Γ(u)|, ties to the smallest id,
+# ext visited in ascending id, each visited q moved from cand to fini) is
+# pinned here by counts derived by hand, independently of the code.
+
+def _star(r):
+    return r + 1, [(0, i) for i in range(1, r + 1)]
+
+
+def _cycle(n):
+    return n, [(i, (i + 1) % n) for i in range(n)]
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 17])
+def test_tree_nodes_complete_graph(n):
+    """K_n: every pivot has count |cand| - 1 and ext = {pivot}, so the tree
+    is a chain of n + 1 nodes.  Per vertex under rank(v) = v, vertex 0 runs
+    the chain below {0} (n nodes); every other vertex has a fini vertex
+    adjacent to all of cand, which wins the pivot with ext = ∅ (1 node)."""
+    pairs = [(i, j) for i in range(n) for j in range(i + 1, n)]
+    g = graph(n, pairs)
+    assert O.ttt_whole(g).nodes == n + 1
+    r = O.parmce(g, np.arange(n, dtype=np.int32), per_vertex=True)
+    assert list(r.per_vertex["nodes"]) == [n] + [1] * (n - 1)
+    assert r.nodes == 2 * n - 1
+    # the degeneracy rank of K_n is the identity (equal core numbers, id order)
+    assert O.parmce(g, O.rank(g, "degen")).nodes == 2 * n - 1
+
+
+@pytest.mark.parametrize("n", [1, 4, 30])
+def test_tree_nodes_empty_graph(n):
+    """No edges: the root's pivot has count 0, ext = V, n leaves."""
+    g = O.Graph(n, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    assert O.ttt_whole(g).nodes == n + 1
+    assert O.parmce(g, np.arange(n, dtype=np.int32)).nodes == n
+
+
+@pytest.mark.parametrize("r", [1, 3, 10])
+def test_tree_nodes_star(r):
+    """K_{1,r} with centre 0: the root pivots on the centre (ext = {0}); below
+    {0} every leaf has count 0, so ext = all r leaves: r + 2 nodes.  Per
+    vertex (rank = id): the centre's subproblem has r + 1 nodes, each leaf
+    (cand = ∅, fini = {0}) one."""
+    n, pairs = _star(r)
+    g = graph(n, pairs)
+    assert O.ttt_whole(g).nodes == r + 2
+    pv = O.parmce(g, np.arange(n, dtype=np.int32), per_vertex=True).per_vertex["nodes"]
+    assert list(pv) == [r + 1] + [1] * r
+
+
+@pytest.mark.parametrize("n", [4, 5, 8, 21])
+def test_tree_nodes_cycle(n):
+    """C_n, n >= 4.  Whole graph: root pivot 0, ext = V \\ {1, n-1}; the
+    child {0} has 3 nodes, the child {2} has 3, each later child {k}
+    (3 <= k <= n-2) has cand = {k+1}, fini = {k-1}: 2 nodes.  Total 2n - 1.
+    Per vertex (rank = id): vertex 0 has 3 nodes; vertex v in 1..n-2 has
+    cand = {v+1}, fini = {v-1}, both with count 0, so the smallest id v-1
+    (a fini vertex) is the pivot and ext = {v+1}: 2 nodes; vertex n-1 has
+    cand = ∅: 1 node."""
+    g = graph(*_cycle(n))
+    assert O.ttt_whole(g).nodes == 2 * n - 1
+    pv = O.parmce(g, np.arange(n, dtype=np.int32), per_vertex=True).per_vertex["nodes"]
+    assert list(pv) == [3] + [2] * (n - 2) + [1]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 7])
+def test_tree_nodes_moon_moser(k):
+    """Moon–Moser graph (k parts of 3): any pivot's ext is its own part, and
+    each of the 3 children is the Moon–Moser graph on the other k - 1 parts
+    with fini = ∅, so T(k) = 1 + 3 T(k-1), T(0) = 1: T(k) = (3^(k+1) - 1)/2.
+    Per vertex (rank = id): a vertex of part 0 has T(k-1) nodes; a vertex of
+    a later part has a fini vertex adjacent to all of cand (ext = ∅): 1 node."""
+    n, pairs, parts = complete_multipartite([3] * k)
+    g = graph(n, pairs)
+
+    def T(j):
+        return (3 ** (j + 1) - 1) // 2
+
+    assert O.ttt_whole(g).nodes == T(k)
+    pv = O.parmce(g, np.arange(n, dtype=np.int32), per_vertex=True).per_vertex["nodes"]
+    assert list(pv) == [T(k - 1)] * 3 + [1] * (n - 3)
+
+
+def test_tree_nodes_hand_traced_example():
+    """A 7-vertex graph whose tree depends on every rule above (the root has
+    a four-way pivot tie, a fini vertex wins a pivot tie below it, and ext
+    order decides which siblings see a vertex in fini); the whole trace is in
+    the fixture."""
+    d = _load("ttt_tree_trace.json")
+    g = graph(d["n"], [tuple(e) for e in d["edges"]])
+    whole = O.ttt_whole(g, want_list=True)
+    assert whole.cliques == [tuple(c) for c in d["cliques"]]
+    assert whole.nodes == d["whole_graph_nodes"] == len(d["whole_graph_trace"])
+    r = O.parmce(g, np.arange(d["n"], dtype=np.int32), per_vertex=True)
+    assert list(r.per_vertex["nodes"]) == d["per_vertex_identity_rank_nodes"]
+    assert list(r.per_vertex["count"]) == d["per_vertex_identity_rank_cliques"]
