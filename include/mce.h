@@ -117,6 +117,11 @@ typedef struct {
      * partial output, while per-subproblem outputs identify them
      * (pv_nodes > budget). */
     uint64_t subproblem_budget;
+    /* Slots of the device task ring that carries handed-over pieces (0 =
+     * automatic: 64 MiB of records, 1024..65536 slots).  A full ring refuses a
+     * hand-over and the donor keeps the work, so any capacity >= 1 gives the
+     * same result. */
+    int32_t queue_capacity;
 } mce_opts;
 
 typedef struct {
@@ -154,6 +159,12 @@ const char *mce_last_error(void);
 void mce_opts_init(mce_opts *o);
 /* Number of kernels this library has launched in this process. */
 uint64_t mce_kernel_launches(void);
+/* Failure injection for tests, on the host: after `after` more successful
+ * device allocations by this library, the next one fails as if the device
+ * were out of memory (MCE_ENOMEM); the injection then disarms itself.
+ * after < 0 disarms it.  Every entry point keeps its all-or-nothing promise
+ * under such a failure (an incremental state is left as it was). */
+void mce_debug_fail_alloc(int64_t after);
 
 /* ---------------------------------------------------------------- graphs */
 
@@ -384,7 +395,12 @@ void imce_server_free(imce_server *s);
  *
  * row_ptr int32[n+1] and col int32[nnz]: a simple undirected graph as CSR
  * on the device, rows sorted (e.g. from mce_graph_csr); rank int32[n]: a
- * permutation of [0, n) on the device (e.g. from mce_rank).  Subproblems run
+ * permutation of [0, n) on the device (e.g. from mce_rank).  Both are checked
+ * on the device before anything reads through them (row_ptr[0] = 0,
+ * row_ptr[n] = nnz, row_ptr non-decreasing, ids in [0, n), rows strictly
+ * increasing, no self loop, (x, y) present iff (y, x) is, rank values in
+ * [0, n) and distinct); a failed check returns MCE_EINVAL with the property
+ * named in mce_last_error().  Subproblems run
  * in vertex order; the result (count, hash, histogram, tree nodes) equals
  * mce_enumerate with the same rank and seed.  Clique lists, per-subproblem
  * outputs and budgets are not offered here.

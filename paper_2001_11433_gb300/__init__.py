@@ -58,6 +58,7 @@ class Opts(ctypes.Structure):
         ("subset_len", ctypes.c_int64),
         ("subset_on_host", ctypes.c_int32),
         ("subproblem_budget", ctypes.c_uint64),
+        ("queue_capacity", ctypes.c_int32),
     ]
 
 
@@ -156,6 +157,7 @@ SIGNATURES = {
     "mce_last_error": ([], ctypes.c_char_p),
     "mce_opts_init": ([_P(Opts)], None),
     "mce_kernel_launches": ([], _u64),
+    "mce_debug_fail_alloc": ([_i64], None),
     "mce_graph_create": ([_vp, _vp, _i64, _i32, _i32, _vp, _P(_vp)], _i32),
     "mce_graph_from_csr": ([_vp, _vp, _i32, _i64, _i32, _vp, _P(_vp)], _i32),
     "mce_graph_csr": ([_vp, _P(_i32), _P(_i64), _P(_vp), _P(_vp)], _i32),
@@ -230,6 +232,12 @@ def _check(st, what):
 
 def kernel_launches() -> int:
     return int(load().mce_kernel_launches())
+
+
+def debug_fail_alloc(after: int):
+    """Make the library's device allocation after `after` more successful ones
+    fail (MCE_ENOMEM); negative disarms."""
+    load().mce_debug_fail_alloc(int(after))
 
 
 def _ptr(t):
@@ -351,7 +359,8 @@ class Graph:
 
 def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, stream=None, list_buf=None,
               per_vertex=None, split=True, order_by_model=False, warps_per_block=0, blocks_per_sm=0,
-              time_limit_ms=0, subset=None, subproblem_budget=0, shared_words=0, split_nodes=0) -> Opts:
+              time_limit_ms=0, subset=None, subproblem_budget=0, shared_words=0, split_nodes=0,
+              queue_capacity=0) -> Opts:
     o = Opts()
     load().mce_opts_init(ctypes.byref(o))
     o.rank_kind = RANKS[rank] if isinstance(rank, str) else int(rank)
@@ -377,6 +386,7 @@ def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, s
         o.subset, o.subset_len = _ptr(subset), int(subset.numel() if hasattr(subset, "numel") else len(subset))
         o.subset_on_host = int(isinstance(subset, np.ndarray) or not subset.is_cuda)
     o.subproblem_budget = subproblem_budget
+    o.queue_capacity = queue_capacity
     return o
 
 
@@ -400,6 +410,17 @@ def enumerate_noalloc(g: Graph, rank_dev, seed: int = 0, stream=None) -> Result:
     r = ResultC()
     st = lib.mce_enumerate_noalloc(rp, cl, n.value, nnz.value, _ptr(rank_dev), seed, _stream_ptr(stream),
                                    ctypes.byref(r))
+    _check(st, "mce_enumerate_noalloc")
+    return _result(r, st)
+
+
+def enumerate_noalloc_csr(row_ptr, col, n: int, rank_dev, seed: int = 0, stream=None) -> Result:
+    """mce_enumerate_noalloc on caller device arrays (row_ptr int32[n+1], col
+    int32[nnz], rank int32[n]); the library checks them before use."""
+    lib = load()
+    r = ResultC()
+    st = lib.mce_enumerate_noalloc(_ptr(row_ptr), _ptr(col), int(n), int(col.numel()), _ptr(rank_dev), seed,
+                                   _stream_ptr(stream), ctypes.byref(r))
     _check(st, "mce_enumerate_noalloc")
     return _result(r, st)
 

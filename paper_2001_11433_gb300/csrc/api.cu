@@ -7,6 +7,22 @@ namespace mce {
 thread_local std::string g_last_error;
 std::atomic<uint64_t> g_launches{0};
 
+// Allocation-failure injection (mce_debug_fail_alloc): the allocation that
+// finds the counter at 0 fails; negative = off.
+static std::atomic<int64_t> g_fail_alloc_after{-1};
+
+mce_status dev_alloc(void **p, size_t bytes, cudaStream_t s, const char *what) {
+    int64_t k = g_fail_alloc_after.load();
+    while (k >= 0 && !g_fail_alloc_after.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 0) {
+        *p = nullptr;
+        g_last_error = std::string(what) + ": injected allocation failure";
+        return MCE_ENOMEM;
+    }
+    return cuda_status(cudaMallocAsync(p, bytes, s), what);
+}
+
 // Keep freed stream-ordered memory in the pool so that repeated calls do not
 // return it to the driver and allocate it again.
 static void init_pool_once() {
@@ -51,6 +67,8 @@ void mce_opts_init(mce_opts *o) {
 
 uint64_t mce_kernel_launches(void) { return g_launches.load(); }
 
+void mce_debug_fail_alloc(int64_t after) { g_fail_alloc_after.store(after < 0 ? -1 : after); }
+
 mce_status mce_graph_create(const int32_t *u, const int32_t *v, int64_t m, int32_t n, int32_t on_device, void *stream,
                             mce_graph **g) {
     if (!g || m < 0 || n < 0 || n >= (1 << 30) || (m > 0 && (!u || !v))) {
@@ -94,8 +112,8 @@ mce_status mce_graph_from_csr(const int32_t *row_ptr, const int32_t *col, int32_
     gr->nnz = nnz;
     gr->id_bits = bits_for(n > 0 ? (uint64_t)(n - 1) : 0);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    mce_status st = cuda_status(cudaMallocAsync((void **)&gr->row_ptr, ((size_t)n + 1) * 4, s), "cudaMallocAsync");
-    if (st == MCE_OK) st = cuda_status(cudaMallocAsync((void **)&gr->col, ((size_t)nnz + 4) * 4, s), "cudaMallocAsync");
+    mce_status st = dev_alloc((void **)&gr->row_ptr, ((size_t)n + 1) * 4, s, "cudaMallocAsync");
+    if (st == MCE_OK) st = dev_alloc((void **)&gr->col, ((size_t)nnz + 4) * 4, s, "cudaMallocAsync");
     if (st == MCE_OK)
         st = cuda_status(cudaMemcpyAsync(gr->row_ptr, row_ptr, ((size_t)n + 1) * 4, kind, s), "copy row_ptr");
     if (st == MCE_OK && nnz > 0)

@@ -350,10 +350,10 @@ mce_status check_csr(const mce_graph *g, cudaStream_t s) {
 mce_status build_csr(const int32_t *u, const int32_t *v, int64_t m, int32_t n, cudaStream_t s, mce_graph *g) {
     g->n = n;
     g->id_bits = bits_for(n > 0 ? (uint64_t)(n - 1) : 0);
-    MCE_CUDA(cudaMallocAsync((void **)&g->row_ptr, ((size_t)n + 1) * sizeof(int32_t), s));
+    MCE_TRY(dev_alloc((void **)&g->row_ptr, ((size_t)n + 1) * sizeof(int32_t), s, "cudaMallocAsync"));
     if (m == 0 || n == 0) {
         MCE_CUDA(cudaMemsetAsync(g->row_ptr, 0, ((size_t)n + 1) * sizeof(int32_t), s));
-        MCE_CUDA(cudaMallocAsync((void **)&g->col, 16, s));
+        MCE_TRY(dev_alloc((void **)&g->col, 16, s, "cudaMallocAsync"));
         g->nnz = 0;
         return MCE_OK;
     }
@@ -385,7 +385,7 @@ mce_status build_csr(const int32_t *u, const int32_t *v, int64_t m, int32_t n, c
     MCE_CUDA(cudaMemcpyAsync(&nnz, flag.as<int32_t>() + k, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     MCE_CUDA(cudaStreamSynchronize(s));
     g->nnz = nnz;
-    MCE_CUDA(cudaMallocAsync((void **)&g->col, ((size_t)nnz + 4) * sizeof(int32_t), s));
+    MCE_TRY(dev_alloc((void **)&g->col, ((size_t)nnz + 4) * sizeof(int32_t), s, "cudaMallocAsync"));
     MCE_CUDA(cudaMemsetAsync(g->row_ptr, 0, ((size_t)n + 1) * sizeof(int32_t), s));
     MCE_LAUNCH(k_compact_csr, grid_for(k, 256), 256, 0, s, keys.as<uint64_t>(), flag.as<int32_t>(), k, B, g->col,
                g->row_ptr);

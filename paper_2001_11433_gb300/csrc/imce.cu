@@ -502,7 +502,7 @@ template <class T> mce_status grow(T *&p, int64_t &cap, int64_t need, int64_t us
     int64_t nc = cap ? cap : 1024;
     while (nc < need) nc *= 2;
     T *q = nullptr;
-    MCE_CUDA(cudaMallocAsync((void **)&q, (size_t)nc * sizeof(T), s));
+    MCE_TRY(dev_alloc((void **)&q, (size_t)nc * sizeof(T), s, "index grow"));
     if (p && used) MCE_CUDA(cudaMemcpyAsync(q, p, (size_t)used * sizeof(T), cudaMemcpyDeviceToDevice, s));
     if (p) MCE_CUDA(cudaFreeAsync(p, s));
     p = q;
@@ -514,10 +514,20 @@ mce_status index_reserve_table(CliqueIndex &I, int64_t n_ids_after, cudaStream_t
     if (I.tcap >= 2 * n_ids_after && I.tcap > 0) return MCE_OK;
     int64_t nc = 1024;
     while (nc < 2 * n_ids_after) nc *= 2;
+    // the new table is allocated before the old one is freed, so a failed
+    // allocation leaves the index as it was
+    unsigned long long *tkey = nullptr;
+    int32_t *tid = nullptr;
+    MCE_TRY(dev_alloc((void **)&tkey, (size_t)nc * 8, s, "index table"));
+    const mce_status st = dev_alloc((void **)&tid, (size_t)nc * 4, s, "index table");
+    if (st != MCE_OK) {
+        cudaFreeAsync(tkey, s);
+        return st;
+    }
     if (I.tkey) MCE_CUDA(cudaFreeAsync(I.tkey, s));
     if (I.tid) MCE_CUDA(cudaFreeAsync(I.tid, s));
-    MCE_CUDA(cudaMallocAsync((void **)&I.tkey, (size_t)nc * 8, s));
-    MCE_CUDA(cudaMallocAsync((void **)&I.tid, (size_t)nc * 4, s));
+    I.tkey = tkey;
+    I.tid = tid;
     MCE_CUDA(cudaMemsetAsync(I.tid, 0, (size_t)nc * 4, s));
     I.tcap = nc;
     if (I.n_ids)
@@ -587,8 +597,8 @@ mce_status copy_graph(const mce_graph *src, cudaStream_t s, mce_graph **out) {
     g->n = src->n;
     g->nnz = src->nnz;
     g->id_bits = src->id_bits;
-    mce_status st = cuda_status(cudaMallocAsync((void **)&g->row_ptr, ((size_t)src->n + 1) * 4, s), "alloc");
-    if (st == MCE_OK) st = cuda_status(cudaMallocAsync((void **)&g->col, ((size_t)src->nnz + 4) * 4, s), "alloc");
+    mce_status st = dev_alloc((void **)&g->row_ptr, ((size_t)src->n + 1) * 4, s, "alloc");
+    if (st == MCE_OK) st = dev_alloc((void **)&g->col, ((size_t)src->nnz + 4) * 4, s, "alloc");
     if (st == MCE_OK)
         st = cuda_status(cudaMemcpyAsync(g->row_ptr, src->row_ptr, ((size_t)src->n + 1) * 4, cudaMemcpyDeviceToDevice, s),
                          "copy");
@@ -703,8 +713,8 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
     g2->n = n;
     g2->id_bits = B;
     g2->nnz = g->nnz + 2 * (int64_t)rho;
-    MCE_CUDA(cudaMallocAsync((void **)&g2->row_ptr, ((size_t)n + 1) * 4, s));
-    MCE_CUDA(cudaMallocAsync((void **)&g2->col, ((size_t)g2->nnz + 4) * 4, s));
+    MCE_TRY(dev_alloc((void **)&g2->row_ptr, ((size_t)n + 1) * 4, s, "alloc G'"));
+    MCE_TRY(dev_alloc((void **)&g2->col, ((size_t)g2->nnz + 4) * 4, s, "alloc G'"));
     MCE_TRY(exclusive_scan_i32(deg2.as<int32_t>(), g2->row_ptr, n, s));
     MCE_LAUNCH(k_merge_rows, grid_for((int64_t)n * 32, 256), 256, 0, s, g->row_ptr, g->col, h_ptr.as<int32_t>(),
                h_adj.as<int32_t>(), g2->row_ptr, n, g2->col);

@@ -41,6 +41,10 @@ inline mce_status cuda_status(cudaError_t e, const char *where) {
 
 // ------------------------------------------------------------------ scratch
 
+// Every device allocation of the library goes through this call, so that a
+// host-side test hook (mce_debug_fail_alloc) can make one of them fail.
+mce_status dev_alloc(void **p, size_t bytes, cudaStream_t s, const char *what);
+
 // Stream-ordered device buffer freed at scope exit.
 struct DevBuf {
     void *p = nullptr;
@@ -60,7 +64,7 @@ struct DevBuf {
         s = stream;
         bytes = nbytes;
         if (nbytes == 0) nbytes = 16;
-        return cuda_status(cudaMallocAsync(&p, nbytes, stream), "cudaMallocAsync");
+        return dev_alloc(&p, nbytes, stream, "cudaMallocAsync");
     }
     template <class T> T *as() const { return reinterpret_cast<T *>(p); }
 };

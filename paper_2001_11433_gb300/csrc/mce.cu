@@ -183,6 +183,7 @@ LaunchShape launch_shape(const mce_opts *o) {
     if (!o || o->shared_words <= 0) words = 0;
     else if (o->shared_words < words) words = o->shared_words & ~3;
     ls.smem_words = (int32_t)words;
+    ls.queue_capacity = (o && o->queue_capacity > 0) ? o->queue_capacity : 0;
     return ls;
 }
 
@@ -198,6 +199,7 @@ mce_status run_bk(BkParams &P, const LaunchShape &ls, int64_t req_max, int64_t c
     int64_t cap = ((int64_t)1 << 26) / P.slot_words;
     if (cap > ((int64_t)1 << 16)) cap = (int64_t)1 << 16;
     if (cap < 1024) cap = 1024;
+    if (ls.queue_capacity > 0) cap = ls.queue_capacity;
     P.qcap = cap;
     MCE_TRY(b.arena.alloc((size_t)P.qcap * P.slot_words * 4, s));
     MCE_TRY(b.qseq.alloc((size_t)P.qcap * 8, s));

@@ -9,6 +9,7 @@ struct LaunchShape {
     int32_t warps_per_block = 8;
     int32_t blocks_per_sm = 4;
     int32_t smem_words = 0;
+    int32_t queue_capacity = 0;   // task ring slots (0 = automatic)
 };
 
 LaunchShape launch_shape(const mce_opts *o);

@@ -48,13 +48,67 @@ __global__ void k_na_up_count(const int32_t *row_ptr, const int32_t *col, const 
 }
 
 __global__ void k_na_up_fill(const int32_t *row_ptr, const int32_t *col, const int32_t *rank, int32_t n,
-                             const int32_t *up_ptr, int32_t *up_col) {
+                             const int32_t *up_ptr, int32_t *up_col, int64_t up_cap) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         int32_t o = up_ptr[v];
         const int32_t rv = rank[v];
         for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e)
-            if (rank[col[e]] > rv) up_col[o++] = col[e];
+            if (rank[col[e]] > rv && o < up_cap) up_col[o++] = col[e];
     }
+}
+
+// Input checks, in two passes so that no pass reads through a value that an
+// earlier pass has not checked.  Bits of *bad:
+//   1 row_ptr[0] != 0 or row_ptr[n] != nnz     2 row_ptr decreases
+//   4 rank value outside [0, n)                8 col id outside [0, n)
+//  16 self loop                               32 row not strictly increasing
+//  64 (x, y) present without (y, x)          128 two vertices with one rank value
+__global__ void k_na_check_ptr(const int32_t *row_ptr, const int32_t *rank, int32_t n, int64_t nnz, int32_t *bad) {
+    int32_t b = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (row_ptr[v] > row_ptr[v + 1]) b |= 2;
+        if (rank[v] < 0 || rank[v] >= n) b |= 4;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz)) b |= 1;
+    if (b) atomicOr(bad, b);
+}
+
+// seen: int32[n], zero on entry
+__global__ void k_na_check_adj(const int32_t *row_ptr, const int32_t *col, const int32_t *rank, int32_t n,
+                               int32_t *seen, int32_t *bad) {
+    int32_t b = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (atomicExch(&seen[rank[v]], 1) != 0) b |= 128;
+        const int32_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
+        for (int32_t e = e0; e < e1; ++e) {
+            const int32_t x = col[e];
+            if (x < 0 || x >= n) {
+                b |= 8;
+                continue;
+            }
+            if (x == v) b |= 16;
+            if (e > e0 && col[e - 1] >= x) b |= 32;
+            // (v, x) needs (x, v): binary search of v in x's row (sorted if the row checks pass)
+            int32_t lo = row_ptr[x], hi = row_ptr[x + 1];
+            while (lo < hi) {
+                const int32_t mid = lo + ((hi - lo) >> 1);
+                if (col[mid] < (int32_t)v) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= row_ptr[x + 1] || col[lo] != (int32_t)v) b |= 64;
+        }
+    }
+    if (b) atomicOr(bad, b);
+}
+
+const char *na_check_text(int32_t b) {
+    if (b & 1) return "mce_enumerate_noalloc: row_ptr[0] must be 0 and row_ptr[n] must equal nnz";
+    if (b & 2) return "mce_enumerate_noalloc: row_ptr decreases";
+    if (b & 4) return "mce_enumerate_noalloc: a rank value lies outside [0, n)";
+    if (b & 8) return "mce_enumerate_noalloc: a column id lies outside [0, n)";
+    if (b & 16) return "mce_enumerate_noalloc: self loop in the CSR";
+    if (b & 32) return "mce_enumerate_noalloc: a row is not strictly increasing (unsorted or repeated ids)";
+    if (b & 64) return "mce_enumerate_noalloc: the CSR is not symmetric ((x, y) without (y, x))";
+    return "mce_enumerate_noalloc: rank is not a permutation (two vertices share a value)";
 }
 
 // per-tile sums
@@ -200,6 +254,10 @@ extern "C" mce_status mce_enumerate_noalloc(const int32_t *row_ptr, const int32_
         g_last_error = "mce_enumerate_noalloc: bad arguments";
         return MCE_EINVAL;
     }
+    if (n == 0 && nnz != 0) {
+        g_last_error = "mce_enumerate_noalloc: nnz must be 0 when n is 0";
+        return MCE_EINVAL;
+    }
     if ((int64_t)n + 1 > kMaxScan) {
         g_last_error = "mce_enumerate_noalloc: more vertices than this entry point handles (4194303)";
         return MCE_EINVAL;
@@ -217,6 +275,7 @@ extern "C" mce_status mce_enumerate_noalloc(const int32_t *row_ptr, const int32_
     int32_t *flag = cv.take<int32_t>((size_t)n + 1);
     int32_t *sums = cv.take<int32_t>(kTile + 1);
     int32_t *order = cv.take<int32_t>((size_t)n + 1);
+    int32_t *bad = cv.take<int32_t>(1);
     if (!cv.ok) {
         g_last_error = "mce_enumerate_noalloc: graph needs more than the MCE_NOALLOC_SCRATCH_BYTES scratch";
         return MCE_EINVAL;
@@ -228,12 +287,29 @@ extern "C" mce_status mce_enumerate_noalloc(const int32_t *row_ptr, const int32_
     int32_t n_act = 0;
     unsigned long long hreq[2] = {0, 0};
     if (n > 0) {
+        // the caller's CSR and rank, checked before anything reads through them
+        int32_t hbad = 0;
+        MCE_CUDA(cudaMemsetAsync(bad, 0, 4, s));
+        MCE_LAUNCH(k_na_check_ptr, grid_for(n, 256), 256, 0, s, row_ptr, rank, n, nnz, bad);
+        MCE_CUDA(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s));
+        MCE_CUDA(cudaStreamSynchronize(s));
+        if (hbad == 0) {
+            MCE_CUDA(cudaMemsetAsync(order, 0, (size_t)n * 4, s));   // `order` serves as the rank-seen flags
+            MCE_LAUNCH(k_na_check_adj, grid_for(n, 256), 256, 0, s, row_ptr, col, rank, n, order, bad);
+            MCE_CUDA(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s));
+            MCE_CUDA(cudaStreamSynchronize(s));
+        }
+        if (hbad) {
+            g_last_error = na_check_text(hbad);
+            return MCE_EINVAL;
+        }
         // Γ+ lists by the caller's rank
         MCE_LAUNCH(k_na_up_count, grid_for(n, 256), 256, 0, s, row_ptr, col, rank, n, flag);
         MCE_LAUNCH(k_na_tile_sum, (unsigned)tiles, 256, 0, s, flag, (int64_t)n, sums);
         MCE_LAUNCH(k_na_scan_sums, 1, 256, 0, s, sums, tiles);
         MCE_LAUNCH(k_na_scan_apply, (unsigned)tiles, 256, 0, s, flag, up_ptr, (int64_t)n, sums);
-        MCE_LAUNCH(k_na_up_fill, grid_for(n, 256), 256, 0, s, row_ptr, col, rank, n, up_ptr, up_col);
+        MCE_LAUNCH(k_na_up_fill, grid_for(n, 256), 256, 0, s, row_ptr, col, rank, n, up_ptr, up_col,
+                   (int64_t)(nnz / 2 + 16));
         // trivial subproblems, sizes, and the list of non-trivial ones (vertex order)
         MCE_LAUNCH(k_na_prepass, grid_for(n, 256), 256, 0, s, row_ptr, up_ptr, n, hash_seed, out, flag, reqc);
         MCE_LAUNCH(k_na_tile_sum, (unsigned)tiles, 256, 0, s, flag, (int64_t)n, sums);

@@ -95,8 +95,17 @@ def test_batched_4096_sampled_graphs(gpu_lib):
     assert 0 < len(ok) < len(gptr) - 1 and not tot.complete
     assert (np.diff(w.u) >= 0).all()            # edges come graph by graph, in increasing u
     bounds = np.searchsorted(w.u, gptr)
-    cand = [i for i in ok if gptr[i + 1] - gptr[i] <= 400]
-    sample = np.random.default_rng(77).choice(cand, min(16, len(cand)), replace=False)
+    # stratified over the whole vertex range: up to 3 finished graphs from each
+    # doubling of n (32-63, 64-127, ..., 1024-2048), so that the large sparse
+    # graphs (wide candidate sets, many handed-over pieces) are compared too
+    sizes = np.diff(gptr)
+    rng = np.random.default_rng(77)
+    sample = []
+    for lo in (32, 64, 128, 256, 512, 1024):
+        hi = 2 * lo if lo < 1024 else 2049
+        pool = [i for i in ok if lo <= sizes[i] < hi]
+        sample += list(rng.choice(pool, min(3, len(pool)), replace=False))
+    assert max(sizes[sample]) >= 1024
     for i in sample:
         a, b = int(gptr[i]), int(gptr[i + 1])
         e0, e1 = int(bounds[i]), int(bounds[i + 1])
@@ -105,3 +114,43 @@ def test_batched_4096_sampled_graphs(gpu_lib):
         o = O.parmce(og, O.rank(og, "degen"), subset=sub, per_vertex=True, threads=8)
         assert int(counts[i]) == int(o.per_vertex["count"].sum()), i      # per-vertex arrays follow `sub`
         assert int(hashes[i]) == int(o.per_vertex["hash"].astype(object).sum()) % (1 << 64), i
+
+
+def _delta_key(d):
+    return (d.applied, d.new_count, d.new_hash, list(d.new_hist), d.sub_count, d.sub_hash, list(d.sub_hist), d.alive)
+
+
+def test_chung_lu_stream_full(gpu_lib):
+    """The dynamic workload at full size: the Chung-Lu base graph (n = 500,000,
+    about 2M edges) and the whole stream of 10^6 new edges in its 45 batches.
+    Every batch's (applied, Λnew and Λdel count, hash and histogram, alive
+    cliques) equals the oracle's (Algorithms 6, 9 and 8), both through
+    imce_add_edges and through the serving loop that the benchmark times."""
+    mce = gpu_lib
+    w = graphgen.chung_lu_stream()
+    su, sv = w.extra["stream_u"], w.extra["stream_v"]
+    sizes = w.extra["batch_sizes"]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    og = O.Graph(w.n, w.u, w.v)
+    ost = O.Imce(og, threads=8)
+    expect = []
+    for i in range(len(sizes)):
+        rho, onew, odel = ost.add(su[offs[i]:offs[i + 1]], sv[offs[i]:offs[i + 1]], want_list=False)
+        expect.append((rho, onew.count, onew.hash, list(onew.hist), odel.count, odel.hash, list(odel.hist),
+                       ost.alive))
+    assert offs[-1] == 1_000_000 and len(sizes) == 45
+    g = mce.Graph(w.n, _t(w.u), _t(w.v))
+    st = mce.Imce(g)
+    for i in range(len(sizes)):
+        d = st.add_edges(_t(su[offs[i]:offs[i + 1]]), _t(sv[offs[i]:offs[i + 1]]))
+        assert _delta_key(d) == expect[i], i
+    st.close()
+    # the serving loop: one tenant, every batch submitted at once, run in order
+    srv = mce.Server(slots=4)
+    t = srv.add_tenant(g)
+    ids = [srv.submit(t, su[offs[i]:offs[i + 1]], sv[offs[i]:offs[i + 1]], arrival_ms=0.0)
+           for i in range(len(sizes))]
+    infos = [srv.wait(i) for i in ids]
+    srv.close()
+    for i, info in enumerate(infos):
+        assert info.status == 0 and _delta_key(info.delta) == expect[i], i
