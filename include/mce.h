@@ -119,8 +119,8 @@ typedef struct {
     uint64_t subproblem_budget;
     /* Slots of the device task ring that carries handed-over pieces (0 =
      * automatic: 64 MiB of records, 1024..65536 slots).  A full ring refuses a
-     * hand-over and the donor keeps the work, so any capacity >= 1 gives the
-     * same result. */
+     * hand-over and the donor keeps the work, so any capacity gives the same
+     * result; values below 2 count as 2. */
     int32_t queue_capacity;
 } mce_opts;
 

@@ -183,7 +183,9 @@ LaunchShape launch_shape(const mce_opts *o) {
     if (!o || o->shared_words <= 0) words = 0;
     else if (o->shared_words < words) words = o->shared_words & ~3;
     ls.smem_words = (int32_t)words;
-    ls.queue_capacity = (o && o->queue_capacity > 0) ? o->queue_capacity : 0;
+    // the ring's sequence numbers tell "published for ticket p" (p + 1) from
+    // "free for ticket p + cap" (p + cap) only when cap >= 2
+    ls.queue_capacity = (o && o->queue_capacity > 0) ? (o->queue_capacity < 2 ? 2 : o->queue_capacity) : 0;
     return ls;
 }
 
