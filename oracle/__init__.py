@@ -69,7 +69,7 @@ def _L():
                 "or_triangles": ([vp, vp], None),
                 "or_rank_from_key": ([i32, vp, vp], None),
                 "or_ttt_whole": ([vp, vp], None),
-                "or_parmce": ([vp, vp, vp, i64, i32, vp, vp, vp, vp], i32),
+                "or_parmce": ([vp, vp, vp, i64, i32, vp, vp, vp, vp, u64, vp], i32),
                 "or_canonical_batch": ([vp, vp, vp, i64, vp, vp], i64),
                 "or_imce_alg": ([vp, vp, vp, i64, vp, vp], None),
                 "or_imce_diff": ([vp, vp, vp, i64, vp, vp], None),
@@ -214,25 +214,31 @@ def ttt_whole(g: Graph, want_list: bool = False, seed: int = 0) -> Result:
 
 
 def parmce(g: Graph, rank_arr, subset=None, threads: int = 1, want_list: bool = False,
-           per_vertex: bool = False, seed: int = 0) -> Result:
+           per_vertex: bool = False, seed: int = 0, node_cap: int = 0) -> Result:
     """Algorithm 5 run one subproblem at a time (on `threads` host threads).
 
     With `subset`, only those vertices' subproblems run; per-vertex arrays
-    are indexed like `subset` (or by vertex id when subset is None)."""
+    are indexed like `subset` (or by vertex id when subset is None).  With
+    `node_cap`, a subproblem whose search tree has more than node_cap nodes
+    is given up, left out of the result and flagged in per_vertex["over"]."""
     lib = _L()
     rank_arr = _i32(rank_arr)
     sub = None if subset is None else _i32(subset)
     ns = g.n if sub is None else len(sub)
     pv = [np.zeros(ns, dtype=np.uint64) for _ in range(3)] if per_vertex else None
+    over = np.zeros(max(ns, 1), dtype=np.uint8) if node_cap else None
     out = lib.or_out_new(int(want_list), seed)
     try:
         used = lib.or_parmce(g._h, rank_arr.ctypes.data, None if sub is None else sub.ctypes.data, ns,
                              threads, out,
-                             *(p.ctypes.data for p in pv) if pv else (None, None, None))
+                             *(p.ctypes.data for p in pv) if pv else (None, None, None),
+                             int(node_cap), None if over is None else over.ctypes.data)
         r = _result(out, want_list)
         r.per_vertex["threads"] = int(used)
         if pv:
             r.per_vertex.update(count=pv[0], hash=pv[1], nodes=pv[2])
+        if over is not None:
+            r.per_vertex["over"] = over[:ns].astype(bool)
         return r
     finally:
         lib.or_out_free(out)

@@ -283,7 +283,7 @@ static void out_merge(or_out *dst, const or_out *src) {
     dst->count += src->count;
     dst->hash += src->hash;
     dst->nodes += src->nodes;
-    for (int i = 0; i < OR_MAX_HIST; ++i) dst->hist[i] += src->hist[i];
+    for (int i = 0; i <= src->max_size && i < OR_MAX_HIST; ++i) dst->hist[i] += src->hist[i];
     if (src->max_size > dst->max_size) dst->max_size = src->max_size;
     dst->overflow |= src->overflow;
     if (!(dst->want_list && src->want_list)) return;
@@ -302,6 +302,15 @@ static void out_merge(or_out *dst, const or_out *src) {
         dst->n_cl++;
         dst->off[dst->n_cl] = dst->nnz;
     }
+}
+
+/* empty the accumulator, keeping its buffers */
+static void out_reset(or_out *o) {
+    for (int i = 0; i <= o->max_size && i < OR_MAX_HIST; ++i) o->hist[i] = 0;
+    o->count = o->hash = o->nodes = 0;
+    o->max_size = 0;
+    o->overflow = 0;
+    o->n_cl = o->nnz = 0;
 }
 
 uint64_t or_out_count(const or_out *o) { return o->count; }
@@ -420,6 +429,8 @@ typedef struct {
     or_out *out;
     int32_t *K;          /* current clique, K[0..klen) */
     const excl_set *ex;  /* NULL for plain TTT */
+    uint64_t stop_after; /* abandon once out->nodes passes this (0 = never) */
+    int abandoned;
 } ttt_ctx;
 
 /* TTT(G, K, cand, fini) of Algorithm 1 (Algorithm 9 when ctx->ex is set).
@@ -430,6 +441,10 @@ typedef struct {
 static void ttt(ttt_ctx *c, int32_t klen, int32_t *cand, int32_t nc, int32_t *fini, int32_t nf) {
     const or_graph *g = c->g;
     c->out->nodes++;
+    if (c->stop_after && c->out->nodes > c->stop_after) {   /* node cap: give the search up */
+        c->abandoned = 1;
+        return;
+    }
     if (nc == 0 && nf == 0) {           /* K is maximal */
         emit(c->out, c->K, klen);
         return;
@@ -468,6 +483,7 @@ static void ttt(ttt_ctx *c, int32_t klen, int32_t *cand, int32_t nc, int32_t *fi
         int32_t nfq = isect(fin, nf, nbr(g, q), deg(g, q), fq);
         c->K[klen] = q;
         ttt(c, klen + 1, cq, ncq, fq, nfq);
+        if (c->abandoned) break;
         nc = erase_sorted(cand, nc, q);
         nf = insert_sorted(fin, nf, q);
     }
@@ -482,7 +498,7 @@ void or_ttt_whole(const or_graph *g, or_out *out) {
     int32_t *cand = (int32_t *)malloc(((size_t)g->n + 1) * sizeof(int32_t));
     int32_t *K = (int32_t *)malloc(((size_t)g->n + 1) * sizeof(int32_t));
     for (int32_t v = 0; v < g->n; ++v) cand[v] = v;
-    ttt_ctx c = {g, out, K, NULL};
+    ttt_ctx c = {g, out, K, NULL, 0, 0};
     if (g->n > 0) ttt(&c, 0, cand, g->n, NULL, 0);
     free(cand);
     free(K);
@@ -494,7 +510,8 @@ void or_ttt_whole(const or_graph *g, or_out *out) {
 
 /* Subproblem of v: K = {v}, cand = higher-ranked neighbours, fini = the
  * lower-ranked ones, then TTT on G_v. */
-static void parmce_one(const or_graph *g, const int32_t *rank, int32_t v, or_out *out, int32_t *K) {
+static int parmce_one(const or_graph *g, const int32_t *rank, int32_t v, or_out *out, int32_t *K,
+                      uint64_t node_cap) {
     int32_t d = deg(g, v);
     const int32_t *nv = nbr(g, v);
     int32_t *cand = (int32_t *)malloc((size_t)(d + 1) * sizeof(int32_t));
@@ -505,10 +522,11 @@ static void parmce_one(const or_graph *g, const int32_t *rank, int32_t v, or_out
         if (rank[w] > rank[v]) cand[nc++] = w; else fini[nf++] = w;
     }
     K[0] = v;
-    ttt_ctx c = {g, out, K, NULL};
+    ttt_ctx c = {g, out, K, NULL, node_cap ? out->nodes + node_cap : 0, 0};
     ttt(&c, 1, cand, nc, fini, nf);
     free(cand);
     free(fini);
+    return c.abandoned;
 }
 
 typedef struct {
@@ -520,6 +538,8 @@ typedef struct {
     or_out *outs;            /* per thread (array of or_out*) */
     or_out **thread_out;
     uint64_t *pv_count, *pv_hash, *pv_nodes;
+    uint64_t node_cap;       /* abandon a subproblem whose tree passes this many nodes (0 = never) */
+    uint8_t *over;           /* per subset index: 1 = abandoned */
 } pm_shared;
 
 static void *pm_worker(void *arg) {
@@ -527,25 +547,37 @@ static void *pm_worker(void *arg) {
     pm_shared *s = (pm_shared *)a[0];
     or_out *out = (or_out *)a[1];
     int32_t *K = (int32_t *)malloc(((size_t)s->g->n + 2) * sizeof(int32_t));
+    /* with a node cap each subproblem runs into its own accumulator, merged
+     * only when it finished within the cap */
+    or_out *one = s->node_cap ? or_out_new(out->want_list, out->seed) : NULL;
     for (;;) {
         int64_t i = __atomic_fetch_add(&s->next, 1, __ATOMIC_RELAXED);
         if (i >= s->nsub) break;
         int32_t v = s->subset ? s->subset[i] : (int32_t)i;
-        uint64_t c0 = out->count, h0 = out->hash, n0 = out->nodes;
-        parmce_one(s->g, s->rank, v, out, K);
-        if (s->pv_count) s->pv_count[i] = out->count - c0;
-        if (s->pv_hash) s->pv_hash[i] = out->hash - h0;
-        if (s->pv_nodes) s->pv_nodes[i] = out->nodes - n0;
+        or_out *dst = one ? one : out;
+        if (one) out_reset(one);
+        uint64_t c0 = dst->count, h0 = dst->hash, n0 = dst->nodes;
+        int ab = parmce_one(s->g, s->rank, v, dst, K, s->node_cap);
+        if (s->pv_count) s->pv_count[i] = dst->count - c0;
+        if (s->pv_hash) s->pv_hash[i] = dst->hash - h0;
+        if (s->pv_nodes) s->pv_nodes[i] = dst->nodes - n0;
+        if (s->over) s->over[i] = (uint8_t)ab;
+        if (one && !ab) out_merge(out, one);
     }
+    or_out_free(one);
     free(K);
     return NULL;
 }
 
 /* Run the subproblems of `subset` (all vertices when NULL) on `threads`
  * host threads, one whole subproblem per thread at a time.  Per-subproblem
- * count/hash/tree-node arrays (indexed like subset) are optional. */
+ * count/hash/tree-node arrays (indexed like subset) are optional.  With
+ * node_cap > 0 a subproblem is given up at its (node_cap + 1)-th tree node:
+ * it is flagged in `over` (optional), its per-subproblem entries hold what it
+ * reached, and it adds nothing to `out`. */
 int32_t or_parmce(const or_graph *g, const int32_t *rank, const int32_t *subset, int64_t nsub,
-                  int32_t threads, or_out *out, uint64_t *pv_count, uint64_t *pv_hash, uint64_t *pv_nodes) {
+                  int32_t threads, or_out *out, uint64_t *pv_count, uint64_t *pv_hash, uint64_t *pv_nodes,
+                  uint64_t node_cap, uint8_t *over) {
     pm_shared s;
     memset(&s, 0, sizeof(s));
     s.g = g;
@@ -555,6 +587,8 @@ int32_t or_parmce(const or_graph *g, const int32_t *rank, const int32_t *subset,
     s.pv_count = pv_count;
     s.pv_hash = pv_hash;
     s.pv_nodes = pv_nodes;
+    s.node_cap = node_cap;
+    s.over = over;
     if (threads < 1) threads = 1;
     if (threads == 1) {
         void *a[2] = {&s, out};
@@ -655,7 +689,7 @@ static void imce_new(const or_graph *gp, const int32_t *hu, const int32_t *hv, i
         excl_set ex = {keys, idx, rho, i};
         K[0] = u;
         K[1] = v;
-        ttt_ctx c = {gp, out, K, &ex};
+        ttt_ctx c = {gp, out, K, &ex, 0, 0};
         ttt(&c, 2, cand, nc, NULL, 0);
         free(cand);
     }
@@ -842,7 +876,7 @@ or_imce *or_imce_open(const or_graph *g0, uint64_t seed, int32_t threads) {
     for (int32_t a = 0; a < g0->n; ++a) key[a] = (double)deg(g0, a);
     or_rank_from_key(g0->n, key, rank);
     or_out *all = or_out_new(1, seed);
-    or_parmce(s->g, rank, NULL, 0, threads, all, NULL, NULL, NULL);
+    or_parmce(s->g, rank, NULL, 0, threads, all, NULL, NULL, NULL, 0, NULL);
     cs_from_out(&s->C, all);
     s->alive = all->n_cl;
     or_out_free(all);

@@ -478,3 +478,28 @@ def test_tree_nodes_hand_traced_example():
     r = O.parmce(g, np.arange(d["n"], dtype=np.int32), per_vertex=True)
     assert list(r.per_vertex["nodes"]) == d["per_vertex_identity_rank_nodes"]
     assert list(r.per_vertex["count"]) == d["per_vertex_identity_rank_cliques"]
+
+
+@pytest.mark.parametrize("threads", [1, 3])
+def test_parmce_node_cap(threads):
+    """The per-subproblem node cap gives up exactly the subproblems whose
+    search tree has more nodes than the cap, and the result then covers
+    the other subproblems only."""
+    u, v = graphgen.er(150, 0.3, 99)
+    g = O.Graph(150, u, v)
+    rk = O.rank(g, "degen")
+    full = O.parmce(g, rk, per_vertex=True, want_list=True)
+    nodes = full.per_vertex["nodes"]
+    cap = int(np.percentile(nodes, 80))
+    r = O.parmce(g, rk, per_vertex=True, node_cap=cap, threads=threads, want_list=True)
+    over = r.per_vertex["over"]
+    assert np.array_equal(over, nodes > cap) and 0 < over.sum() < 150
+    keep = ~over
+    assert np.array_equal(r.per_vertex["count"][keep], full.per_vertex["count"][keep])
+    assert np.array_equal(r.per_vertex["nodes"][keep], nodes[keep])
+    assert (r.per_vertex["nodes"][over] == cap + 1).all()
+    assert r.count == int(full.per_vertex["count"][keep].sum())
+    assert r.nodes == int(nodes[keep].sum())
+    # the kept cliques are exactly those whose lowest-ranked vertex has a kept subproblem
+    low = {c: min(c, key=lambda x: rk[x]) for c in full.cliques}
+    assert r.cliques == sorted(c for c in full.cliques if keep[low[c]])
