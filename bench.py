@@ -7,12 +7,22 @@ most 2^24 nodes.  The full graph has far more maximal cliques than any
 implementation can enumerate in a benchmark (scale 16 already exceeds 1.2e10);
 the cap removes 17 of the 173,824 non-trivial subproblems and keeps about
 1.5e9 cliques.  The capped set is fixed by the algorithm (tree size under the
-stated rank and pivot rule), found once in an untimed sizing pass.
+stated rank and pivot rule), found in an untimed sizing pass and checked
+against the oracle's list (tests/golden/rmat_18_capped.json).  The 17 left
+out are far beyond a benchmark: 120 s of search on them reached 9.4e11 tree
+nodes and 4.0e11 cliques without finishing (vertex 0 alone 8.7e11 nodes).
 
 One step = the whole static path on input already resident in device memory:
 CSR ingest of the raw edge samples, core-number ranking, Γ+ lists,
 subproblem scheduling and the persistent search kernel over the fixed set,
 ending with the summary (count, histogram, set hash) read back.
+
+After the timed region the same line also reports the rest of the metric:
+the rank comparison on the Chung-Lu 1.7M graph with planted cliques (rank
+and enumeration time per rank, learned vs degree, degeneracy and triangles,
+with makespan and imbalance: key "c3_ranks") and the incremental serving
+loop on the Chung-Lu 500k graph with its 10^6-edge stream (edges/s, p50/p99
+batch latency, per-batch latency against change size: key "c5_serving").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batched   # 4,096 disjoint G(n, p), batched plan
@@ -150,7 +160,7 @@ def k_bk_traffic(tree_nodes: int):
             if hashlib.sha256(f.read()).hexdigest() != digest:
                 return None        # the kernel changed since the counters were taken
     return K_BK_TRAFFIC["bytes"] * tree_nodes / K_BK_TRAFFIC["tree_nodes"]
-CPU_SAMPLE_MAX_CAND = 150    # the CPU baseline samples subproblems with |Γ+(v)| <= this
+CPU_NODE_BUDGET = 2_000_000   # tree nodes of the subproblem sample the CPU baseline times
 
 
 def workload():
@@ -158,50 +168,84 @@ def workload():
     return graphgen.rmat_18()
 
 
-# --------------------------------------------------------------------------- reference arm (CPU oracle)
+def capped_vertices():
+    """Subproblems of the R-MAT 18 workload whose search tree (degeneracy rank)
+    has more than TREE_CAP nodes, as the oracle found them
+    (tests/golden/rmat_18_capped.json, written by tests/golden/make_golden.py);
+    None if that file is absent."""
+    p = os.path.join(ROOT, "tests", "golden", "rmat_18_capped.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    assert d["tree_cap"] == TREE_CAP
+    return np.array(d["capped_vertices"], dtype=np.int32)
 
-def cpu_sample(w, threads, target_s=15.0, seed=7):
-    """Time the oracle's per-vertex decomposition on a seeded sample of the
-    workload's subproblems; returns (cliques/s, cliques, seconds, description).
-    Candidates for the sample: vertices with 1 <= |Γ+(v)| <= CPU_SAMPLE_MAX_CAND
-    (computed with the oracle), whose trees are small enough for a bounded run."""
+
+def sample_prefix(subset, nodes, budget, seed):
+    """A seeded permutation of the benchmark set, cut before the first
+    subproblem that would take the sample past `budget` tree nodes.  No
+    subproblem is skipped for its size: the sample is a plain prefix."""
+    perm = np.random.default_rng(seed).permutation(subset)
+    cum = np.cumsum(nodes[perm].astype(np.float64))
+    k = int(np.searchsorted(cum, budget, side="right"))
+    return np.sort(perm[:max(k, 1)]).astype(np.int32)
+
+
+def cpu_baseline_same_set(w, sample, repeats=3):
+    """Time the oracle (Algorithm 5 + Algorithm 1, degeneracy rank) on a
+    sample of the benchmark set: one host thread and all host threads, median
+    of `repeats` runs each (graph and rank built untimed).  Returns a dict."""
     import oracle as O
     g = O.Graph(w.n, w.u, w.v)
     rk = O.rank(g, "degen")
-    rp, col = g.csr()
-    d = np.diff(rp)
-    src = np.repeat(np.arange(w.n), d)
-    c = np.bincount(src[rk[col] > rk[src]], minlength=w.n)
-    pool = np.nonzero((c >= 1) & (c <= CPU_SAMPLE_MAX_CAND))[0]
-    rng = np.random.default_rng(seed)
-    verts = rng.permutation(pool).astype(np.int32)
-    done, cl, el, size = 0, 0, 0.0, 256
-    while el < target_s and done < len(verts):
-        sub = verts[done:done + size]
-        t0 = time.perf_counter()
-        r = O.parmce(g, rk, subset=sub, threads=threads)
-        el += time.perf_counter() - t0
-        cl += r.count
-        done += len(sub)
-        size *= 2
-    desc = (f"oracle ParMCE (Algorithm 5 + Algorithm 1, degeneracy rank, {threads} threads) on {done} subproblems "
-            f"drawn by a seeded permutation from the {len(pool)} with 1 <= |Γ+(v)| <= {CPU_SAMPLE_MAX_CAND}; "
-            f"{cl} cliques in {el:.1f} s")
-    return cl / el if el > 0 else 0.0, cl, el, desc
+    out = {}
+    for label, th in (("single_thread", 1), ("all_threads", os.cpu_count() or 1)):
+        ts, r = [], None
+        for _ in range(repeats):
+            t0 = time.perf_counter()
+            r = O.parmce(g, rk, subset=sample, threads=th, node_cap=TREE_CAP)
+            ts.append(time.perf_counter() - t0)
+        el = float(np.median(ts))
+        out[label] = {"threads": th, "seconds": el, "cliques": r.count, "tree_nodes": r.nodes,
+                      "cliques_per_s": r.count / el if el > 0 else 0.0, "hash": f"{r.hash:#018x}",
+                      "runs_s": ts}
+    return out
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import oracle as O
     w = workload()
     threads = os.cpu_count() or 1
-    vals = []
+    g = O.Graph(w.n, w.u, w.v)
+    rk = O.rank(g, "degen")
+    capped = capped_vertices()
+    pool = np.setdiff1d(np.arange(w.n, dtype=np.int32), capped if capped is not None else [])
+    perm = np.random.default_rng(100).permutation(pool).astype(np.int32)
+    target = max(2.0, 60.0 / max(1, args.warmup + args.steps))
+    vals, pos, descs = [], 0, []
     for i in range(args.warmup + args.steps):
-        v, cl, el, desc = cpu_sample(w, threads, target_s=max(2.0, 20.0 / max(1, args.steps)), seed=100 + i)
+        cl, el, done, chunk = 0, 0.0, 0, 256
+        while el < target and pos < len(perm):
+            sub = perm[pos:pos + chunk]
+            t0 = time.perf_counter()
+            r = O.parmce(g, rk, subset=sub, threads=threads, node_cap=TREE_CAP)
+            el += time.perf_counter() - t0
+            cl += r.count
+            pos += len(sub)
+            done += len(sub)
+            chunk *= 2
         if i >= args.warmup:
-            vals.append(v)
+            vals.append(cl / el if el > 0 else 0.0)
+            descs.append(done)
     value = float(np.median(vals)) if vals else 0.0
+    desc = (f"oracle ParMCE (Algorithm 5 + Algorithm 1, degeneracy rank, {threads} threads, node cap {TREE_CAP}) "
+            f"on consecutive chunks of one seeded permutation of the benchmark set (every vertex except the "
+            f"{0 if capped is None else len(capped)} whose tree passes the cap); {int(np.median(descs)) if descs else 0} "
+            f"subproblems per timed step (median), value = median over steps of cliques / seconds")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "int32",
@@ -311,9 +355,38 @@ def run_ours(args):
     peak_ops = POPC_PER_CLK_PER_SM * props.multi_processor_count * sm_mhz * 1e6
     kern_s = float(np.mean(search_ms)) / 1000.0
     achieved = float(np.mean(word_ops)) / kern_s if kern_s > 0 else 0.0
-    cpu_v, cpu_cl, cpu_el, cpu_desc = (None, None, None, "skipped")
+    # the capped set must be the one the oracle found (tests/golden/rmat_18_capped.json)
+    capped = capped_vertices()
+    capped_match = None
+    if capped is not None and args.sample >= 1.0:
+        capped_match = bool(np.array_equal(np.nonzero(nodes > TREE_CAP)[0], capped))
+        assert capped_match, "capped subproblems differ from the oracle's"
+    cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": "skipped"}
     if not args.no_cpu_baseline:
-        cpu_v, cpu_cl, cpu_el, cpu_desc = cpu_sample(w, os.cpu_count() or 1, target_s=args.cpu_seconds)
+        sample = sample_prefix(subset_host, nodes, CPU_NODE_BUDGET, seed=7)
+        base = cpu_baseline_same_set(w, sample)
+        # the GPU on the very same subproblems (enumeration time: Γ+ lists, prepass, search)
+        gs = mce.Graph(w.n, dev_u, dev_v)
+        gpu_runs = [mce.enumerate_cliques(gs, rank="degen", subset=torch.from_numpy(sample).cuda(),
+                                          blocks_per_sm=BLOCKS_PER_SM, split_nodes=SPLIT_NODES) for _ in range(3)]
+        gs.close()
+        assert all(x.count == base["all_threads"]["cliques"] for x in gpu_runs)
+        assert all(f"{x.hash:#018x}" == base["single_thread"]["hash"] for x in gpu_runs)
+        gpu_ms = float(np.median([x.ms_enum for x in gpu_runs]))
+        cpu = {"value": base["all_threads"]["cliques_per_s"], "unit": UNIT, "cores": base["all_threads"]["threads"],
+               "kind": "oracle",
+               "sample": (f"{len(sample)} subproblems: a seeded permutation of the benchmark set cut before the first "
+                          f"subproblem that would pass {CPU_NODE_BUDGET} tree nodes (no size filter); "
+                          f"{base['all_threads']['cliques']} cliques, {base['all_threads']['tree_nodes']} tree nodes; "
+                          "oracle ParMCE with the degeneracy rank, median of 3 runs, graph and rank built untimed"),
+               "single_thread": base["single_thread"], "all_threads": base["all_threads"],
+               "gpu_same_sample": {"enumerate_ms": gpu_ms, "cliques_per_s": gpu_runs[0].count / (gpu_ms / 1e3),
+                                   "note": "mce_enumerate on the same subproblems, ms_enum (rank excluded like the "
+                                           "oracle's), median of 3"}}
+    secondary = {}
+    if not args.no_secondary:
+        secondary["c3_ranks"] = measure_ranks(mce, steps=3, warmup=1)
+        secondary["c5_serving"] = measure_serve(mce)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -338,9 +411,11 @@ def run_ours(args):
                 "d2h_bytes_per_step": 8 * (16 + 1024) + 8 * 8},
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": cpu_desc},
+        "cpu_baseline": cpu,
+        "capped_set_matches_oracle": capped_match,
+        "balance": balance_stats(res),
         "peaks_source": peak_src,
+        **secondary,
     }
     print(json.dumps(line), flush=True)
 
@@ -424,16 +499,15 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
+def measure_serve(mce, slots=4, load=0.7):
     """IMCE serving: base Chung-Lu graph (n = 500,000, about 2M edges,
     exponent 2.3) and a stream of 10^6 new edges in batches of log-uniform size
     10^3..10^5.  Pass 1 submits every batch at time 0 (saturation: service
     throughput); pass 2 replays the stream on a fresh state with Poisson
-    arrivals at `--load` times that throughput (latency p50/p99)."""
+    arrivals at `load` times that throughput (latency p50/p99).  Both passes
+    must give the same per-batch results."""
     import torch
     import graphgen
-    import paper_2001_11433_gb300 as mce
-    mce.load(build_if_missing=False)
     w = graphgen.chung_lu_stream()
     su, sv = w.extra["stream_u"], w.extra["stream_v"]
     sizes, gaps = w.extra["batch_sizes"], w.extra["gaps"]
@@ -441,7 +515,7 @@ def run_serve(args):
     g = mce.Graph(w.n, torch.from_numpy(w.u).cuda(), torch.from_numpy(w.v).cuda())
 
     def one_pass(arrivals):
-        srv = mce.Server(slots=args.slots)
+        srv = mce.Server(slots=slots)
         t0 = time.perf_counter()
         t = srv.add_tenant(g)
         open_s = time.perf_counter() - t0
@@ -456,34 +530,53 @@ def run_serve(args):
         assert all(i.status == 0 for i in infos)
         return st, infos, open_s, launches
 
-    sampler = ClockSampler(0)
-    sampler.start()
     sat, sat_infos, open_s, _ = one_pass([0.0] * len(sizes))
     rate = sat["edges"] / (sat["span_ms"] / 1000.0)                 # edges/s at saturation
-    mean_gap_ms = float(np.mean(sizes)) / (args.load * rate) * 1000.0
+    mean_gap_ms = float(np.mean(sizes)) / (load * rate) * 1000.0
     arrivals = np.concatenate([[0.0], np.cumsum(gaps[:-1])]) * mean_gap_ms
     st, infos, _, launches = one_pass(list(arrivals))
+    g.close()
+    assert [(i.delta.new_hash, i.delta.sub_hash) for i in infos] == \
+        [(i.delta.new_hash, i.delta.sub_hash) for i in sat_infos]
+    return {
+        "workload": w.name, "n": w.n, "base_edge_samples": len(w.u), "stream_edges": int(len(su)),
+        "batches": int(len(sizes)), "slots": slots, "offered_load": load, "mean_gap_ms": mean_gap_ms,
+        "imce_open_s": open_s, "edges_per_s": st["edges_per_s"], "span_ms": st["span_ms"],
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+        "wait_p50_ms": st["wait_p50_ms"], "wait_p99_ms": st["wait_p99_ms"],
+        "saturation_edges_per_s": rate, "saturation_p50_ms": sat["p50_ms"], "saturation_p99_ms": sat["p99_ms"],
+        "new_cliques": int(st["new_cliques"]), "subsumed_cliques": int(st["subsumed_cliques"]),
+        "alive_after": int(infos[-1].delta.alive), "applied_edges": int(st["applied"]),
+        "device_ms_total": float(sum(i.delta.ms for i in infos)), "gpu_launches": int(launches),
+        "batch_latency": [{"edges": int(sizes[i]), "new": int(x.delta.new_count), "subsumed": int(x.delta.sub_count),
+                           "device_ms": float(x.delta.ms)} for i, x in enumerate(sat_infos)],
+    }
+
+
+def run_serve(args):
+    import paper_2001_11433_gb300 as mce
+    mce.load(build_if_missing=False)
+    sampler = ClockSampler(0)
+    sampler.start()
+    m = measure_serve(mce, args.slots, args.load)
     clocks = sampler.stop()
-    assert [i.delta.new_hash for i in infos] == [i.delta.new_hash for i in sat_infos]
-    dev_ms = float(sum(i.delta.ms for i in infos))
     line = {
         "metric": "IMCE serving: edges/s and p99 batch latency (arrival to completion)",
-        "value": st["edges_per_s"], "unit": "edges/s", "n_gpus": 1, "steps": len(sizes), "warmup": 0,
-        "ms_per_step": st["span_ms"] / len(sizes), "higher_is_better": True, "scaling": "weak",
+        "value": m["edges_per_s"], "unit": "edges/s", "n_gpus": 1, "steps": m["batches"], "warmup": 0,
+        "ms_per_step": m["span_ms"] / m["batches"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "base_edge_samples": len(w.u), "stream_edges": int(len(su)),
-                   "batches": int(len(sizes)), "slots": args.slots, "offered_load": args.load,
-                   "mean_gap_ms": mean_gap_ms, "imce_open_s": open_s,
-                   "saturation_edges_per_s": rate, "saturation_p50_ms": sat["p50_ms"],
-                   "saturation_p99_ms": sat["p99_ms"]},
-        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "max": st["max_ms"],
-                       "wait_p50": st["wait_p50_ms"], "wait_p99": st["wait_p99_ms"]},
-        "cliques": {"new": int(st["new_cliques"]), "subsumed": int(st["subsumed_cliques"]),
-                    "alive_after": int(infos[-1].delta.alive), "applied_edges": int(st["applied"])},
-        "device_ms_total": dev_ms,
-        "e2e": {"value": st["edges_per_s"], "unit": "edges/s", "h2d_bytes_per_step": int(8 * np.mean(sizes)),
+        "config": {k: m[k] for k in ("workload", "n", "base_edge_samples", "stream_edges", "batches", "slots",
+                                     "offered_load", "mean_gap_ms", "imce_open_s", "saturation_edges_per_s",
+                                     "saturation_p50_ms", "saturation_p99_ms")},
+        "latency_ms": {"p50": m["p50_ms"], "p99": m["p99_ms"], "max": m["max_ms"],
+                       "wait_p50": m["wait_p50_ms"], "wait_p99": m["wait_p99_ms"]},
+        "cliques": {"new": m["new_cliques"], "subsumed": m["subsumed_cliques"], "alive_after": m["alive_after"],
+                    "applied_edges": m["applied_edges"]},
+        "device_ms_total": m["device_ms_total"],
+        "e2e": {"value": m["edges_per_s"], "unit": "edges/s", "h2d_bytes_per_step": int(8 * m["stream_edges"] /
+                                                                                       m["batches"]),
                 "d2h_bytes_per_step": 2 * 8 * (1024 + 8)},
-        "gpu_launches": int(launches), "clocks": clocks,
+        "gpu_launches": m["gpu_launches"], "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 
@@ -542,22 +635,13 @@ def neighbourhood_cost_labels(mce, g, rounds=4, seed=5):
     return np.concatenate(vs), np.concatenate(ls)
 
 
-def run_ranks(args):
-    """Chung-Lu n = 1.7M (exponent 2.2, w_max 35,000, about 11M edges) plus
-    200 planted cliques of size U[20, 60].  Per rank: rank time (RT) and
-    enumeration time (ET), CUDA events inside the library, median of the timed
-    runs; every rank must give the same clique set (count, hash, histogram).
-    The learned rank uses an MLP 8-64-64-1 trained (FP32, on the GPU) on a
-    smaller Chung-Lu graph of the same family (n = 200,000, another seed) to
+def train_learned_model(mce):
+    """MLP 8-64-64-1 trained (FP32, on the GPU, the library's own kernels) on
+    a smaller Chung-Lu graph of the C3 family (n = 200,000, another seed) to
     predict log(1 + search-tree nodes) of a vertex's whole neighbourhood
-    (neighbourhood_cost_labels); inference is BF16."""
+    (neighbourhood_cost_labels).  Returns (model, info)."""
     import torch
     import graphgen
-    import paper_2001_11433_gb300 as mce
-    mce.load(build_if_missing=False)
-    w = graphgen.chung_lu_planted()
-    g = mce.Graph(w.n, torch.from_numpy(w.u).cuda(), torch.from_numpy(w.v).cuda())
-    # training graph of the same family, another seed, n = 200,000
     tu, tv, _ = graphgen.chung_lu(200_000, 2.2, 35_000.0 * (200_000 / 1_700_000) ** 0.5, 200_000 * 6.47,
                                   graphgen.substream_seed(graphgen.BASE_SEED + 103, 0))
     tg = mce.Graph(200_000, torch.from_numpy(tu).cuda(), torch.from_numpy(tv).cuda())
@@ -567,33 +651,70 @@ def run_ranks(args):
     model = mce.Model(64, seed=3)
     loss = model.train(feat, torch.from_numpy(lab).cuda(), epochs=60, batch=2048, lr=3e-3, seed=4)
     train_s = time.perf_counter() - t0
+    tg.close()
+    return model, {"graph": "chung-lu n=200000, other seed", "labels": int(len(lab)),
+                   "label": "log1p(tree nodes of the whole neighbourhood)", "epochs": 60, "final_mse": loss,
+                   "seconds": train_s}
+
+
+def balance_stats(r):
+    """Makespan and per-warp busy-time imbalance of one search launch, from
+    the kernel's own counters (stats: build ns, search ns, idle ns, builds,
+    pieces, largest busy ns of one warp, warps, endgame ns)."""
+    st = r.stats
+    warps = max(st[6], 1)
+    mean_busy = (st[0] + st[1]) / warps
+    return {"search_ms": r.ms_search, "max_warp_busy_ms": st[5] / 1e6, "mean_warp_busy_ms": mean_busy / 1e6,
+            "imbalance": st[5] / mean_busy if mean_busy else None, "idle_frac": st[2] / max(st[0] + st[1] + st[2], 1),
+            "endgame_ms": st[7] / 1e6, "pieces": st[4], "builds": st[3]}
+
+
+def measure_ranks(mce, steps=3, warmup=1, kinds=("degree", "degen", "triangle", "learned")):
+    """Chung-Lu n = 1.7M (exponent 2.2, w_max 35,000, about 11M edges) plus
+    200 planted cliques of size U[20, 60].  Per rank: rank time (RT) and
+    enumeration time (ET), CUDA events inside the library, median of the timed
+    runs, with the search's makespan and imbalance; every rank must give the
+    same clique set (count, hash, histogram)."""
+    import torch
+    import graphgen
+    w = graphgen.chung_lu_planted()
+    g = mce.Graph(w.n, torch.from_numpy(w.u).cuda(), torch.from_numpy(w.v).cuda())
+    model, train = train_learned_model(mce) if "learned" in kinds else (None, None)
     out, ref = {}, None
-    for kind in ("degree", "degen", "triangle", "learned"):
+    for kind in kinds:
         kw = {"rank": kind, "model": model} if kind == "learned" else {"rank": kind}
         runs = []
-        for it in range(args.warmup + args.steps):
+        for it in range(warmup + steps):
             r = mce.enumerate_cliques(g, **kw)
-            if it >= args.warmup:
+            if it >= warmup:
                 runs.append(r)
         key = (runs[0].count, runs[0].hash, tuple(runs[0].hist))
         ref = ref or key
         assert key == ref, f"{kind}: clique set differs"
         rt = float(np.median([x.ms_rank for x in runs]))
         et = float(np.median([x.ms_enum for x in runs]))
+        mid = sorted(runs, key=lambda x: x.ms_enum)[len(runs) // 2]
         out[kind] = {"rt_ms": rt, "et_ms": et, "total_ms": rt + et, "cliques_per_s": runs[0].count / ((rt + et) / 1e3),
-                     "tree_nodes": runs[0].tree_nodes, "splits": runs[0].tasks_split}
+                     "tree_nodes": runs[0].tree_nodes, "splits": mid.tasks_split, **balance_stats(mid)}
+    g.close()
     best = min(out, key=lambda k: out[k]["total_ms"])
+    return {"workload": w.name, "n": w.n, "edge_samples": len(w.u), "cliques": ref[0], "hash": f"{ref[1]:#018x}",
+            "max_clique": len(ref[2]) - 1, "learned_train": train, "fastest_rank": best, "ranks": out,
+            "steps": steps, "warmup": warmup}
+
+
+def run_ranks(args):
+    import paper_2001_11433_gb300 as mce
+    mce.load(build_if_missing=False)
+    m = measure_ranks(mce, args.steps, args.warmup)
+    out = m["ranks"]
     line = {
         "metric": "MCE wall time (RT + ET) and cliques/s per rank, learned vs degeneracy (bit-exact across ranks)",
         "value": out["degen"]["cliques_per_s"], "unit": "cliques/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": out["degen"]["total_ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32 (features FP32, inference BF16)", "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "edge_samples": len(w.u), "cliques": ref[0], "hash": f"{ref[1]:#018x}",
-                   "max_clique": len(ref[2]) - 1, "learned_train": {"graph": "chung-lu n=200000, other seed",
-                                                                    "labels": int(len(lab)), "label": "log1p(tree nodes "
-                                                                    "of the whole neighbourhood)", "epochs": 60,
-                                                                    "final_mse": loss, "seconds": train_s},
-                   "fastest_rank": best},
+        "config": {k: m[k] for k in ("workload", "n", "edge_samples", "cliques", "hash", "max_clique", "learned_train",
+                                     "fastest_rank")},
         "ranks": out,
     }
     print(json.dumps(line), flush=True)
@@ -606,7 +727,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="rmat18: skip the Chung-Lu rank comparison and the serving loop after the timed region")
     ap.add_argument("--sample", type=float, default=1.0, help="rmat18: timed fraction of the subproblem set")
     ap.add_argument("--workload", choices=["rmat18", "batched", "serve", "ranks"], default="rmat18")
     ap.add_argument("--graph-budget", type=int, default=1 << 20, help="batched: tree nodes per graph")

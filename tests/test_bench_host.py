@@ -35,3 +35,19 @@ def test_user_rank_puts_the_set_lowest():
     assert sorted(rank[S].tolist()) == list(range(len(S)))
     for x in S:
         assert (rank[col[row[x]:row[x + 1]]] > rank[x]).all()
+
+
+def test_cpu_sample_is_a_plain_prefix():
+    """The CPU baseline's sample: a seeded permutation of the benchmark set cut
+    before the first subproblem that would pass the node budget, so a heavy
+    subproblem ends the sample instead of being skipped."""
+    rng = np.random.default_rng(0)
+    subset = np.arange(5000, dtype=np.int32) * 2
+    nodes = np.zeros(10000, np.uint64)
+    nodes[subset] = rng.integers(1, 1000, len(subset)).astype(np.uint64)
+    s1 = bench.sample_prefix(subset, nodes, 50_000, seed=7)
+    assert np.array_equal(s1, bench.sample_prefix(subset, nodes, 50_000, seed=7))
+    perm = np.random.default_rng(7).permutation(subset)
+    k = len(s1)
+    assert np.array_equal(np.sort(perm[:k]), s1)
+    assert nodes[s1].sum() <= 50_000 < nodes[perm[:k + 1]].sum()
