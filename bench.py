@@ -297,8 +297,8 @@ def run_ours(args):
 
     def step_device():
         g = mce.Graph(w.n, dev_u, dev_v)
-        r = mce.enumerate_cliques(g, rank="degen", subset=dev_subset, blocks_per_sm=BLOCKS_PER_SM,
-                                  split_nodes=SPLIT_NODES)
+        r = mce.enumerate_cliques(g, rank="degen", subset=dev_subset, blocks_per_sm=args.blocks_per_sm,
+                                  split_nodes=SPLIT_NODES, warp_small_search=args.warp_small_search)
         g.close()
         return r
 
@@ -335,8 +335,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g = mce.Graph(w.n, pin_u.numpy(), pin_v.numpy())
-        r2 = mce.enumerate_cliques(g, rank="degen", subset=pin_subset.numpy(), blocks_per_sm=BLOCKS_PER_SM,
-                                   split_nodes=SPLIT_NODES)
+        r2 = mce.enumerate_cliques(g, rank="degen", subset=pin_subset.numpy(), blocks_per_sm=args.blocks_per_sm,
+                                   split_nodes=SPLIT_NODES, warp_small_search=args.warp_small_search)
         g.close()
         e2e_times.append((time.perf_counter() - t0) * 1000.0)
     clocks = sampler.stop()
@@ -368,7 +368,8 @@ def run_ours(args):
         # the GPU on the very same subproblems (enumeration time: Γ+ lists, prepass, search)
         gs = mce.Graph(w.n, dev_u, dev_v)
         gpu_runs = [mce.enumerate_cliques(gs, rank="degen", subset=torch.from_numpy(sample).cuda(),
-                                          blocks_per_sm=BLOCKS_PER_SM, split_nodes=SPLIT_NODES) for _ in range(3)]
+                                          blocks_per_sm=args.blocks_per_sm, split_nodes=SPLIT_NODES,
+                                          warp_small_search=args.warp_small_search) for _ in range(3)]
         gs.close()
         assert all(x.count == base["all_threads"]["cliques"] for x in gpu_runs)
         assert all(f"{x.hash:#018x}" == base["single_thread"]["hash"] for x in gpu_runs)
@@ -397,7 +398,8 @@ def run_ours(args):
                    "max_clique": len(res.hist) - 1, "tree_nodes": res.tree_nodes,
                    "tree_nodes_per_s": world * res.tree_nodes / (ms / 1000.0),
                    "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{world}",
-                   "launch": {"blocks_per_sm": BLOCKS_PER_SM, "warps_per_block": 8, "split_nodes": SPLIT_NODES}},
+                   "launch": {"blocks_per_sm": args.blocks_per_sm, "warps_per_block": 8, "split_nodes": SPLIT_NODES,
+                              "small_search": "warp" if args.warp_small_search else "lane-parallel"}},
         "phases_ms": {"rank": res.ms_rank, "enumerate": res.ms_enum, "search_kernel": float(np.mean(search_ms))},
         "roofline": {"bound": "alu", "kernel": "k_bk (persistent search)", "achieved": achieved, "peak": peak_ops,
                      "unit": "word-ops/s", "frac": achieved / peak_ops if peak_ops else None,
@@ -731,6 +733,9 @@ def main():
                     help="rmat18: skip the Chung-Lu rank comparison and the serving loop after the timed region")
     ap.add_argument("--sample", type=float, default=1.0, help="rmat18: timed fraction of the subproblem set")
     ap.add_argument("--workload", choices=["rmat18", "batched", "serve", "ranks"], default="rmat18")
+    ap.add_argument("--blocks-per-sm", type=int, default=BLOCKS_PER_SM, help="rmat18: resident search blocks per SM")
+    ap.add_argument("--warp-small-search", action="store_true",
+                    help="rmat18: search small subtrees with the whole warp (the lane-parallel search is the default)")
     ap.add_argument("--graph-budget", type=int, default=1 << 20, help="batched: tree nodes per graph")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent batches")
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load / saturation throughput")

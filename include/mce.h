@@ -122,6 +122,11 @@ typedef struct {
      * hand-over and the donor keeps the work, so any capacity gives the same
      * result; values below 2 count as 2. */
     int32_t queue_capacity;
+    /* 1 = search every small subtree (at most 32 candidates and 32 fini
+     * vertices) with the whole warp, one node at a time; 0 (default) = one
+     * small subtree per lane, 32 at a time (static MCE without clique lists).
+     * Both give the same trees, node counts and cliques. */
+    int32_t warp_small_search;
 } mce_opts;
 
 typedef struct {
@@ -308,6 +313,17 @@ mce_status imce_open(const mce_graph *g, const mce_opts *opts, imce_state **s);
  * mce_opts list) receive Λnew and Λdel when not NULL. */
 mce_status imce_add_edges(imce_state *s, const int32_t *u, const int32_t *v, int64_t k,
                           int32_t on_device, imce_delta *out);
+/* Delete k raw pairs (device if on_device, else host) from the graph and
+ * update C(G).  The batch is canonicalised as for additions (arrival order;
+ * self loops, pairs that are not edges of G and repeats dropped and counted in
+ * out->dropped; out->applied = deleted edges).  Deletions reduce to additions
+ * (Section 5: G = (G - H) + H): out->sub_* describe the removed cliques
+ * C(G) \ C(G - H), which are the new cliques of adding H to G - H and are
+ * found on G by Algorithms 6 and 7; out->new_* describe the created cliques
+ * C(G - H) \ C(G), Algorithm 8's splits of the removed cliques that are
+ * maximal in G - H.  All or nothing: on an error the state is unchanged. */
+mce_status imce_remove_edges(imce_state *s, const int32_t *u, const int32_t *v, int64_t k,
+                             int32_t on_device, imce_delta *out);
 /* Current graph (owned by the state). */
 const mce_graph *imce_graph(const imce_state *s);
 /* Alive cliques of the index into a caller list (layout as mce_opts). */

@@ -59,6 +59,7 @@ class Opts(ctypes.Structure):
         ("subset_on_host", ctypes.c_int32),
         ("subproblem_budget", ctypes.c_uint64),
         ("queue_capacity", ctypes.c_int32),
+        ("warp_small_search", ctypes.c_int32),
     ]
 
 
@@ -193,6 +194,7 @@ SIGNATURES = {
     "imce_server_tenant": ([_vp, _i32], _vp),
     "imce_server_free": ([_vp], None),
     "imce_add_edges": ([_vp, _vp, _vp, _i64, _i32, _P(DeltaC)], _i32),
+    "imce_remove_edges": ([_vp, _vp, _vp, _i64, _i32, _P(DeltaC)], _i32),
     "imce_graph": ([_vp], _vp),
     "imce_cliques": ([_vp, _vp, _vp, _i64, _i64, _P(_i64), _P(_i64)], _i32),
     "imce_close": ([_vp], None),
@@ -360,7 +362,7 @@ class Graph:
 def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, stream=None, list_buf=None,
               per_vertex=None, split=True, order_by_model=False, warps_per_block=0, blocks_per_sm=0,
               time_limit_ms=0, subset=None, subproblem_budget=0, shared_words=0, split_nodes=0,
-              queue_capacity=0) -> Opts:
+              queue_capacity=0, warp_small_search=False) -> Opts:
     o = Opts()
     load().mce_opts_init(ctypes.byref(o))
     o.rank_kind = RANKS[rank] if isinstance(rank, str) else int(rank)
@@ -387,6 +389,7 @@ def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, s
         o.subset_on_host = int(isinstance(subset, np.ndarray) or not subset.is_cuda)
     o.subproblem_budget = subproblem_budget
     o.queue_capacity = queue_capacity
+    o.warp_small_search = int(warp_small_search)
     return o
 
 
@@ -627,6 +630,18 @@ class Imce:
         d = DeltaC()
         _check(load().imce_add_edges(self._h, _ptr(u), _ptr(v), len(u), int(on_dev), ctypes.byref(d)),
                "imce_add_edges")
+        return _delta(d)
+
+    def remove_edges(self, u, v) -> Delta:
+        """imce_remove_edges: delta.new_* = created cliques, delta.sub_* = removed ones."""
+        import torch
+        on_dev = isinstance(u, torch.Tensor) and u.is_cuda
+        if not isinstance(u, torch.Tensor):
+            u = np.ascontiguousarray(u, dtype=np.int32)
+            v = np.ascontiguousarray(v, dtype=np.int32)
+        d = DeltaC()
+        _check(load().imce_remove_edges(self._h, _ptr(u), _ptr(v), len(u), int(on_dev), ctypes.byref(d)),
+               "imce_remove_edges")
         return _delta(d)
 
     def graph(self) -> Graph:

@@ -137,6 +137,8 @@ mce_status plan_shape(mce_batched *b, cudaStream_t s) {
     BkParams &P = b->P;
     P.gws_words = b->per_warp > b->ls.smem_words ? b->per_warp : 16;
     P.smem_words = b->ls.smem_words;
+    P.lp_words = b->ls.lp_words;
+    MCE_TRY(alloc_lp_tasks(P, nwarps, s, b->bb));
     MCE_TRY(b->bb.gws.alloc((size_t)nwarps * P.gws_words * 4, s));
     P.gws = b->bb.gws.as<uint32_t>();
     const int64_t wcmax = (b->cmax + 31) / 32;
@@ -315,7 +317,8 @@ mce_status mce_batched_run(mce_batched *b, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     if (!b->exec) {
         // capture the run once; later runs replay it
-        MCE_TRY(bk_prepare(b->ls.warps_per_block, b->ls.blocks_per_sm, b->ls.smem_words));
+        MCE_TRY(bk_prepare(b->ls.blocks_per_sm,
+                           bk_block_smem_bytes(b->ls.warps_per_block, b->ls.smem_words, b->ls.lp_words)));
         const uint64_t before = g_launches.load(std::memory_order_relaxed);
         // captured on the plan's own stream (the legacy default stream
         // cannot be captured); the graph is launched on the caller's stream

@@ -57,6 +57,10 @@ struct Ws {
     int32_t frw;                  // words per frame
     int32_t dcap;                 // frames available
     uint32_t *piv;                // this warp's pivot scratch in shared memory
+    // lane-parallel small search: this warp's region in shared memory (root
+    // table, then the arena of relabelled universes), roots and arena words in use
+    uint32_t *lp;
+    int32_t lp_n, lp_top;
 };
 
 __device__ __forceinline__ uint32_t *fr_cand(const Ws &s, int d) { return s.fr + (int64_t)d * s.frw; }
@@ -486,6 +490,7 @@ struct Acc {
     unsigned long long t_count, t_hash, t_nodes;   // per task
     int tick;                                      // nodes between checks (shorter in the endgame)
     int give;                                      // hand-overs per check at most
+    int lp_hold;                                   // warps wait for work: small subtrees stay with the whole warp
 };
 
 // Algorithmic word operations of one tree node with |cand| = cn and |fini| =
@@ -624,6 +629,7 @@ struct Task {
 __device__ int poll(const BkParams &P, Acc &acc, int lane, int32_t root, uint64_t t_start,
                     unsigned long long &hungry_out) {
     unsigned long long ab = 0, hungry = 0;
+    int lph = 0;
     if (lane == 0) {
         if (globaltimer_ns() - t_start > P.max_run_ns) atomicOr(&P.ctl[CTL_ABORT], 2ULL);
         ab = *(volatile unsigned long long *)&P.ctl[CTL_ABORT];
@@ -653,6 +659,9 @@ __device__ int poll(const BkParams &P, Acc &acc, int lane, int32_t root, uint64_
             const unsigned long long qh = *(volatile unsigned long long *)&P.ctl[CTL_QHEAD];
             const unsigned long long qt = *(volatile unsigned long long *)&P.ctl[CTL_QTAIL];
             const unsigned long long qlen = qt > qh ? qt - qh : 0ULL;
+            // while warps wait for work, small subtrees are searched by the whole
+            // warp, whose frames can be handed over
+            lph = hungry > qlen;
             if (qlen >= hungry) hungry = 0;
             // a task hands over again only after 2048 more nodes of its own:
             // pieces cut too small cost their receivers more than they hold
@@ -675,6 +684,7 @@ __device__ int poll(const BkParams &P, Acc &acc, int lane, int32_t root, uint64_
     }
     ab = __shfl_sync(FULL, ab, 0);
     hungry = __shfl_sync(FULL, hungry, 0);
+    acc.lp_hold = __shfl_sync(FULL, lph, 0);
     hungry_out = hungry;
     if (ab & 3ULL) return 1;
     if (ab & 16ULL) return 2;
@@ -891,20 +901,17 @@ __device__ bool small_donate(const BkParams &P, const Ws &s, const Task &T, cons
     return true;
 }
 
-// The subtree of the node at memory depth d (its cand/finic in rc/rf, conf
-// in rx, F list Fd[0..flen)), already counted, with cand not empty.
-// Frames 0..d-1 are in memory.  Returns as search<NR>.
+// Relabel the node (cand rc, finic rf, F list Fd[0..flen)) as a small
+// universe: u gets lane l's rows and tie keys, gC / cidC the global and local
+// id of C_l, cidX the local id of X_l.  The C and X lists pass through the
+// pivot scratch, which is free again on return.
 template <int NR>
-__device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigned long long *shist, int lane,
-                            int &node_tick, uint64_t t_start, int32_t root, int k0, int d, uint64_t hsum,
-                            const uint32_t (&rc)[NR], const uint32_t (&rf)[NR], const uint32_t (&rx)[NR],
-                            const int32_t *Fd, int flen) {
+__device__ __forceinline__ void small_relabel(const BkParams &P, const Ws &s, int lane, const uint32_t (&rc)[NR],
+                                              const uint32_t (&rf)[NR], const int32_t *Fd, int flen, SmallU &u,
+                                              int32_t &gC, int32_t &cidC, int32_t &cidX) {
     const bool imce = P.mode == BK_IMCE;
-    const int wc = s.wc;
-    // ---- relabel: C and X lists in the pivot scratch
     int32_t *Cl = reinterpret_cast<int32_t *>(s.piv + 64);
     int32_t *Xl = Cl + 32;
-    SmallU u;
     {
         int base_c = 0, base_f = 0;
 #pragma unroll
@@ -940,8 +947,8 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
         if (lane < flen) Xl[base_f + lane] = Fd[lane];
     }
     __syncwarp();
-    const int32_t cidC = lane < u.cn ? Cl[lane] : 0;
-    const int32_t cidX = lane < u.xn ? Xl[lane] : 0;
+    cidC = lane < u.cn ? Cl[lane] : 0;
+    cidX = lane < u.xn ? Xl[lane] : 0;
     u.adjC = u.adjX = u.exclC = 0u;
     {
         const uint32_t *rowC = s.A + (int64_t)cidC * s.S;
@@ -957,7 +964,7 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
         }
     }
     {
-        const int32_t gC = lane < u.cn ? s.gid[cidC] : 0x7fffffff;
+        gC = lane < u.cn ? s.gid[cidC] : 0x7fffffff;
         const int32_t gX = lane < u.xn ? s.gid[cidX] : 0x7fffffff;
         // C is in increasing global id, so C_l has l smaller ids in C
         int oc = lane, ox = 0;
@@ -969,15 +976,31 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
         for (int k = 0; k < u.cn; ++k) ox += __shfl_sync(FULL, gC, k) < gX;
         u.tC = 127u - (uint32_t)oc;
         u.tX = 127u - (uint32_t)ox;
-        // the tables live where the wide pivot keeps its cand and after the stack
-        // (Cl / Xl, read above, sit inside the stack area)
-        if (lane < u.cn) {
-            small_h(s)[lane] = vertex_hash(gC, P.seed);
-            small_gid(s)[lane] = gC;
-            small_cidc(s)[lane] = cidC;
-        }
-        if (lane < u.xn) small_cidx(s)[lane] = cidX;
     }
+    __syncwarp();   // Cl / Xl are scratch again after this point
+}
+
+// The subtree of the node at memory depth d (its cand/finic in rc/rf, conf
+// in rx, F list Fd[0..flen)), already counted, with cand not empty.
+// Frames 0..d-1 are in memory.  Returns as search<NR>.
+template <int NR>
+__device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigned long long *shist, int lane,
+                            int &node_tick, uint64_t t_start, int32_t root, int k0, int d, uint64_t hsum,
+                            const uint32_t (&rc)[NR], const uint32_t (&rf)[NR], const uint32_t (&rx)[NR],
+                            const int32_t *Fd, int flen) {
+    const bool imce = P.mode == BK_IMCE;
+    const int wc = s.wc;
+    SmallU u;
+    int32_t gC, cidC, cidX;
+    small_relabel<NR>(P, s, lane, rc, rf, Fd, flen, u, gC, cidC, cidX);
+    // the tables live where the wide pivot keeps its cand and after the stack
+    // (the relabel lists, read by now, sit inside the stack area)
+    if (lane < u.cn) {
+        small_h(s)[lane] = vertex_hash(gC, P.seed);
+        small_gid(s)[lane] = gC;
+        small_cidc(s)[lane] = cidC;
+    }
+    if (lane < u.xn) small_cidx(s)[lane] = cidX;
     uint32_t conf = 0u;
     if (imce) {
         const int wd = cidC >> 5;
@@ -988,7 +1011,7 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
         }
         conf = __ballot_sync(FULL, lane < u.cn && ((wv >> (cidC & 31)) & 1u));
     }
-    __syncwarp();   // Cl / Xl are scratch again after this point
+    __syncwarp();   // the tables are read by every lane below
     // ---- the search
     uint32_t cand = u.cn == 32 ? FULL : ((1u << u.cn) - 1u);
     uint32_t finc = 0u, ext = 0u;
@@ -1208,6 +1231,346 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
     }
 }
 
+// ------------------------------------------------------------------ lane-parallel small search
+//
+// In static MCE without clique lists the small nodes are not searched by the
+// whole warp one node at a time.  The warp relabels each small node it
+// reaches (small_relabel) into a universe in its shared-memory arena and goes
+// on with the wide search; when the arena or the root table is full, or the
+// task ends, every lane runs whole small subtrees on its own (lp_run): the
+// TTT step of search_small on 32-bit masks, one lane per subtree, a lane
+// taking the next universe when it is done.  Trees, node counts, word
+// operations and cliques are those of search_small.
+//
+// Universe of a small node with cn candidates and xn fini vertices (arena
+// words): h(C_k) as uint64 [2 cn], then rows adjC [cn], the columns of adjX
+// (adjXT[k] = {x : X_x ~ C_k}) [cn], rows adjX [xn], then the tie keys as
+// bytes (C members, then X members).  Root record (4 words): arena offset,
+// cn | xn << 8 | (clique size at the node) << 16, hash sum at the node.
+
+__device__ __forceinline__ int lp_universe_words(int cn, int xn) {
+    return (4 * cn + xn + ((cn + xn + 3) >> 2) + 1) & ~1;
+}
+
+struct LpSums {
+    unsigned long long hash, wops;
+    uint32_t count, nodes, smax;
+};
+
+// A small-subtree node for one lane: its universe and its state.
+struct LpNode {
+    const uint64_t *hC;
+    const uint32_t *adjC, *adjXT, *adjX;
+    const uint8_t *key;
+    int cn;
+    uint32_t base;     // clique size at the universe's root
+    uint32_t cand, finc, xs;
+    uint64_t hs;
+    int depth;         // below the universe's root
+};
+
+__device__ __forceinline__ void lp_emit(const BkParams &P, unsigned long long *shist, LpSums &o, uint32_t size,
+                                        uint64_t hsum) {
+    o.count++;
+    o.hash += clique_hash_from_sum(hsum, size);
+    o.wops += size;
+    if (size < 256) atomicAdd(&shist[size], 1ULL);
+    else if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
+    else atomicOr(&P.out[OUT_FLAGS], 2ULL);
+    if (size > o.smax) o.smax = size;
+}
+
+// Pivot of an entered node (cand not empty): ext = cand minus the pivot's
+// neighbours, with the pivot the largest (count + 1, tie key) over cand ∪
+// finc and xs (the order of search_small).
+__device__ __forceinline__ uint32_t lp_pivot_ext(const LpNode &u, LpSums &o) {
+    const uint32_t cf = u.cand | u.finc;
+    uint32_t best = 0u, badj = 0u;
+    for (uint32_t m = cf; m; m &= m - 1u) {
+        const int k = __ffs(m) - 1;
+        const uint32_t a = u.adjC[k];
+        const uint32_t kk = ((uint32_t)(__popc(u.cand & a) + 1) << 7) | u.key[k];
+        if (kk > best) {
+            best = kk;
+            badj = a;
+        }
+    }
+    for (uint32_t m = u.xs; m; m &= m - 1u) {
+        const int x = __ffs(m) - 1;
+        const uint32_t a = u.adjX[x];
+        const uint32_t kk = ((uint32_t)(__popc(u.cand & a) + 1) << 7) | u.key[u.cn + x];
+        if (kk > best) {
+            best = kk;
+            badj = a;
+        }
+    }
+    const uint32_t ext = u.cand & ~badj;
+    const uint32_t t = (uint32_t)(__popc(cf) + __popc(u.xs));
+    o.wops += t + 2u * (uint32_t)__popc(ext) * ((t + 31u) >> 5);
+    return ext;
+}
+
+// Child q of a node whose cand / finc already exclude / include q: leaves
+// and one-candidate children are settled here (returns false); otherwise the
+// child's sets are returned for a push (returns true).  Node counts and word
+// operations follow search_small.
+__device__ __forceinline__ bool lp_child(const BkParams &P, unsigned long long *shist, const LpNode &u, int q,
+                                         LpSums &o, uint32_t &cc, uint32_t &cf, uint32_t &cx, uint64_t &hq) {
+    const uint32_t aq = u.adjC[q];
+    cc = u.cand & aq;
+    cf = u.finc & aq;
+    cx = u.xs & u.adjXT[q];
+    hq = u.hC[q];
+    if (cc == 0u) {
+        // a leaf: a maximal clique unless fini is left
+        ++o.nodes;
+        if ((cf | cx) == 0u) lp_emit(P, shist, o, u.base + (uint32_t)u.depth + 1u, u.hs + hq);
+        return false;
+    }
+    if ((cc & (cc - 1u)) == 0u) {
+        // one candidate c: one more node and the clique K + q + c, unless a fini
+        // vertex adjacent to c is the pivot (then no child)
+        const int c = __ffs(cc) - 1;
+        const uint32_t t = 1u + (uint32_t)(__popc(cf) + __popc(cx));
+        if ((cf & u.adjC[c]) != 0u || (cx & u.adjXT[c]) != 0u) {
+            ++o.nodes;
+            o.wops += t;
+        } else {
+            o.nodes += 2;
+            o.wops += t + 2u * ((t + 31u) >> 5);
+            lp_emit(P, shist, o, u.base + (uint32_t)u.depth + 2u, u.hs + hq + u.hC[c]);
+        }
+        return false;
+    }
+    ++o.nodes;
+    return true;
+}
+
+// The whole subtree below an entered-but-not-yet-pivoted node, depth first.
+__device__ void lp_dfs(const BkParams &P, unsigned long long *shist, LpNode u, LpSums &o) {
+    uint32_t stk[32 * 5];   // frames: cand, finc, xs, ext, q (a frame adds a distinct candidate: depth < 31)
+    const int d0 = u.depth;
+    uint32_t ext = 0u;
+    bool enter = true;
+    for (;;) {
+        if (enter) {
+            if (u.cand == 0u) {
+                if ((u.finc | u.xs) == 0u) lp_emit(P, shist, o, u.base + (uint32_t)u.depth, u.hs);
+                goto lpop;
+            }
+            ext = lp_pivot_ext(u, o);
+            enter = false;
+        }
+        if (ext == 0u) goto lpop;
+        {
+            const int q = __ffs(ext) - 1;
+            const uint32_t qb = 1u << q;
+            ext &= ~qb;
+            u.cand &= ~qb;
+            u.finc |= qb;
+            uint32_t cc, cf, cx;
+            uint64_t hq;
+            if (!lp_child(P, shist, u, q, o, cc, cf, cx, hq)) continue;
+            uint32_t *f = stk + 5 * (u.depth - d0);
+            f[0] = u.cand;
+            f[1] = u.finc;
+            f[2] = u.xs;
+            f[3] = ext;
+            f[4] = (uint32_t)q;
+            ++u.depth;
+            u.cand = cc;
+            u.finc = cf;
+            u.xs = cx;
+            u.hs += hq;
+            enter = true;
+            continue;
+        }
+    lpop:
+        if (u.depth == d0) break;
+        --u.depth;
+        {
+            const uint32_t *f = stk + 5 * (u.depth - d0);
+            u.cand = f[0];
+            u.finc = f[1];
+            u.xs = f[2];
+            ext = f[3];
+            u.hs -= u.hC[f[4]];
+        }
+    }
+}
+
+__device__ __forceinline__ LpNode lp_root_node(const uint32_t *lp, int r) {
+    const uint32_t *rec = lp + 4 * r;
+    const uint32_t meta = rec[1];
+    LpNode u;
+    u.cn = (int)(meta & 0xffu);
+    const int xn = (int)((meta >> 8) & 0xffu);
+    u.base = meta >> 16;
+    const uint32_t *uni = lp + BK_LP_TABLE_WORDS + rec[0];
+    u.hC = reinterpret_cast<const uint64_t *>(uni);
+    u.adjC = uni + 2 * u.cn;
+    u.adjXT = uni + 3 * u.cn;
+    u.adjX = uni + 4 * u.cn;
+    u.key = reinterpret_cast<const uint8_t *>(uni + 4 * u.cn + xn);
+    u.cand = u.cn == 32 ? FULL : ((1u << u.cn) - 1u);
+    u.xs = xn == 32 ? FULL : ((1u << xn) - 1u);
+    u.finc = 0u;
+    u.hs = (uint64_t)rec[2] | ((uint64_t)rec[3] << 32);
+    u.depth = 0;
+    return u;
+}
+
+__device__ __forceinline__ void lp_task_put(uint32_t *t, int r, const LpNode &u) {
+    t[0] = (uint32_t)r | ((uint32_t)u.depth << 8);
+    t[1] = u.cand;
+    t[2] = u.finc;
+    t[3] = u.xs;
+    t[4] = (uint32_t)u.hs;
+    t[5] = (uint32_t)(u.hs >> 32);
+}
+
+__device__ __forceinline__ LpNode lp_task_get(const uint32_t *lp, const uint32_t *t) {
+    LpNode u = lp_root_node(lp, (int)(t[0] & 0xffu));
+    u.depth = (int)(t[0] >> 8);
+    u.cand = t[1];
+    u.finc = t[2];
+    u.xs = t[3];
+    u.hs = (uint64_t)t[4] | ((uint64_t)t[5] << 32);
+    return u;
+}
+
+// Enter node u and put its non-trivial children into the list `dst` (leaves
+// and one-candidate children are settled at once); a child that finds the
+// list full is searched here instead.
+__device__ void lp_expand(const BkParams &P, unsigned long long *shist, LpNode u, int r, LpSums &o, uint32_t *dst,
+                          uint32_t *dst_n) {
+    if (u.cand == 0u) {
+        if ((u.finc | u.xs) == 0u) lp_emit(P, shist, o, u.base + (uint32_t)u.depth, u.hs);
+        return;
+    }
+    uint32_t ext = lp_pivot_ext(u, o);
+    while (ext) {
+        const int q = __ffs(ext) - 1;
+        const uint32_t qb = 1u << q;
+        ext &= ~qb;
+        u.cand &= ~qb;
+        u.finc |= qb;
+        uint32_t cc, cf, cx;
+        uint64_t hq;
+        if (!lp_child(P, shist, u, q, o, cc, cf, cx, hq)) continue;
+        LpNode c = u;
+        c.cand = cc;
+        c.finc = cf;
+        c.xs = cx;
+        c.hs = u.hs + hq;
+        c.depth = u.depth + 1;
+        const uint32_t slot = atomicAdd(dst_n, 1u);
+        if (slot < (uint32_t)P.lp_task_cap) lp_task_put(dst + (int64_t)slot * BK_LP_TASK_WORDS, r, c);
+        else lp_dfs(P, shist, c, o);
+    }
+}
+
+// The buffered small subtrees, one lane per task.  The roots are expanded
+// breadth first (one level, and a second while the tasks number fewer than
+// four per lane) so that the heavy-tailed subtree sizes spread over the lanes;
+// the last list is then taken task by task, each searched depth first.
+__device__ __noinline__ LpSums lp_run(const BkParams &P, uint32_t *lp, int nroots, unsigned long long *shist,
+                                      uint32_t *tasks, int lane) {
+    LpSums o = {0ULL, 0ULL, 0u, 0u, 0u};
+    uint32_t *ctr = lp + BK_LP_MAX_ROOTS * 4;   // [0] list A size, [1] list B size, [2] next task
+    uint32_t *la = tasks, *lb = tasks + (int64_t)P.lp_task_cap * BK_LP_TASK_WORDS;
+    if (lane == 0) ctr[0] = ctr[1] = ctr[2] = 0u;
+    __syncwarp();
+    for (int r = lane; r < nroots; r += 32) lp_expand(P, shist, lp_root_node(lp, r), r, o, la, &ctr[0]);
+    __syncwarp();
+    uint32_t n = min(ctr[0], (uint32_t)P.lp_task_cap);
+    uint32_t *list = la;
+    if (n > 0u && n < 128u) {
+        for (uint32_t i = (uint32_t)lane; i < n; i += 32u) {
+            const uint32_t *t = la + (int64_t)i * BK_LP_TASK_WORDS;
+            lp_expand(P, shist, lp_task_get(lp, t), (int)(t[0] & 0xffu), o, lb, &ctr[1]);
+        }
+        __syncwarp();
+        n = min(ctr[1], (uint32_t)P.lp_task_cap);
+        list = lb;
+    }
+    for (uint32_t i = atomicAdd(&ctr[2], 1u); i < n; i = atomicAdd(&ctr[2], 1u)) {
+        const uint32_t *t = list + (int64_t)i * BK_LP_TASK_WORDS;
+        lp_dfs(P, shist, lp_task_get(lp, t), o);
+    }
+    __syncwarp();
+    return o;
+}
+
+// Run the buffered small subtrees and fold their sums into the task.
+__device__ void lp_flush(const BkParams &P, Ws &s, Acc &acc, unsigned long long *shist, int lane, int &node_tick) {
+    if (s.lp_n == 0) return;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const LpSums r = lp_run(P, s.lp, s.lp_n, shist, P.lp_tasks + gwarp * 2 * (int64_t)P.lp_task_cap * BK_LP_TASK_WORDS,
+                            lane);
+    unsigned long long cnt = r.count, nodes = r.nodes, hsh = r.hash, wops = r.wops;
+    uint32_t smax = r.smax;
+    for (int o = 16; o; o >>= 1) {
+        cnt += __shfl_xor_sync(FULL, cnt, o);
+        nodes += __shfl_xor_sync(FULL, nodes, o);
+        hsh += __shfl_xor_sync(FULL, hsh, o);
+        wops += __shfl_xor_sync(FULL, wops, o);
+        smax = max(smax, __shfl_xor_sync(FULL, smax, o));
+    }
+    acc.t_count += cnt;
+    acc.t_hash += hsh;
+    acc.t_nodes += nodes;
+    if (lane == 0) {
+        acc.wops += wops;
+        if (smax > cold().maxsize) cold().maxsize = smax;
+    }
+    node_tick += nodes > 4096ULL ? 4096 : (int)nodes;
+    s.lp_n = 0;
+    s.lp_top = 0;
+}
+
+// Relabel the small node (as search_small does) into the arena; the search
+// of its subtree is left to the next lp_flush.
+template <int NR>
+__device__ void lp_enqueue(const BkParams &P, Ws &s, Acc &acc, unsigned long long *shist, int lane, int &node_tick,
+                           int k0, int d, uint64_t hsum, const uint32_t (&rc)[NR], const uint32_t (&rf)[NR],
+                           const int32_t *Fd, int flen) {
+    SmallU u;
+    int32_t gC, cidC, cidX;
+    small_relabel<NR>(P, s, lane, rc, rf, Fd, flen, u, gC, cidC, cidX);
+    const int need = lp_universe_words(u.cn, u.xn);
+    if (s.lp_n == BK_LP_MAX_ROOTS || s.lp_top + need > P.lp_words - BK_LP_TABLE_WORDS)
+        lp_flush(P, s, acc, shist, lane, node_tick);
+    // column k of adjX to lane k
+    uint32_t adjXT = 0u;
+    for (int k = 0; k < u.cn; ++k) {
+        const uint32_t b = __ballot_sync(FULL, (u.adjX >> k) & 1u);
+        if (lane == k) adjXT = b;
+    }
+    uint32_t *uni = s.lp + BK_LP_TABLE_WORDS + s.lp_top;
+    uint8_t *key = reinterpret_cast<uint8_t *>(uni + 4 * u.cn + u.xn);
+    if (lane < u.cn) {
+        reinterpret_cast<uint64_t *>(uni)[lane] = vertex_hash(gC, P.seed);
+        uni[2 * u.cn + lane] = u.adjC;
+        uni[3 * u.cn + lane] = adjXT;
+        key[lane] = (uint8_t)u.tC;
+    }
+    if (lane < u.xn) {
+        uni[4 * u.cn + lane] = u.adjX;
+        key[u.cn + lane] = (uint8_t)u.tX;
+    }
+    if (lane == 0) {
+        uint32_t *rec = s.lp + 4 * s.lp_n;
+        rec[0] = (uint32_t)s.lp_top;
+        rec[1] = (uint32_t)u.cn | ((uint32_t)u.xn << 8) | ((uint32_t)(k0 + d) << 16);
+        rec[2] = (uint32_t)hsum;
+        rec[3] = (uint32_t)(hsum >> 32);
+    }
+    s.lp_n++;
+    s.lp_top += need;
+    __syncwarp();
+}
+
 template <int NR>
 __device__ __forceinline__ uint32_t bcast(const uint32_t (&r)[NR], int k) {
     return __shfl_sync(FULL, (NR == 1 || k < 32) ? r[0] : r[NR - 1], k & 31);
@@ -1296,6 +1659,10 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
                 node_fn = fcn + (int)flen;
                 if (cn <= 32 && fcn + (int)flen <= 32) {
                     const int32_t *Fd = (T.kdepth == 0 && d == 0) ? s.F0 : s.F;
+                    if (P.lp_words && P.mode == BK_MCE && !P.list_off && !acc.lp_hold) {
+                        lp_enqueue<NR>(P, s, acc, shist, lane, node_tick, k0, d, hsum, rc, rf, Fd, (int)flen);
+                        goto pop;
+                    }
                     const int code = search_small<NR>(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, d,
                                                       hsum, rc, rf, rx, Fd, (int)flen);
                     if (code) return code;
@@ -1497,7 +1864,10 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
             continue;
         }
     pop:
-        if (d == 0) return 0;
+        if (d == 0) {
+            lp_flush(P, s, acc, shist, lane, node_tick);
+            return 0;
+        }
         if (P.mode == BK_MCE && !(T.kdepth == 0 && d == 1)) {
             // put frame d-1's F back in bnd order (the child split it into adjacent | rest);
             // the root frame reads F0, which no child touches
@@ -1658,6 +2028,7 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
                          uint32_t *ws_smem, uint32_t *ws_glob, const uint32_t *taskbuf, int lane,
                          int32_t &built, int &node_tick, uint64_t t_start) {
     const int32_t root = T.root;
+    s.lp_n = s.lp_top = 0;   // nothing buffered survives a dropped task
     // ---- build (or reuse) the subproblem
     int32_t w, c;
     if (P.mode == BK_MCE) {
@@ -1815,13 +2186,16 @@ __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
     for (int i = threadIdx.x; i < 256; i += blockDim.x) shist[i] = 0ULL;
     __syncthreads();
     uint32_t *ws_smem = smem + 512 + (int64_t)nw_block * BK_PIV_WORDS + (int64_t)wib * P.smem_words;
+    uint32_t *lp_smem = smem + 512 + (int64_t)nw_block * (BK_PIV_WORDS + P.smem_words) + (int64_t)wib * P.lp_words;
     const int64_t gwarp = (int64_t)blockIdx.x * nw_block + wib;
     uint32_t *ws_glob = P.gws + gwarp * P.gws_words;
     uint32_t *taskbuf = P.taskbuf + gwarp * P.slot_words;
-    Acc acc = {0, 0, 0, 0, 64, 4};
+    Acc acc = {0, 0, 0, 0, 64, 4, 0};
     if (lane == 0) cold() = AccCold{0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     Ws s;
     s.piv = smem + 512 + (int64_t)wib * BK_PIV_WORDS;
+    s.lp = lp_smem;
+    s.lp_n = s.lp_top = 0;
     int32_t built = -1;
     int node_tick = 0;
     bool hungry = false;
@@ -1981,11 +2355,11 @@ mce_status init_queue_seq(unsigned long long *seq, int64_t n, cudaStream_t s) {
     return MCE_OK;
 }
 
-mce_status bk_prepare(int32_t warps_per_block, int32_t blocks_per_sm, int32_t smem_words) {
+mce_status bk_prepare(int32_t blocks_per_sm, int64_t smem_bytes) {
     // dynamic shared memory above the 48 KB default must be opted into once
     // per kernel, outside any stream capture
     static std::atomic<int> granted[3] = {48 * 1024, 48 * 1024, 48 * 1024};
-    const int smem = (int)bk_block_smem_bytes(warps_per_block, smem_words);
+    const int smem = (int)smem_bytes;
     const int t = blocks_per_sm >= 4 ? 2 : (blocks_per_sm == 3 ? 1 : 0);
     if (smem <= granted[t].load()) return MCE_OK;
     if (t == 2) MCE_CUDA(cudaFuncSetAttribute(k_bk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -1998,9 +2372,9 @@ mce_status bk_prepare(int32_t warps_per_block, int32_t blocks_per_sm, int32_t sm
 }
 
 mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s) {
-    const size_t smem = (size_t)bk_block_smem_bytes(warps_per_block, p.smem_words);
+    const size_t smem = (size_t)bk_block_smem_bytes(warps_per_block, p.smem_words, p.lp_words);
     const unsigned blocks = (unsigned)(num_sms() * blocks_per_sm);
-    MCE_TRY(bk_prepare(warps_per_block, blocks_per_sm, p.smem_words));
+    MCE_TRY(bk_prepare(blocks_per_sm, (int64_t)smem));
     // 4 resident blocks of 256 threads leave 64 registers a thread; fewer
     // blocks let the compiler keep the search state in more registers
     if (blocks_per_sm >= 4) MCE_LAUNCH(k_bk<4>, blocks, warps_per_block * 32, smem, s, p);

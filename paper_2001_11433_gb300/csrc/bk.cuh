@@ -98,6 +98,9 @@ struct BkParams {
     uint32_t split_nodes;     // a task hands over a piece after this many nodes (0 = only when warps wait)
     uint64_t timeout_ns;      // bound on any single wait
     uint64_t max_run_ns;      // bound on a warp's time in one launch
+    int32_t lp_words;         // per-warp shared words of the lane-parallel small search (0 = off)
+    uint32_t *lp_tasks;       // per warp: two lists of lp_task_cap node records (BK_LP_TASK_WORDS each)
+    int32_t lp_task_cap;
 };
 
 // Words of the read-only part of a built subproblem with w local vertices of
@@ -124,10 +127,22 @@ __host__ __device__ inline int64_t bk_shared_words(int64_t w, int64_t c) {
 // global and local ids of C and the local ids of X.
 constexpr int BK_PIV_WORDS = 64 + 256 + 96;
 
+// Lane-parallel small search: per warp a table of up to BK_LP_MAX_ROOTS
+// relabelled small nodes (4 words each, then the next-root counter) and an
+// arena for their universes.
+constexpr int BK_LP_MAX_ROOTS = 64;
+constexpr int BK_LP_TABLE_WORDS = BK_LP_MAX_ROOTS * 4 + 4;
+// A node of a small subtree waiting for a lane: root index | depth << 8,
+// cand, finc, xs, hash sum (2 words).
+constexpr int BK_LP_TASK_WORDS = 6;
+constexpr int BK_LP_TASK_CAP = 1024;
+
 // Dynamic shared memory of one search block: 256 histogram bins, the pivot
-// scratch of every warp, then the optional per-warp workspace slots.
-__host__ __device__ inline int64_t bk_block_smem_bytes(int32_t warps_per_block, int32_t smem_words) {
-    return (int64_t)512 * 4 + (int64_t)warps_per_block * (BK_PIV_WORDS + smem_words) * 4;
+// scratch of every warp, the optional per-warp workspace slots, then the
+// per-warp regions of the lane-parallel small search.
+__host__ __device__ inline int64_t bk_block_smem_bytes(int32_t warps_per_block, int32_t smem_words,
+                                                       int32_t lp_words) {
+    return (int64_t)512 * 4 + (int64_t)warps_per_block * (BK_PIV_WORDS + smem_words + lp_words) * 4;
 }
 
 // Frames of the explicit stack: one per clique vertex beyond the seeds,
@@ -150,7 +165,7 @@ __host__ __device__ inline int64_t bk_ws_words(int64_t w, int64_t c, int32_t mod
     return bk_shared_words(w, c) + bk_private_words(w, c, mode);
 }
 
-mce_status bk_prepare(int32_t warps_per_block, int32_t blocks_per_sm, int32_t smem_words);
+mce_status bk_prepare(int32_t blocks_per_sm, int64_t smem_bytes);
 mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s);
 mce_status init_queue_seq(unsigned long long *seq, int64_t n, cudaStream_t s);
 

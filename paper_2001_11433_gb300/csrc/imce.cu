@@ -16,6 +16,15 @@
 //   5. index := index \ Λdel ∪ Λnew, G := G'.
 // Steps 1-4 leave the state untouched until everything succeeded; a failure
 // restores the alive flags claimed in step 4.
+//
+// imce_remove_edges, one deletion batch H (edges of G), by the paper's
+// reduction to additions (G = (G - H) + H):
+//   removed = C(G) \ C(G - H): the cliques of G through an edge of H, step 3
+//             run on G itself;
+//   created = C(G - H) \ C(G): Algorithm 8's splits of the removed cliques
+//             that are maximal in G - H, each once           k_dmce_created
+// then the removed cliques leave the index, the created ones enter it, and
+// G := G - H, all or nothing.
 #include <string.h>
 
 #include <vector>
@@ -66,7 +75,7 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t 
 // ------------------------------------------------------------------ canonical batch
 
 __global__ void k_batch_keys(const int32_t *u, const int32_t *v, int64_t k, int32_t n, const int32_t *row_ptr,
-                             const int32_t *col, int32_t B, int32_t IB, uint64_t *keys, int32_t *bad) {
+                             const int32_t *col, int32_t B, int32_t IB, int32_t present, uint64_t *keys, int32_t *bad) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a0 = u[i], b0 = v[i];
         uint64_t key = ~0ULL;
@@ -76,7 +85,8 @@ __global__ void k_batch_keys(const int32_t *u, const int32_t *v, int64_t k, int3
             const int32_t a = min(a0, b0), b = max(a0, b0);
             const int32_t r0 = row_ptr[a], d = row_ptr[a + 1] - r0;
             const int p = lower_bound_i32(col + r0, d, b);
-            if (!(p < d && col[r0 + p] == b)) key = ((((uint64_t)a << B) | (uint64_t)b) << IB) | (uint64_t)i;
+            const bool in_g = p < d && col[r0 + p] == b;
+            if (in_g == (present != 0)) key = ((((uint64_t)a << B) | (uint64_t)b) << IB) | (uint64_t)i;
         }
         keys[i] = key;
     }
@@ -469,6 +479,345 @@ __global__ void __launch_bounds__(256) k_imce_sub(SubParams P) {
     }
 }
 
+// ------------------------------------------------------------------ edge deletions
+
+__global__ void k_sub_deg(const int32_t *row_ptr, const int32_t *hdeg, int32_t n, int32_t *deg2) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        deg2[x] = row_ptr[x + 1] - row_ptr[x] - hdeg[x];
+}
+
+// Row x of G - H: the old row without the deleted neighbours (a sorted
+// subset of it), each kept entry moved down by the deleted ones before it.
+__global__ void k_minus_rows(const int32_t *row_ptr, const int32_t *col, const int32_t *h_ptr, const int32_t *h_adj,
+                             const int32_t *row_ptr2, int32_t n, int32_t *col2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = warp; x < n; x += nw) {
+        const int32_t o0 = row_ptr[x], od = row_ptr[x + 1] - o0;
+        const int32_t n0 = h_ptr[x], nd = h_ptr[x + 1] - n0;
+        const int32_t dst = row_ptr2[x];
+        for (int i = lane; i < od; i += 32) {
+            const int32_t val = col[o0 + i];
+            const int p = nd ? lower_bound_i32(h_adj + n0, nd, val) : 0;
+            if (p < nd && h_adj[n0 + p] == val) continue;
+            col2[dst + i - p] = val;
+        }
+    }
+}
+
+__device__ __forceinline__ bool has_edge_csr(const int32_t *row_ptr, const int32_t *col, int32_t a, int32_t b) {
+    const int32_t r0 = row_ptr[a], d = row_ptr[a + 1] - r0;
+    const int p = lower_bound_i32(col + r0, d, b);
+    return p < d && col[r0 + p] == b;
+}
+
+// The members of candidate m (bit j of the mask = cv[j]) form a maximal
+// clique of G (row_ptr, col) iff no vertex outside them is adjacent to all.
+__device__ bool cand_is_maximal(const int32_t *row_ptr, const int32_t *col, const int32_t *cv, int32_t s,
+                                const unsigned long long (&m)[kSubMaxWords]) {
+    int32_t best = -1, bd = 0x7fffffff;
+    for (int w = 0; w < kSubMaxWords; ++w)
+        for (unsigned long long x = m[w]; x; x &= x - 1) {
+            const int32_t v = cv[w * 64 + __ffsll((long long)x) - 1];
+            const int32_t dv = row_ptr[v + 1] - row_ptr[v];
+            if (dv < bd) {
+                bd = dv;
+                best = v;
+            }
+        }
+    if (best < 0) return false;
+    for (int32_t e = row_ptr[best]; e < row_ptr[best + 1]; ++e) {
+        const int32_t y = col[e];
+        const int p = lower_bound_i32(cv, s, y);
+        if (p < s && cv[p] == y && ((m[p >> 6] >> (p & 63)) & 1ULL)) continue;   // a member
+        bool all = true;
+        for (int w = 0; w < kSubMaxWords && all; ++w)
+            for (unsigned long long x = m[w]; x && all; x &= x - 1) {
+                const int32_t v = cv[w * 64 + __ffsll((long long)x) - 1];
+                if (v != best && !has_edge_csr(row_ptr, col, y, v)) all = false;
+            }
+        if (all) return false;
+    }
+    return true;
+}
+
+struct DelParams {
+    const int64_t *roff;      // removed cliques (sorted lists)
+    const int32_t *rvtx;
+    int64_t n_rem;
+    const int32_t *h_ptr, *h_adj;
+    const int32_t *row_ptr, *col;   // G - H
+    uint64_t seed;
+    unsigned long long *scratch;   // per warp: 2 * kSubCap masks of kSubMaxWords words
+    // created cliques, each once: records (removed clique index, H(K), mask)
+    // and a table of record + 1 that keeps one record per distinct clique
+    int64_t *rec_c;
+    unsigned long long *rec_h;
+    unsigned long long *rec_m;     // kSubMaxWords words per record
+    int32_t *rec_win;              // 1 = the record that stands for its clique
+    unsigned long long *n_rec;
+    int64_t rec_cap;
+    int32_t *tid;
+    int64_t tmask;
+    unsigned long long *out;       // OUT block of the created cliques
+    int32_t *status;               // 1 = a clique too large, 2 = too many candidates, 4 = record space full
+};
+
+// Do record b (written by another warp: read through L2) and the candidate
+// (clique ca, mask ma) have the same members?
+__device__ bool same_members(const DelParams &P, int64_t ca, const unsigned long long (&ma)[kSubMaxWords],
+                             int64_t b) {
+    unsigned long long mb[kSubMaxWords];
+#pragma unroll
+    for (int w = 0; w < kSubMaxWords; ++w) mb[w] = __ldcg(P.rec_m + b * kSubMaxWords + w);
+    const int64_t cb = __ldcg(P.rec_c + b);
+    const int32_t *va = P.rvtx + P.roff[ca] + 1, *vb = P.rvtx + P.roff[cb] + 1;
+    int wa = 0, wb = 0;
+    unsigned long long xa = ma[0], xb = mb[0];
+    for (;;) {
+        while (!xa && wa + 1 < kSubMaxWords) xa = ma[++wa];
+        while (!xb && wb + 1 < kSubMaxWords) xb = mb[++wb];
+        if (!xa || !xb) return !xa && !xb;
+        if (va[wa * 64 + __ffsll((long long)xa) - 1] != vb[wb * 64 + __ffsll((long long)xb) - 1]) return false;
+        xa &= xa - 1;
+        xb &= xb - 1;
+    }
+}
+
+// Edge deletions by reduction to additions: G = (G - H) + H, so the cliques
+// that the deletion creates are Algorithm 8's splits of the removed cliques
+// (those of G through an edge of H) that are maximal in G - H.  One warp per
+// removed clique splits it as k_imce_sub does; each split that is maximal in
+// G - H is inserted once into a table keyed by H(K) with member comparison.
+__global__ void __launch_bounds__(256) k_dmce_created(DelParams P) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int MW = kSubMaxWords;
+    unsigned long long *S = P.scratch + gw * (int64_t)2 * kSubCap * MW;
+    unsigned long long *S2 = S + (int64_t)kSubCap * MW;
+    __shared__ int32_t edges_s[8][2 * 512];
+    int32_t *edges = edges_s[threadIdx.x >> 5];
+    for (int64_t c = gw; c < P.n_rem; c += nw) {
+        const int32_t *cv = P.rvtx + P.roff[c] + 1;
+        const int32_t s = cv[-1];
+        if (s > 64 * MW) {
+            if (lane == 0) atomicOr(P.status, 1);
+            continue;
+        }
+        // deleted edges inside c: (i, j) positions, i < j, lexicographic
+        int ne = 0;
+        for (int i = 0; i < s; ++i) {
+            const int32_t a = cv[i];
+            const int32_t h0 = P.h_ptr[a], hd = P.h_ptr[a + 1] - h0;
+            for (int t0 = 0; t0 < hd; t0 += 32) {
+                int j = -1;
+                if (t0 + lane < hd) {
+                    const int32_t y = P.h_adj[h0 + t0 + lane];
+                    if (y > a) {
+                        const int p = lower_bound_i32(cv, s, y);
+                        if (p < s && cv[p] == y) j = p;
+                    }
+                }
+                const uint32_t b = __ballot_sync(FULL, j >= 0);
+                if (j >= 0) {
+                    const int slot = ne + __popc(b & lanemask_lt());
+                    if (slot < 512) {
+                        edges[2 * slot] = i;
+                        edges[2 * slot + 1] = j;
+                    }
+                }
+                ne += __popc(b);
+            }
+        }
+        __syncwarp();
+        if (ne > 512) {
+            if (lane == 0) atomicOr(P.status, 2);
+            continue;
+        }
+        int ns = 1;
+        if (lane < MW) {
+            const int lo = lane * 64;
+            const int nb = s - lo;
+            S[lane] = nb >= 64 ? ~0ULL : (nb > 0 ? ((1ULL << nb) - 1) : 0ULL);
+        }
+        __syncwarp();
+        bool overflow = false;
+        for (int e = 0; e < ne && !overflow; ++e) {
+            const int ei = edges[2 * e], ej = edges[2 * e + 1];
+            const int wi = ei >> 6, wj = ej >> 6;
+            const unsigned long long bi = 1ULL << (ei & 63), bj = 1ULL << (ej & 63);
+            int n2 = 0;
+            for (int t0 = 0; t0 < ns; t0 += 32) {
+                const int t = t0 + lane;
+                bool both = false, valid = t < ns;
+                unsigned long long m[MW];
+                if (valid) {
+#pragma unroll
+                    for (int w = 0; w < MW; ++w) m[w] = S[(int64_t)t * MW + w];
+                    both = (m[wi] & bi) && (m[wj] & bj);
+                }
+                const uint32_t bb = __ballot_sync(FULL, valid && both);
+                const uint32_t bv = __ballot_sync(FULL, valid);
+                const int before = 2 * __popc(bb & lanemask_lt()) + __popc(bv & ~bb & lanemask_lt());
+                const int total = 2 * __popc(bb) + __popc(bv & ~bb);
+                if (n2 + total > kSubCap) {
+                    overflow = true;
+                    break;
+                }
+                if (valid) {
+                    unsigned long long *d0 = S2 + (int64_t)(n2 + before) * MW;
+                    if (both) {
+#pragma unroll
+                        for (int w = 0; w < MW; ++w) {
+                            d0[w] = m[w] & ~(w == wi ? bi : 0ULL);
+                            d0[MW + w] = m[w] & ~(w == wj ? bj : 0ULL);
+                        }
+                    } else {
+#pragma unroll
+                        for (int w = 0; w < MW; ++w) d0[w] = m[w];
+                    }
+                }
+                n2 += total;
+            }
+            __syncwarp();
+            if (overflow) break;
+            ns = 0;
+            for (int t = 0; t < n2; ++t) {
+                const unsigned long long *cand = S2 + (int64_t)t * MW;
+                bool dup = false;
+                for (int q0 = 0; q0 < ns && !dup; q0 += 32) {
+                    const int q = q0 + lane;
+                    bool eq = false;
+                    if (q < ns) {
+                        eq = true;
+#pragma unroll
+                        for (int w = 0; w < MW; ++w) eq &= S[(int64_t)q * MW + w] == cand[w];
+                    }
+                    dup = __any_sync(FULL, eq);
+                }
+                if (!dup) {
+                    if (lane < MW) S[(int64_t)ns * MW + lane] = cand[lane];
+                    ++ns;
+                    __syncwarp();
+                }
+            }
+            __syncwarp();
+        }
+        if (overflow) {
+            if (lane == 0) atomicOr(P.status, 2);
+            continue;
+        }
+        // every split maximal in G - H, inserted once
+        for (int t0 = 0; t0 < ns; t0 += 32) {
+            const int t = t0 + lane;
+            if (t >= ns) continue;
+            unsigned long long m[MW];
+            int32_t size = 0;
+            uint64_t hs = 0;
+#pragma unroll
+            for (int w = 0; w < MW; ++w) {
+                m[w] = S[(int64_t)t * MW + w];
+                for (unsigned long long x = m[w]; x; x &= x - 1) {
+                    hs += vertex_hash(cv[w * 64 + __ffsll((long long)x) - 1], P.seed);
+                    ++size;
+                }
+            }
+            if (size == 0 || !cand_is_maximal(P.row_ptr, P.col, cv, s, m)) continue;
+            const uint64_t h = clique_hash_from_sum(hs, (uint32_t)size);
+            const unsigned long long r = atomicAdd(P.n_rec, 1ULL);
+            if ((int64_t)r >= P.rec_cap) {
+                atomicOr(P.status, 4);
+                continue;
+            }
+            P.rec_c[r] = c;
+            P.rec_h[r] = h;
+#pragma unroll
+            for (int w = 0; w < MW; ++w) P.rec_m[r * MW + w] = m[w];
+            __threadfence();   // the record is complete before its slot is published
+            int64_t slot = (int64_t)(h & (uint64_t)P.tmask);
+            bool fresh = false;
+            for (int64_t probe = 0; probe <= P.tmask; ++probe) {
+                const int32_t prev = atomicCAS(&P.tid[slot], 0, (int32_t)(r + 1));
+                if (prev == 0) {
+                    fresh = true;
+                    break;
+                }
+                const int64_t o = prev - 1;
+                if (__ldcg(P.rec_h + o) == h && same_members(P, c, m, o)) break;   // already there
+                slot = (slot + 1) & P.tmask;
+            }
+            if (!fresh) continue;
+            P.rec_win[r] = 1;
+            atomicAdd(&P.out[OUT_COUNT], 1ULL);
+            atomicAdd(&P.out[OUT_HASH], h);
+            if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
+            atomicMax(&P.out[OUT_MAXSIZE], (unsigned long long)size);
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_rec_words(const int32_t *win, const unsigned long long *rec_m, int64_t n, int32_t *flag,
+                            int64_t *words) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t sz = 0;
+        for (int w = 0; w < kSubMaxWords; ++w) sz += __popcll(rec_m[r * kSubMaxWords + w]);
+        flag[r] = win[r];
+        words[r] = win[r] ? sz + 1 : 0;
+    }
+}
+
+// winning record r -> list entry flag_scan[r] at word offset wpos[r]: size, then the members ascending
+__global__ void k_rec_lists(const int32_t *flag_scan, const int64_t *wpos, const int64_t *rec_c,
+                            const unsigned long long *rec_m, int64_t n, const int64_t *roff, const int32_t *rvtx,
+                            int64_t *loff, int32_t *lvtx) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        if (flag_scan[r + 1] == flag_scan[r]) continue;
+        const int32_t *cv = rvtx + roff[rec_c[r]] + 1;
+        int64_t p = wpos[r];
+        loff[flag_scan[r]] = p;
+        int32_t sz = 0;
+        for (int w = 0; w < kSubMaxWords; ++w)
+            for (unsigned long long x = rec_m[r * kSubMaxWords + w]; x; x &= x - 1) lvtx[p + 1 + sz++] = cv[w * 64 + __ffsll((long long)x) - 1];
+        lvtx[p] = sz;
+    }
+}
+
+// Claim (alive 1 -> 0) the index entry of every listed clique; a clique not
+// found alive sets *missing.
+__global__ void k_index_claim(const int64_t *loff, const int32_t *lvtx, int64_t nc, const int32_t *pool,
+                              const int64_t *off, int32_t *alive, const unsigned long long *tkey, const int32_t *tid,
+                              int64_t tmask, uint64_t seed, int64_t *claimed, unsigned long long *n_claimed,
+                              int32_t *missing) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t *src = lvtx + loff[c];
+        const int32_t sz = src[0];
+        const uint64_t h = list_hash(src + 1, sz, seed);
+        int64_t slot = (int64_t)(h & (uint64_t)tmask), found = -1;
+        for (int64_t probe = 0; probe <= tmask; ++probe) {
+            const int32_t id1 = tid[slot];
+            if (id1 == 0) break;
+            if (tkey[slot] == h) {
+                const int32_t *pl = pool + off[id1 - 1];
+                bool eq = pl[0] == sz;
+                for (int q = 1; q <= sz && eq; ++q) eq = pl[q] == src[q];
+                if (eq && alive[id1 - 1]) {
+                    found = id1 - 1;
+                    break;
+                }
+            }
+            slot = (slot + 1) & tmask;
+        }
+        if (found >= 0 && atomicCAS(&alive[found], 1, 0) == 1) {
+            claimed[atomicAdd(n_claimed, 1ULL)] = found;
+        } else {
+            atomicOr(missing, 1);
+        }
+    }
+}
+
 __global__ void k_restore_alive(const int64_t *claimed, int64_t n, int32_t *alive) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         alive[claimed[i]] = 1;
@@ -620,28 +969,27 @@ void fill_hist(const unsigned long long *h, int32_t *len, uint64_t *hist) {
     for (int i = 0; i < MCE_HIST_CAP; ++i) hist[i] = i < *len ? h[OUT_HIST + i] : 0;
 }
 
-mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t k, imce_delta *out) {
+// A canonical batch: e_1..e_rho in arrival order (Algorithm 6 line 2) and
+// its adjacency (both directions, sorted by neighbour, with edge indices).
+struct Batch {
+    DevBuf eu, ev, hdeg, h_ptr, h_adj, h_idx;   // hdeg: batch edges at each vertex; h_ptr: their offsets
+    int32_t rho = 0;
+};
+
+// Canonicalise k raw pairs against G: additions keep the pairs that are not
+// edges of G, deletions those that are; self loops and repeats are dropped
+// and the first arrival of a pair kept.
+mce_status canonical_batch(imce_state *S, const int32_t *u, const int32_t *v, int64_t k, bool deletion,
+                           const char *who, Batch &bt) {
     cudaStream_t s = S->s;
-    mce_graph *g = S->g;
+    const mce_graph *g = S->g;
     const int32_t n = g->n, B = g->id_bits;
     const int32_t IB = bits_for((uint64_t)(k > 0 ? k : 1));
     if (2 * B + IB > 63) {
-        g_last_error = "imce_add_edges: batch too large for this graph";
+        g_last_error = std::string(who) + ": batch too large for this graph";
         return MCE_EINVAL;
     }
-    cudaEvent_t e0, e1;
-    MCE_CUDA(cudaEventCreate(&e0));
-    MCE_CUDA(cudaEventCreate(&e1));
-    struct EvG {
-        cudaEvent_t a, b;
-        ~EvG() {
-            cudaEventDestroy(a);
-            cudaEventDestroy(b);
-        }
-    } evg{e0, e1};
-    MCE_CUDA(cudaEventRecord(e0, s));
-    // ---- 1. canonical batch
-    DevBuf keys, tmp, keep, bad, eu, ev;
+    DevBuf keys, tmp, keep, bad;
     const int64_t kk = k > 0 ? k : 1;
     MCE_TRY(keys.alloc((size_t)kk * 8, s));
     MCE_TRY(tmp.alloc((size_t)kk * 8, s));
@@ -649,122 +997,133 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
     MCE_TRY(bad.alloc(4, s));
     MCE_CUDA(cudaMemsetAsync(bad.p, 0, 4, s));
     MCE_CUDA(cudaMemsetAsync(keep.p, 0, (size_t)(kk + 1) * 4, s));
-    int32_t rho = 0;
+    bt.rho = 0;
     if (k > 0) {
         MCE_LAUNCH(k_batch_keys, grid_for(k, 256), 256, 0, s, u, v, k, n, g->row_ptr, g->col, B, IB,
-                   keys.as<uint64_t>(), bad.as<int32_t>());
+                   (int32_t)deletion, keys.as<uint64_t>(), bad.as<int32_t>());
         MCE_TRY(radix_sort_u64(keys.as<uint64_t>(), tmp.as<uint64_t>(), k, 64, s));
         MCE_LAUNCH(k_first_arrival, grid_for(k, 256), 256, 0, s, keys.as<uint64_t>(), k, IB, keep.as<int32_t>());
         MCE_TRY(exclusive_scan_i32(keep.as<int32_t>(), keep.as<int32_t>(), k, s));
         int32_t hb = 0;
         MCE_CUDA(cudaMemcpyAsync(&hb, bad.p, 4, cudaMemcpyDeviceToHost, s));
-        MCE_CUDA(cudaMemcpyAsync(&rho, keep.as<int32_t>() + k, 4, cudaMemcpyDeviceToHost, s));
+        MCE_CUDA(cudaMemcpyAsync(&bt.rho, keep.as<int32_t>() + k, 4, cudaMemcpyDeviceToHost, s));
         MCE_CUDA(cudaStreamSynchronize(s));
         if (hb) {
-            g_last_error = "imce_add_edges: vertex id outside [0, n)";
+            g_last_error = std::string(who) + ": vertex id outside [0, n)";
             return MCE_EINVAL;
         }
     }
-    memset(out, 0, sizeof(*out));
-    out->applied = rho;
-    out->dropped = k - rho;
-    if (rho == 0) {
-        out->alive = (uint64_t)S->idx.n_alive;
-        MCE_CUDA(cudaEventRecord(e1, s));
-        MCE_CUDA(cudaEventSynchronize(e1));
-        cudaEventElapsedTime(&out->ms, e0, e1);
-        return MCE_OK;
-    }
-    MCE_TRY(eu.alloc((size_t)rho * 4, s));
-    MCE_TRY(ev.alloc((size_t)rho * 4, s));
-    MCE_LAUNCH(k_emit_batch, grid_for(k, 256), 256, 0, s, u, v, keep.as<int32_t>(), k, eu.as<int32_t>(),
-               ev.as<int32_t>());
-    // ---- batch adjacency (both directions, sorted by neighbour, with edge index)
+    const int32_t rho = bt.rho;
+    if (rho == 0) return MCE_OK;
+    MCE_TRY(bt.eu.alloc((size_t)rho * 4, s));
+    MCE_TRY(bt.ev.alloc((size_t)rho * 4, s));
+    MCE_LAUNCH(k_emit_batch, grid_for(k, 256), 256, 0, s, u, v, keep.as<int32_t>(), k, bt.eu.as<int32_t>(),
+               bt.ev.as<int32_t>());
     const int32_t IBr = bits_for((uint64_t)rho);
-    DevBuf hkeys, htmp, h_ptr, h_adj, h_idx;
+    DevBuf hkeys, htmp;
     MCE_TRY(hkeys.alloc((size_t)2 * rho * 8, s));
     MCE_TRY(htmp.alloc((size_t)2 * rho * 8, s));
-    MCE_TRY(h_ptr.alloc(((size_t)n + 1) * 4, s));
-    MCE_TRY(h_adj.alloc((size_t)2 * rho * 4, s));
-    MCE_TRY(h_idx.alloc((size_t)2 * rho * 4, s));
-    MCE_CUDA(cudaMemsetAsync(h_ptr.p, 0, ((size_t)n + 1) * 4, s));
-    MCE_LAUNCH(k_h_keys, grid_for(rho, 256), 256, 0, s, eu.as<int32_t>(), ev.as<int32_t>(), rho, B, IBr,
-               hkeys.as<uint64_t>(), h_ptr.as<int32_t>());
+    MCE_TRY(bt.hdeg.alloc(((size_t)n + 1) * 4, s));
+    MCE_TRY(bt.h_ptr.alloc(((size_t)n + 1) * 4, s));
+    MCE_TRY(bt.h_adj.alloc((size_t)2 * rho * 4, s));
+    MCE_TRY(bt.h_idx.alloc((size_t)2 * rho * 4, s));
+    MCE_CUDA(cudaMemsetAsync(bt.hdeg.p, 0, ((size_t)n + 1) * 4, s));
+    MCE_LAUNCH(k_h_keys, grid_for(rho, 256), 256, 0, s, bt.eu.as<int32_t>(), bt.ev.as<int32_t>(), rho, B, IBr,
+               hkeys.as<uint64_t>(), bt.hdeg.as<int32_t>());
     MCE_TRY(radix_sort_u64(hkeys.as<uint64_t>(), htmp.as<uint64_t>(), 2 * (int64_t)rho, 2 * B + IBr, s));
     MCE_LAUNCH(k_h_fill, grid_for(2 * (int64_t)rho, 256), 256, 0, s, hkeys.as<uint64_t>(), 2 * (int64_t)rho, B, IBr,
-               h_adj.as<int32_t>(), h_idx.as<int32_t>());
-    // ---- 2. G' = G + H
+               bt.h_adj.as<int32_t>(), bt.h_idx.as<int32_t>());
+    MCE_TRY(exclusive_scan_i32(bt.hdeg.as<int32_t>(), bt.h_ptr.as<int32_t>(), n, s));
+    return MCE_OK;
+}
+
+struct GraphGuard {
+    mce_graph *g = nullptr;
+    ~GraphGuard() {
+        if (g) {
+            cudaFree(g->row_ptr);
+            cudaFree(g->col);
+            delete g;
+        }
+    }
+};
+
+// G + H (add) or G - H (every batch edge an edge of G).
+mce_status combine_graph(const mce_graph *g, Batch &bt, bool add, cudaStream_t s, GraphGuard &out) {
+    const int32_t n = g->n;
     DevBuf deg2;
     MCE_TRY(deg2.alloc(((size_t)n + 1) * 4, s));
-    MCE_LAUNCH(k_add_deg, grid_for(n, 256), 256, 0, s, g->row_ptr, h_ptr.as<int32_t>(), n, deg2.as<int32_t>());
-    MCE_TRY(exclusive_scan_i32(h_ptr.as<int32_t>(), h_ptr.as<int32_t>(), n, s));
+    if (add) MCE_LAUNCH(k_add_deg, grid_for(n, 256), 256, 0, s, g->row_ptr, bt.hdeg.as<int32_t>(), n, deg2.as<int32_t>());
+    else MCE_LAUNCH(k_sub_deg, grid_for(n, 256), 256, 0, s, g->row_ptr, bt.hdeg.as<int32_t>(), n, deg2.as<int32_t>());
     mce_graph *g2 = new mce_graph();
-    struct GGuard {
-        mce_graph *&g;
-        bool keep = false;
-        ~GGuard() {
-            if (!keep && g) {
-                cudaFree(g->row_ptr);
-                cudaFree(g->col);
-                delete g;
-            }
-        }
-    } gg{g2};
+    out.g = g2;
     g2->n = n;
-    g2->id_bits = B;
-    g2->nnz = g->nnz + 2 * (int64_t)rho;
+    g2->id_bits = g->id_bits;
+    g2->nnz = g->nnz + (add ? 2 : -2) * (int64_t)bt.rho;
     MCE_TRY(dev_alloc((void **)&g2->row_ptr, ((size_t)n + 1) * 4, s, "alloc G'"));
     MCE_TRY(dev_alloc((void **)&g2->col, ((size_t)g2->nnz + 4) * 4, s, "alloc G'"));
     MCE_TRY(exclusive_scan_i32(deg2.as<int32_t>(), g2->row_ptr, n, s));
-    MCE_LAUNCH(k_merge_rows, grid_for((int64_t)n * 32, 256), 256, 0, s, g->row_ptr, g->col, h_ptr.as<int32_t>(),
-               h_adj.as<int32_t>(), g2->row_ptr, n, g2->col);
+    if (add)
+        MCE_LAUNCH(k_merge_rows, grid_for((int64_t)n * 32, 256), 256, 0, s, g->row_ptr, g->col, bt.h_ptr.as<int32_t>(),
+                   bt.h_adj.as<int32_t>(), g2->row_ptr, n, g2->col);
+    else
+        MCE_LAUNCH(k_minus_rows, grid_for((int64_t)n * 32, 256), 256, 0, s, g->row_ptr, g->col, bt.h_ptr.as<int32_t>(),
+                   bt.h_adj.as<int32_t>(), g2->row_ptr, n, g2->col);
+    return MCE_OK;
+}
+
+// The maximal cliques of gp (a graph holding every batch edge) through an edge
+// of the batch, each found once: Algorithm 6 with the exclusion of Algorithm
+// 7/9, on the persistent engine.  Sorted lists in (loff, lvtx), summary in h.
+mce_status batch_cliques(imce_state *S, const mce_graph *gp, Batch &bt, DevBuf &loff, DevBuf &lvtx,
+                         unsigned long long *h) {
+    cudaStream_t s = S->s;
+    const int32_t n = gp->n, rho = bt.rho;
+    const int32_t IBr = bits_for((uint64_t)rho);
     // degree-oriented Γ'+ lists
     DevBuf dkey, drank, up_ptr, up_col;
     MCE_TRY(dkey.alloc((size_t)n * 8, s));
     MCE_TRY(drank.alloc((size_t)n * 4, s));
-    MCE_TRY(vertex_key(g2, MCE_RANK_DEGREE, s, dkey.as<int64_t>()));
-    MCE_TRY(rank_from_key_i64(dkey.as<int64_t>(), n, B, s, drank.as<int32_t>()));
+    MCE_TRY(vertex_key(gp, MCE_RANK_DEGREE, s, dkey.as<int64_t>()));
+    MCE_TRY(rank_from_key_i64(dkey.as<int64_t>(), n, gp->id_bits, s, drank.as<int32_t>()));
     int64_t up_nnz = 0;
-    MCE_TRY(build_up_lists(g2, drank.as<int32_t>(), s, up_ptr, up_col, &up_nnz));
-    // ---- 3. Λnew
+    MCE_TRY(build_up_lists(gp, drank.as<int32_t>(), s, up_ptr, up_col, &up_nnz));
     DevBuf okeys, otmp, order, reqb, nout;
     MCE_TRY(okeys.alloc((size_t)rho * 8, s));
     MCE_TRY(otmp.alloc((size_t)rho * 8, s));
     MCE_TRY(order.alloc((size_t)rho * 4, s));
     MCE_TRY(reqb.alloc(16, s));
     MCE_CUDA(cudaMemsetAsync(reqb.p, 0, 16, s));
-    MCE_LAUNCH(k_edge_order_keys, grid_for(rho, 256), 256, 0, s, g2->row_ptr, eu.as<int32_t>(), ev.as<int32_t>(), rho,
-               IBr, okeys.as<uint64_t>(), reqb.as<unsigned long long>());
+    MCE_LAUNCH(k_edge_order_keys, grid_for(rho, 256), 256, 0, s, gp->row_ptr, bt.eu.as<int32_t>(), bt.ev.as<int32_t>(),
+               rho, IBr, okeys.as<uint64_t>(), reqb.as<unsigned long long>());
     MCE_TRY(radix_sort_u64(okeys.as<uint64_t>(), otmp.as<uint64_t>(), rho, 30 + IBr, s));
     MCE_LAUNCH(k_keys_low, grid_for(rho, 256), 256, 0, s, okeys.as<uint64_t>(), rho, IBr, order.as<int32_t>());
     unsigned long long reqc[2] = {0, 0};
     MCE_CUDA(cudaMemcpyAsync(reqc, reqb.p, 16, cudaMemcpyDeviceToHost, s));
     MCE_CUDA(cudaStreamSynchronize(s));
     MCE_TRY(nout.alloc(OUT_WORDS * 8, s));
-    DevBuf nloff, nlvtx;
     int64_t mc = 1 << 14, mw = 1 << 18;
-    unsigned long long hn[OUT_WORDS];
     for (int attempt = 0;; ++attempt) {
-        MCE_TRY(nloff.alloc((size_t)mc * 8, s));
-        MCE_TRY(nlvtx.alloc((size_t)mw * 4, s));
+        MCE_TRY(loff.alloc((size_t)mc * 8, s));
+        MCE_TRY(lvtx.alloc((size_t)mw * 4, s));
         MCE_CUDA(cudaMemsetAsync(nout.p, 0, OUT_WORDS * 8, s));
         BkParams P{};
         P.mode = BK_IMCE;
-        P.row_ptr = g2->row_ptr;
-        P.col = g2->col;
+        P.row_ptr = gp->row_ptr;
+        P.col = gp->col;
         P.up_ptr = up_ptr.as<int32_t>();
         P.up_col = up_col.as<int32_t>();
         P.order = order.as<int32_t>();
         P.n_sub = rho;
-        P.eu = eu.as<int32_t>();
-        P.ev = ev.as<int32_t>();
-        P.h_ptr = h_ptr.as<int32_t>();
-        P.h_adj = h_adj.as<int32_t>();
-        P.h_idx = h_idx.as<int32_t>();
+        P.eu = bt.eu.as<int32_t>();
+        P.ev = bt.ev.as<int32_t>();
+        P.h_ptr = bt.h_ptr.as<int32_t>();
+        P.h_adj = bt.h_adj.as<int32_t>();
+        P.h_idx = bt.h_idx.as<int32_t>();
         P.seed = S->seed;
         P.out = nout.as<unsigned long long>();
-        P.list_off = nloff.as<int64_t>();
-        P.list_vtx = nlvtx.as<int32_t>();
+        P.list_off = loff.as<int64_t>();
+        P.list_vtx = lvtx.as<int32_t>();
         P.list_max_cliques = mc;
         P.list_max_words = mw;
         P.split = S->opts.split;
@@ -777,7 +1136,7 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
         const LaunchShape ls = launch_shape(&shape);
         MCE_TRY(run_bk(P, ls, (int64_t)reqc[0], (int64_t)reqc[1], s, bb));
         unsigned long long c[CTL_WORDS];
-        MCE_CUDA(cudaMemcpyAsync(hn, nout.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
+        MCE_CUDA(cudaMemcpyAsync(h, nout.p, OUT_WORDS * 8, cudaMemcpyDeviceToHost, s));
         MCE_CUDA(cudaMemcpyAsync(c, bb.ctl.p, sizeof(c), cudaMemcpyDeviceToHost, s));
         MCE_CUDA(cudaStreamSynchronize(s));
         if (c[CTL_ABORT] & 2ULL) {
@@ -788,17 +1147,57 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
             g_last_error = "imce: search workspace smaller than a subproblem";
             return MCE_ESTATE;
         }
-        if (!(hn[OUT_FLAGS] & 1ULL)) break;
+        if (!(h[OUT_FLAGS] & 1ULL)) break;
         if (attempt >= 6) return MCE_EOVERFLOW;
-        mc = (int64_t)hn[OUT_LIST_CLIQUES] + 16;
-        mw = (int64_t)hn[OUT_LIST_WORDS] + 64;
+        mc = (int64_t)h[OUT_LIST_CLIQUES] + 16;
+        mw = (int64_t)h[OUT_LIST_WORDS] + 64;
     }
-    if (hn[OUT_FLAGS] & 2ULL) {
+    if (h[OUT_FLAGS] & 2ULL) {
         g_last_error = "imce: clique larger than the histogram";
         return MCE_EOVERFLOW;
     }
+    const int64_t nl = (int64_t)h[OUT_LIST_CLIQUES];
+    if (nl) MCE_LAUNCH(k_sort_cliques, grid_for(nl, 128), 128, 0, s, loff.as<int64_t>(), nl, lvtx.as<int32_t>());
+    return MCE_OK;
+}
+
+struct EvTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EvTimer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t k, imce_delta *out) {
+    cudaStream_t s = S->s;
+    mce_graph *g = S->g;
+    EvTimer ev;
+    MCE_CUDA(cudaEventCreate(&ev.a));
+    MCE_CUDA(cudaEventCreate(&ev.b));
+    MCE_CUDA(cudaEventRecord(ev.a, s));
+    // ---- 1. canonical batch
+    Batch bt;
+    MCE_TRY(canonical_batch(S, u, v, k, false, "imce_add_edges", bt));
+    const int32_t rho = bt.rho;
+    memset(out, 0, sizeof(*out));
+    out->applied = rho;
+    out->dropped = k - rho;
+    if (rho == 0) {
+        out->alive = (uint64_t)S->idx.n_alive;
+        MCE_CUDA(cudaEventRecord(ev.b, s));
+        MCE_CUDA(cudaEventSynchronize(ev.b));
+        cudaEventElapsedTime(&out->ms, ev.a, ev.b);
+        return MCE_OK;
+    }
+    // ---- 2. G' = G + H
+    GraphGuard gg;
+    MCE_TRY(combine_graph(g, bt, true, s, gg));
+    // ---- 3. Λnew
+    DevBuf nloff, nlvtx;
+    unsigned long long hn[OUT_WORDS];
+    MCE_TRY(batch_cliques(S, gg.g, bt, nloff, nlvtx, hn));
     const int64_t n_new = (int64_t)hn[OUT_LIST_CLIQUES];
-    if (n_new) MCE_LAUNCH(k_sort_cliques, grid_for(n_new, 128), 128, 0, s, nloff.as<int64_t>(), n_new, nlvtx.as<int32_t>());
     // ---- 4. Λdel (Algorithm 8)
     DevBuf sout, scratch, claimed, nclaimed, sstat;
     MCE_TRY(sout.alloc(OUT_WORDS * 8, s));
@@ -821,8 +1220,8 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
         Q.noff = nloff.as<int64_t>();
         Q.nvtx = nlvtx.as<int32_t>();
         Q.n_new = n_new;
-        Q.h_ptr = h_ptr.as<int32_t>();
-        Q.h_adj = h_adj.as<int32_t>();
+        Q.h_ptr = bt.h_ptr.as<int32_t>();
+        Q.h_adj = bt.h_adj.as<int32_t>();
         Q.pool = S->idx.pool;
         Q.off = S->idx.off;
         Q.alive = S->idx.alive;
@@ -857,20 +1256,190 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
         return st;
     }
     S->idx.n_alive -= (int64_t)ncl;
-    gg.keep = true;
     cudaFreeAsync(g->row_ptr, s);
     cudaFreeAsync(g->col, s);
     delete g;
-    S->g = g2;
-    MCE_CUDA(cudaEventRecord(e1, s));
-    MCE_CUDA(cudaEventSynchronize(e1));
-    cudaEventElapsedTime(&out->ms, e0, e1);
+    S->g = gg.g;
+    gg.g = nullptr;
+    MCE_CUDA(cudaEventRecord(ev.b, s));
+    MCE_CUDA(cudaEventSynchronize(ev.b));
+    cudaEventElapsedTime(&out->ms, ev.a, ev.b);
     out->new_count = hn[OUT_COUNT];
     out->new_hash = hn[OUT_HASH];
     fill_hist(hn, &out->new_hist_len, out->new_hist);
     out->sub_count = hs[OUT_COUNT];
     out->sub_hash = hs[OUT_HASH];
     fill_hist(hs, &out->sub_hist_len, out->sub_hist);
+    out->alive = (uint64_t)S->idx.n_alive;
+    return MCE_OK;
+}
+
+// Edge deletions (the paper reduces them to additions: G = (G - H) + H):
+//   removed = the cliques of G through an edge of H = Λnew of adding H to
+//             G - H, found on G by Algorithm 6 with Algorithm 7/9;
+//   created = Algorithm 8's splits of the removed cliques that are maximal
+//             in G - H (= Λdel of adding H to G - H).
+mce_status remove_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t k, imce_delta *out) {
+    cudaStream_t s = S->s;
+    mce_graph *g = S->g;
+    EvTimer ev;
+    MCE_CUDA(cudaEventCreate(&ev.a));
+    MCE_CUDA(cudaEventCreate(&ev.b));
+    MCE_CUDA(cudaEventRecord(ev.a, s));
+    Batch bt;
+    MCE_TRY(canonical_batch(S, u, v, k, true, "imce_remove_edges", bt));
+    const int32_t rho = bt.rho;
+    memset(out, 0, sizeof(*out));
+    out->applied = rho;
+    out->dropped = k - rho;
+    if (rho == 0) {
+        out->alive = (uint64_t)S->idx.n_alive;
+        MCE_CUDA(cudaEventRecord(ev.b, s));
+        MCE_CUDA(cudaEventSynchronize(ev.b));
+        cudaEventElapsedTime(&out->ms, ev.a, ev.b);
+        return MCE_OK;
+    }
+    // ---- removed cliques, on G (which holds every batch edge)
+    DevBuf rloff, rlvtx;
+    unsigned long long hr[OUT_WORDS];
+    MCE_TRY(batch_cliques(S, g, bt, rloff, rlvtx, hr));
+    const int64_t n_rem = (int64_t)hr[OUT_LIST_CLIQUES];
+    // ---- G - H
+    GraphGuard gm;
+    MCE_TRY(combine_graph(g, bt, false, s, gm));
+    // ---- created cliques
+    DevBuf cout_, scratch, rc, rh, rm, rw, nrec, tid, sstat;
+    MCE_TRY(cout_.alloc(OUT_WORDS * 8, s));
+    MCE_CUDA(cudaMemsetAsync(cout_.p, 0, OUT_WORDS * 8, s));
+    unsigned long long hc[OUT_WORDS];
+    memset(hc, 0, sizeof(hc));
+    DevBuf cloff, clvtx;
+    int64_t n_cre = 0;
+    if (n_rem) {
+        const unsigned blocks = (unsigned)num_sms() * 2;
+        const int64_t warps = (int64_t)blocks * 8;
+        MCE_TRY(scratch.alloc((size_t)warps * 2 * kSubCap * kSubMaxWords * 8, s));
+        int64_t cap = 8 * n_rem + 4096;
+        MCE_TRY(sstat.alloc(4, s));
+        MCE_TRY(nrec.alloc(8, s));
+        unsigned long long nr = 0;
+        int32_t hst = 0;
+        for (int attempt = 0;; ++attempt) {
+            int64_t tcap = 1024;
+            while (tcap < 2 * cap) tcap *= 2;
+            MCE_TRY(rc.alloc((size_t)cap * 8, s));
+            MCE_TRY(rh.alloc((size_t)cap * 8, s));
+            MCE_TRY(rm.alloc((size_t)cap * kSubMaxWords * 8, s));
+            MCE_TRY(rw.alloc((size_t)(cap + 1) * 4, s));
+            MCE_TRY(tid.alloc((size_t)tcap * 4, s));
+            MCE_CUDA(cudaMemsetAsync(rw.p, 0, (size_t)(cap + 1) * 4, s));
+            MCE_CUDA(cudaMemsetAsync(tid.p, 0, (size_t)tcap * 4, s));
+            MCE_CUDA(cudaMemsetAsync(nrec.p, 0, 8, s));
+            MCE_CUDA(cudaMemsetAsync(sstat.p, 0, 4, s));
+            MCE_CUDA(cudaMemsetAsync(cout_.p, 0, OUT_WORDS * 8, s));
+            DelParams Q{};
+            Q.roff = rloff.as<int64_t>();
+            Q.rvtx = rlvtx.as<int32_t>();
+            Q.n_rem = n_rem;
+            Q.h_ptr = bt.h_ptr.as<int32_t>();
+            Q.h_adj = bt.h_adj.as<int32_t>();
+            Q.row_ptr = gm.g->row_ptr;
+            Q.col = gm.g->col;
+            Q.seed = S->seed;
+            Q.scratch = scratch.as<unsigned long long>();
+            Q.rec_c = rc.as<int64_t>();
+            Q.rec_h = rh.as<unsigned long long>();
+            Q.rec_m = rm.as<unsigned long long>();
+            Q.rec_win = rw.as<int32_t>();
+            Q.n_rec = nrec.as<unsigned long long>();
+            Q.rec_cap = cap;
+            Q.tid = tid.as<int32_t>();
+            Q.tmask = tcap - 1;
+            Q.out = cout_.as<unsigned long long>();
+            Q.status = sstat.as<int32_t>();
+            MCE_LAUNCH(k_dmce_created, blocks, 256, 0, s, Q);
+            MCE_CUDA(cudaMemcpyAsync(&nr, nrec.p, 8, cudaMemcpyDeviceToHost, s));
+            MCE_CUDA(cudaMemcpyAsync(&hst, sstat.p, 4, cudaMemcpyDeviceToHost, s));
+            MCE_CUDA(cudaMemcpyAsync(hc, cout_.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+            MCE_CUDA(cudaStreamSynchronize(s));
+            if (hst & 3) {
+                g_last_error = hst & 1 ? "imce: removed clique larger than 256 vertices"
+                                       : "imce: too many split candidates";
+                return MCE_ESTATE;
+            }
+            if (!(hst & 4)) break;
+            if (attempt >= 4) return MCE_EOVERFLOW;
+            cap = (int64_t)nr + 1024;   // room for every record of the last try
+        }
+        // winning records -> sorted lists
+        const int64_t nrec_all = (int64_t)nr;
+        DevBuf flag, words;
+        MCE_TRY(flag.alloc((size_t)(nrec_all + 1) * 4, s));
+        MCE_TRY(words.alloc((size_t)(nrec_all + 1) * 8, s));
+        if (nrec_all)
+            MCE_LAUNCH(k_rec_words, grid_for(nrec_all, 256), 256, 0, s, rw.as<int32_t>(), rm.as<unsigned long long>(),
+                       nrec_all, flag.as<int32_t>(), words.as<int64_t>());
+        MCE_TRY(exclusive_scan_i32(flag.as<int32_t>(), flag.as<int32_t>(), nrec_all, s));
+        MCE_TRY(exclusive_scan_i64(words.as<int64_t>(), words.as<int64_t>(), nrec_all, s));
+        int32_t ncr = 0;
+        int64_t nwd = 0;
+        MCE_CUDA(cudaMemcpyAsync(&ncr, flag.as<int32_t>() + nrec_all, 4, cudaMemcpyDeviceToHost, s));
+        MCE_CUDA(cudaMemcpyAsync(&nwd, words.as<int64_t>() + nrec_all, 8, cudaMemcpyDeviceToHost, s));
+        MCE_CUDA(cudaStreamSynchronize(s));
+        n_cre = ncr;
+        MCE_TRY(cloff.alloc((size_t)(n_cre + 1) * 8, s));
+        MCE_TRY(clvtx.alloc((size_t)(nwd + 1) * 4, s));
+        if (nrec_all)
+            MCE_LAUNCH(k_rec_lists, grid_for(nrec_all, 256), 256, 0, s, flag.as<int32_t>(), words.as<int64_t>(),
+                       rc.as<int64_t>(), rm.as<unsigned long long>(), nrec_all, rloff.as<int64_t>(),
+                       rlvtx.as<int32_t>(), cloff.as<int64_t>(), clvtx.as<int32_t>());
+    }
+    // ---- commit: removed cliques leave the index, created ones enter it, G := G - H
+    DevBuf claimed, nclaimed, missing;
+    MCE_TRY(claimed.alloc((size_t)(n_rem + 1) * 8, s));
+    MCE_TRY(nclaimed.alloc(8, s));
+    MCE_TRY(missing.alloc(4, s));
+    MCE_CUDA(cudaMemsetAsync(nclaimed.p, 0, 8, s));
+    MCE_CUDA(cudaMemsetAsync(missing.p, 0, 4, s));
+    unsigned long long ncl = 0;
+    if (n_rem) {
+        int32_t hm = 0;
+        MCE_LAUNCH(k_index_claim, grid_for(n_rem, 256), 256, 0, s, rloff.as<int64_t>(), rlvtx.as<int32_t>(), n_rem,
+                   S->idx.pool, S->idx.off, S->idx.alive, S->idx.tkey, S->idx.tid, S->idx.tcap - 1, S->seed,
+                   claimed.as<int64_t>(), nclaimed.as<unsigned long long>(), missing.as<int32_t>());
+        MCE_CUDA(cudaMemcpyAsync(&ncl, nclaimed.p, 8, cudaMemcpyDeviceToHost, s));
+        MCE_CUDA(cudaMemcpyAsync(&hm, missing.p, 4, cudaMemcpyDeviceToHost, s));
+        MCE_CUDA(cudaStreamSynchronize(s));
+        if (hm) {
+            if (ncl) MCE_LAUNCH(k_restore_alive, grid_for((int64_t)ncl, 256), 256, 0, s, claimed.as<int64_t>(),
+                                (int64_t)ncl, S->idx.alive);
+            MCE_CUDA(cudaStreamSynchronize(s));
+            g_last_error = "imce_remove_edges: a removed clique is not in the index";
+            return MCE_ESTATE;
+        }
+    }
+    mce_status st = MCE_OK;
+    if (n_cre) st = index_append(S->idx, cloff.as<int64_t>(), clvtx.as<int32_t>(), n_cre, s, S->seed);
+    if (st != MCE_OK) {
+        if (ncl) MCE_LAUNCH(k_restore_alive, grid_for((int64_t)ncl, 256), 256, 0, s, claimed.as<int64_t>(),
+                            (int64_t)ncl, S->idx.alive);
+        return st;
+    }
+    S->idx.n_alive -= (int64_t)ncl;
+    cudaFreeAsync(g->row_ptr, s);
+    cudaFreeAsync(g->col, s);
+    delete g;
+    S->g = gm.g;
+    gm.g = nullptr;
+    MCE_CUDA(cudaEventRecord(ev.b, s));
+    MCE_CUDA(cudaEventSynchronize(ev.b));
+    cudaEventElapsedTime(&out->ms, ev.a, ev.b);
+    out->new_count = hc[OUT_COUNT];
+    out->new_hash = hc[OUT_HASH];
+    fill_hist(hc, &out->new_hist_len, out->new_hist);
+    out->sub_count = hr[OUT_COUNT];
+    out->sub_hash = hr[OUT_HASH];
+    fill_hist(hr, &out->sub_hist_len, out->sub_hist);
     out->alive = (uint64_t)S->idx.n_alive;
     return MCE_OK;
 }
@@ -939,6 +1508,29 @@ mce_status imce_add_edges(imce_state *S, const int32_t *u, const int32_t *v, int
         pv = dv.as<int32_t>();
     }
     return add_edges(S, pu, pv, k, out);
+}
+
+mce_status imce_remove_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t k, int32_t on_device,
+                             imce_delta *out) {
+    if (!S || !out || k < 0 || (k > 0 && (!u || !v))) {
+        g_last_error = "imce_remove_edges: bad arguments";
+        return MCE_EINVAL;
+    }
+    if (k >= (int64_t)1 << 30) {
+        g_last_error = "imce_remove_edges: batch too large";
+        return MCE_EINVAL;
+    }
+    DevBuf du, dv;
+    const int32_t *pu = u, *pv = v;
+    if (!on_device && k > 0) {
+        MCE_TRY(du.alloc((size_t)k * 4, S->s));
+        MCE_TRY(dv.alloc((size_t)k * 4, S->s));
+        MCE_CUDA(cudaMemcpyAsync(du.p, u, (size_t)k * 4, cudaMemcpyHostToDevice, S->s));
+        MCE_CUDA(cudaMemcpyAsync(dv.p, v, (size_t)k * 4, cudaMemcpyHostToDevice, S->s));
+        pu = du.as<int32_t>();
+        pv = dv.as<int32_t>();
+    }
+    return remove_edges(S, pu, pv, k, out);
 }
 
 const mce_graph *imce_graph(const imce_state *S) { return S ? S->g : nullptr; }

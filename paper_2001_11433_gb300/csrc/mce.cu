@@ -183,16 +183,39 @@ LaunchShape launch_shape(const mce_opts *o) {
     if (!o || o->shared_words <= 0) words = 0;
     else if (o->shared_words < words) words = o->shared_words & ~3;
     ls.smem_words = (int32_t)words;
+    // what is left of the block's shared memory goes to the lane-parallel small
+    // search (up to 16 KB a warp; below 2 KB a warp it stays off)
+    if (!o || !o->warp_small_search) {
+        int64_t lp = (per_block - 2048) / 4 / ls.warps_per_block - BK_PIV_WORDS - ls.smem_words;
+        if (lp > 4096) lp = 4096;
+        lp &= ~int64_t(1);
+        ls.lp_words = lp >= 512 ? (int32_t)lp : 0;
+    }
     // the ring's sequence numbers tell "published for ticket p" (p + 1) from
     // "free for ticket p + cap" (p + cap) only when cap >= 2
     ls.queue_capacity = (o && o->queue_capacity > 0) ? (o->queue_capacity < 2 ? 2 : o->queue_capacity) : 0;
     return ls;
 }
 
+mce_status alloc_lp_tasks(BkParams &P, int64_t nwarps, cudaStream_t s, BkBuffers &b) {
+    if (P.mode != BK_MCE || P.lp_words == 0) {
+        P.lp_words = 0;
+        P.lp_tasks = nullptr;
+        P.lp_task_cap = 0;
+        return MCE_OK;
+    }
+    P.lp_task_cap = BK_LP_TASK_CAP;
+    MCE_TRY(b.lp_tasks.alloc((size_t)nwarps * 2 * BK_LP_TASK_CAP * BK_LP_TASK_WORDS * 4, s));
+    P.lp_tasks = b.lp_tasks.as<uint32_t>();
+    return MCE_OK;
+}
+
 mce_status run_bk(BkParams &P, const LaunchShape &ls, int64_t req_max, int64_t cmax, cudaStream_t s, BkBuffers &b) {
     const int64_t nwarps = (int64_t)num_sms() * ls.blocks_per_sm * ls.warps_per_block;
     P.gws_words = req_max > ls.smem_words ? req_max : 16;
     P.smem_words = ls.smem_words;
+    P.lp_words = ls.lp_words;
+    MCE_TRY(alloc_lp_tasks(P, nwarps, s, b));
     MCE_TRY(b.gws.alloc((size_t)nwarps * P.gws_words * 4, s));
     P.gws = b.gws.as<uint32_t>();
     // one ring slot holds (root, depth, path <= c, cand, finic, ext, conf)

@@ -10,12 +10,15 @@ struct LaunchShape {
     int32_t blocks_per_sm = 4;
     int32_t smem_words = 0;
     int32_t queue_capacity = 0;   // task ring slots (0 = automatic)
+    int32_t lp_words = 0;         // per-warp shared words of the lane-parallel small search (0 = off)
 };
 
 LaunchShape launch_shape(const mce_opts *o);
 struct BkBuffers {
-    DevBuf gws, arena, qseq, taskbuf, ctl;
+    DevBuf gws, arena, qseq, taskbuf, ctl, lp_tasks;
 };
+// task lists of the lane-parallel small search (static MCE only)
+mce_status alloc_lp_tasks(BkParams &P, int64_t nwarps, cudaStream_t s, BkBuffers &b);
 mce_status run_bk(BkParams &P, const LaunchShape &ls, int64_t req_max, int64_t cmax, cudaStream_t s, BkBuffers &b);
 mce_status compute_rank(const mce_graph *g, const mce_opts *o, cudaStream_t s, int32_t *rank);
 mce_status read_result(const DevBuf &out, const DevBuf &ctl, cudaStream_t s, mce_result *res);
