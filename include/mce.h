@@ -127,6 +127,17 @@ typedef struct {
      * small subtree per lane, 32 at a time (static MCE without clique lists).
      * Both give the same trees, node counts and cliques. */
     int32_t warp_small_search;
+    /* 1 = ParTTT (Algorithm 3) on the whole graph from K = ∅, cand = V, fini =
+     * ∅, instead of the per-vertex decomposition: the root's pivot is a vertex
+     * p of largest degree (smallest id), its children are the vertices of
+     * ext = V \ Γ(p) in increasing id, and each child's subtree is searched
+     * (and split across warps) as a subproblem.  tree_nodes counts the root
+     * too and equals Algorithm 1's count on the whole graph.  rank_kind,
+     * user_rank and subset are ignored. */
+    int32_t whole_graph;
+    /* Streaming multiprocessors the search launch covers (0 = all), for
+     * scaling measurements; the result does not depend on it. */
+    int32_t sm_limit;
 } mce_opts;
 
 typedef struct {

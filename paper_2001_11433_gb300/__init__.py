@@ -60,6 +60,8 @@ class Opts(ctypes.Structure):
         ("subproblem_budget", ctypes.c_uint64),
         ("queue_capacity", ctypes.c_int32),
         ("warp_small_search", ctypes.c_int32),
+        ("whole_graph", ctypes.c_int32),
+        ("sm_limit", ctypes.c_int32),
     ]
 
 
@@ -362,7 +364,7 @@ class Graph:
 def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, stream=None, list_buf=None,
               per_vertex=None, split=True, order_by_model=False, warps_per_block=0, blocks_per_sm=0,
               time_limit_ms=0, subset=None, subproblem_budget=0, shared_words=0, split_nodes=0,
-              queue_capacity=0, warp_small_search=False) -> Opts:
+              queue_capacity=0, warp_small_search=False, whole_graph=False, sm_limit=0) -> Opts:
     o = Opts()
     load().mce_opts_init(ctypes.byref(o))
     o.rank_kind = RANKS[rank] if isinstance(rank, str) else int(rank)
@@ -390,6 +392,8 @@ def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, s
     o.subproblem_budget = subproblem_budget
     o.queue_capacity = queue_capacity
     o.warp_small_search = int(warp_small_search)
+    o.whole_graph = int(whole_graph)
+    o.sm_limit = sm_limit
     return o
 
 

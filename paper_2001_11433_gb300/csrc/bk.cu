@@ -2371,10 +2371,28 @@ mce_status bk_prepare(int32_t blocks_per_sm, int64_t smem_bytes) {
     return MCE_OK;
 }
 
-mce_status launch_bk(const BkParams &p, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s) {
-    const size_t smem = (size_t)bk_block_smem_bytes(warps_per_block, p.smem_words, p.lp_words);
-    const unsigned blocks = (unsigned)(num_sms() * blocks_per_sm);
-    MCE_TRY(bk_prepare(blocks_per_sm, (int64_t)smem));
+namespace {
+int resident_blocks(int32_t blocks_per_sm, int32_t threads, size_t smem) {
+    int active = 0;
+    if (blocks_per_sm >= 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&active, k_bk<4>, threads, smem);
+    else if (blocks_per_sm == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&active, k_bk<3>, threads, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&active, k_bk<2>, threads, smem);
+    return active;
+}
+}  // namespace
+
+mce_status launch_bk(const BkParams &p0, int32_t warps_per_block, int32_t blocks_per_sm, cudaStream_t s) {
+    // a persistent grid must be resident at once: shrink the lane-parallel
+    // regions until blocks_per_sm blocks fit on an SM
+    BkParams p = p0;
+    size_t smem = (size_t)bk_block_smem_bytes(warps_per_block, p.smem_words, p.lp_words);
+    MCE_TRY(bk_prepare(blocks_per_sm, (int64_t)smem));   // the grant covers every smaller size below
+    while (p.lp_words > 0 && resident_blocks(blocks_per_sm, warps_per_block * 32, smem) < blocks_per_sm) {
+        p.lp_words = p.lp_words - 128 >= 512 ? p.lp_words - 128 : 0;
+        smem = (size_t)bk_block_smem_bytes(warps_per_block, p.smem_words, p.lp_words);
+    }
+    const int32_t sms = (p.sm_limit > 0 && p.sm_limit < num_sms()) ? p.sm_limit : num_sms();
+    const unsigned blocks = (unsigned)(sms * blocks_per_sm);
     // 4 resident blocks of 256 threads leave 64 registers a thread; fewer
     // blocks let the compiler keep the search state in more registers
     if (blocks_per_sm >= 4) MCE_LAUNCH(k_bk<4>, blocks, warps_per_block * 32, smem, s, p);

@@ -101,6 +101,7 @@ struct BkParams {
     int32_t lp_words;         // per-warp shared words of the lane-parallel small search (0 = off)
     uint32_t *lp_tasks;       // per warp: two lists of lp_task_cap node records (BK_LP_TASK_WORDS each)
     int32_t lp_task_cap;
+    int32_t sm_limit;         // SMs the persistent grid covers (0 = all)
 };
 
 // Words of the read-only part of a built subproblem with w local vertices of

@@ -447,14 +447,16 @@ __global__ void __launch_bounds__(256) k_imce_sub(SubParams P) {
                                 }
                             }
                         }
-                        if (eq) {
+                        // the index keeps dead entries: a clique that died and was
+                        // created again (after an edge deletion) has a later alive copy
+                        if (eq && atomicCAS(&P.alive[id1 - 1], 1, 0) == 1) {
                             found = id1 - 1;
                             break;
                         }
                     }
                     slot = (slot + 1) & P.tmask;
                 }
-                if (found >= 0 && atomicCAS(&P.alive[found], 1, 0) == 1) {
+                if (found >= 0) {
                     const unsigned long long k = atomicAdd(P.n_claimed, 1ULL);
                     if ((int64_t)k < P.claimed_cap) P.claimed[k] = found;
                     atomicAdd(&P.out[OUT_COUNT], 1ULL);

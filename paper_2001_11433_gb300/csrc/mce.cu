@@ -134,6 +134,39 @@ __global__ void k_order_from_keys(const uint64_t *keys, int32_t m, int32_t idb, 
 
 __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
 
+// Whole-graph TTT (Algorithm 3 from K = ∅, cand = V): the root's pivot is a
+// vertex of largest degree (|V ∩ Γ(u)| = deg u), smallest id among ties.
+__global__ void k_whole_pivot(const int32_t *row_ptr, int32_t n, unsigned long long *best) {
+    unsigned long long b = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = ((unsigned long long)(row_ptr[v + 1] - row_ptr[v]) << 32) |
+                                     (unsigned long long)(0x7fffffffu - (uint32_t)v);
+        b = max(b, k);
+    }
+    for (int o = 16; o; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(best, b);
+}
+
+// key(v) = 1 for the neighbours of the pivot, else 0 (the root's ext, which
+// holds the pivot itself); in_ext[v] = 1 - key(v).  k_whole_init, then
+// k_whole_mark over the pivot's row.
+__global__ void k_whole_init(int32_t n, int64_t *key, uint8_t *in_ext) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        key[v] = 0;
+        in_ext[v] = 1;
+    }
+}
+
+__global__ void k_whole_mark(const int32_t *row_ptr, const int32_t *col, const unsigned long long *best, int64_t *key,
+                             uint8_t *in_ext) {
+    const int32_t p = (int32_t)(0x7fffffffu - (uint32_t)(*best & 0xffffffffULL));
+    for (int32_t e = row_ptr[p] + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); e < row_ptr[p + 1];
+         e += (int32_t)(gridDim.x * blockDim.x)) {
+        key[col[e]] = 1;
+        in_ext[col[e]] = 0;
+    }
+}
+
 struct EvPair {
     cudaEvent_t a, b;
     ~EvPair() {
@@ -173,8 +206,9 @@ LaunchShape launch_shape(const mce_opts *o) {
     // are the robust choice (Chung-Lu, incremental, sampled R-MAT sets); three
     // (80 registers) win about 10 % on the full R-MAT 18 set only
     ls.blocks_per_sm = (o && o->blocks_per_sm > 0) ? o->blocks_per_sm : 2;
-    // shared memory per SM is 228 KB with 1 KB reserved per block
-    const int64_t per_block = (int64_t)228 * 1024 / ls.blocks_per_sm - 1024;
+    // shared memory per SM is 228 KB with 1 KB reserved per block; the search
+    // kernel also has about 1 KB of static shared memory
+    const int64_t per_block = (int64_t)228 * 1024 / ls.blocks_per_sm - 2048;
     int64_t words = (per_block - 2048) / 4 / ls.warps_per_block - BK_PIV_WORDS;
     words &= ~int64_t(3);
     if (words < 0) words = 0;
@@ -340,9 +374,30 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         }
     } evg{e0, e1, e2};
     MCE_CUDA(cudaEventRecord(e0, s));
-    DevBuf rank, out, up_ptr, up_col, flag, keys, tmp, order, cost;
+    DevBuf rank, out, up_ptr, up_col, flag, keys, tmp, order, cost, wmask;
     MCE_TRY(rank.alloc((size_t)(n + 1) * 4, s));
-    MCE_TRY(compute_rank(g, o, s, rank.as<int32_t>()));
+    if (o->whole_graph) {
+        // Algorithm 3 from K = ∅, cand = V: the root (pivot p of largest degree)
+        // has the children q ∈ ext = V \ Γ(p), in increasing id; child q is
+        // TTT({q}, Γ(q) minus the earlier ext vertices, Γ(q) ∩ earlier ext),
+        // which is the subproblem of q (Algorithm 5) under the rank that puts
+        // ext first (by id) and Γ(p) after it (by id).  Every maximal clique
+        // has a vertex in ext (else p would extend it).
+        if (n > 0) {
+            DevBuf best, wkey;
+            MCE_TRY(best.alloc(8, s));
+            MCE_TRY(wkey.alloc((size_t)n * 8, s));
+            MCE_TRY(wmask.alloc((size_t)n + 16, s));
+            MCE_CUDA(cudaMemsetAsync(best.p, 0, 8, s));
+            MCE_LAUNCH(k_whole_pivot, grid_for(n, 256), 256, 0, s, g->row_ptr, n, best.as<unsigned long long>());
+            MCE_LAUNCH(k_whole_init, grid_for(n, 256), 256, 0, s, n, wkey.as<int64_t>(), wmask.as<uint8_t>());
+            MCE_LAUNCH(k_whole_mark, 64, 256, 0, s, g->row_ptr, g->col, best.as<unsigned long long>(),
+                       wkey.as<int64_t>(), wmask.as<uint8_t>());
+            MCE_TRY(rank_from_key_i64(wkey.as<int64_t>(), n, g->id_bits, s, rank.as<int32_t>()));
+        }
+    } else {
+        MCE_TRY(compute_rank(g, o, s, rank.as<int32_t>()));
+    }
     MCE_CUDA(cudaEventRecord(e1, s));
     int64_t up_nnz = 0;
     MCE_TRY(build_up_lists(g, rank.as<int32_t>(), s, up_ptr, up_col, &up_nnz));
@@ -370,7 +425,9 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         MCE_CUDA(cudaMemcpyAsync(hsub.p, o->subset, (size_t)o->subset_len * 4, cudaMemcpyHostToDevice, s));
         subp = hsub.as<int32_t>();
     }
-    if (o->subset) {
+    if (o->whole_graph) {
+        maskp = wmask.as<uint8_t>();
+    } else if (o->subset) {
         DevBuf bad;
         MCE_TRY(bad.alloc(4, s));
         MCE_TRY(mask.alloc((size_t)n + 16, s));
@@ -447,6 +504,7 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         }
         P.split = o->split;
         P.split_nodes = o->split ? (o->split_nodes ? o->split_nodes : 4096u) : 0u;
+        P.sm_limit = o->sm_limit;
         P.max_run_ns = (uint64_t)o->time_limit_ms * 1000000ULL;
         // build cache for every subproblem (up to 2^30 words); when it holds them
         // all, a warp's own workspace only needs the private search state
@@ -491,6 +549,7 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         res->incomplete = (int64_t)hc;
     }
     mce_status st = read_result(out, bb.ctl, s, res);
+    if (o->whole_graph && n > 0) res->tree_nodes += 1;   // the root node of the whole-graph tree
     float a = 0, b = 0;
     cudaEventElapsedTime(&a, e0, e1);
     cudaEventElapsedTime(&b, e1, e2);

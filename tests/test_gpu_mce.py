@@ -349,3 +349,48 @@ def test_graph_from_csr_round_trip_and_validation(gpu_lib):
         with pytest.raises(mce.MceError) as e:
             mce.Graph.from_csr(rp, cl)
         assert e.value.status == mce.MCE_EINVAL and what in str(e.value), what
+
+
+# ---------------------------------------------------------------- whole-graph ParTTT (Algorithm 3)
+
+@pytest.mark.parametrize("case", ["complete", "empty", "star", "cycle", "moon_moser", "traced", "er", "rmat12"])
+def test_whole_graph_tree_equals_oracle(gpu_lib, case):
+    """Algorithm 3 from K = ∅, cand = V on the GPU: the clique set and the
+    search-tree node count equal the oracle's whole-graph TTT (pinned by the
+    hand-derived closed forms and the traced example), with splitting on."""
+    import json
+    mce = gpu_lib
+    if case == "complete":
+        n = 30
+        pairs = [(i, j) for i in range(n) for j in range(i + 1, n)]
+    elif case == "empty":
+        n, pairs = 9, []
+    elif case == "star":
+        n, pairs = 12, [(0, i) for i in range(1, 12)]
+    elif case == "cycle":
+        n = 21
+        pairs = [(i, (i + 1) % n) for i in range(n)]
+    elif case == "moon_moser":
+        k = 6
+        parts = [list(range(3 * i, 3 * i + 3)) for i in range(k)]
+        n = 3 * k
+        pairs = [(a, b) for i in range(k) for j in range(i + 1, k) for a in parts[i] for b in parts[j]]
+    elif case == "traced":
+        with open(os.path.join(GOLDEN, "ttt_tree_trace.json")) as f:
+            d = json.load(f)
+        n, pairs = d["n"], [tuple(e) for e in d["edges"]]
+    elif case == "er":
+        n = 400
+        u, v = graphgen.er(n, 0.05, 12)
+        pairs = list(zip(u.tolist(), v.tolist()))
+    else:
+        n, u, v = rmat(12)
+        pairs = list(zip(u.tolist(), v.tolist()))
+    u = np.array([a for a, b in pairs], np.int32)
+    v = np.array([b for a, b in pairs], np.int32)
+    og = O.Graph(n, u, v)
+    ref = O.ttt_whole(og)
+    g = gpu_graph(mce, n, u, v)
+    for split_nodes in (0, 64):
+        r = mce.enumerate_cliques(g, whole_graph=True, split_nodes=split_nodes)
+        assert (r.count, r.hash, list(r.hist), r.tree_nodes) == (ref.count, ref.hash, list(ref.hist), ref.nodes)
