@@ -138,6 +138,10 @@ typedef struct {
     /* Streaming multiprocessors the search launch covers (0 = all), for
      * scaling measurements; the result does not depend on it. */
     int32_t sm_limit;
+    /* Per-warp shared-memory words of the lane-parallel small search (0 =
+     * automatic; values below 512 turn it off).  Shared memory comes out of
+     * the SM's L1, which also caches the per-lane search stacks. */
+    int32_t lane_search_words;
 } mce_opts;
 
 typedef struct {
@@ -232,16 +236,28 @@ mce_status mce_enumerate(const mce_graph *g, const mce_opts *opts, mce_result *r
 
 /* ---------------------------------------------------------------- learned cost model */
 
-/* Per-vertex features, device float[n*8], row-major:
+/* Per-vertex features, device float[n*8], row-major (MCE_FEATURES_FULL):
  *   0 log1p(degree)              1 core number
  *   2 log1p(triangles)           3 mean log1p(neighbour degree)
  *   4 std log1p(neighbour degree) 5 max log1p(neighbour degree)
  *   6 log1p(#higher-degree-rank neighbours)  7 local clustering 2t/(d(d-1)) */
 mce_status mce_features(const mce_graph *g, void *stream, float *feat);
+/* Feature sets: MCE_FEATURES_FULL as above (needs core numbers and triangle
+ * counts); MCE_FEATURES_LIGHT from one pass over the CSR (degrees only):
+ *   0 log1p(d)   1/2/3 mean / std / max log1p(neighbour degree)
+ *   4 log1p(#higher-degree-rank neighbours)
+ *   5 log1p(sum over neighbours w of min(d, d(w)) / 2)  (a triangle bound)
+ *   6 fraction of higher-degree-rank neighbours   7 log1p(sum of neighbour degrees) */
+#define MCE_FEATURES_FULL 0
+#define MCE_FEATURES_LIGHT 1
+mce_status mce_features_kind(const mce_graph *g, int32_t kind, void *stream, float *feat);
 
 /* MLP 8 -> hidden -> hidden -> 1, ReLU, weights initialised from `seed`. */
 mce_status mce_model_create(int32_t hidden, uint64_t seed, mce_model **m);
 void mce_model_free(mce_model *m);
+/* Feature set (MCE_FEATURES_*) the model reads when it ranks or orders
+ * subproblems (default MCE_FEATURES_FULL). */
+mce_status mce_model_set_features(mce_model *m, int32_t kind);
 /* Weights as host float arrays in the order W1[h*8], b1[h], W2[h*h], b2[h],
  * w3[h], b3[1] (row-major, y = W x + b); n_params = 8h + h + h*h + h + h + 1. */
 int64_t mce_model_num_params(const mce_model *m);

@@ -99,3 +99,34 @@ def features(g: Graph) -> np.ndarray:
     with np.errstate(divide="ignore", invalid="ignore"):
         F[:, 7] = np.where(d >= 2, 2.0 * tri / (d * (d - 1)), 0.0)
     return F
+
+
+def features_light(g: Graph) -> np.ndarray:
+    """One-pass per-vertex features [n, 8] (no core numbers, no triangles):
+    0 log1p(degree d),
+    1/2/3 mean / standard deviation / max of log1p(neighbour degree),
+    4 log1p(number of neighbours of higher degree rank),
+    5 log1p(sum over neighbours w of min(d, d(w)) / 2), a bound on the
+      triangles through the vertex,
+    6 fraction of neighbours of higher degree rank (0 without neighbours),
+    7 log1p(sum of the neighbours' degrees)."""
+    n = g.n
+    rp, col = g.csr()
+    d = degree(g).astype(np.float64)
+    drank = rank(g, "degree")
+    F = np.zeros((n, N_FEAT), dtype=np.float64)
+    F[:, 0] = np.log1p(d)
+    ld = np.log1p(d)
+    for v in range(n):
+        nb = col[rp[v]:rp[v + 1]]
+        if len(nb):
+            x = ld[nb]
+            hi = np.count_nonzero(drank[nb] > drank[v])
+            F[v, 1] = x.mean()
+            F[v, 2] = np.sqrt(max((x * x).mean() - x.mean() ** 2, 0.0))
+            F[v, 3] = x.max()
+            F[v, 4] = np.log1p(hi)
+            F[v, 5] = np.log1p(np.minimum(d[nb], d[v]).sum() / 2.0)
+            F[v, 6] = hi / len(nb)
+            F[v, 7] = np.log1p(d[nb].sum())
+    return F

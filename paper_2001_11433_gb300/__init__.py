@@ -62,6 +62,7 @@ class Opts(ctypes.Structure):
         ("warp_small_search", ctypes.c_int32),
         ("whole_graph", ctypes.c_int32),
         ("sm_limit", ctypes.c_int32),
+        ("lane_search_words", ctypes.c_int32),
     ]
 
 
@@ -170,6 +171,8 @@ SIGNATURES = {
     "mce_rank": ([_vp, _P(Opts), _vp], _i32),
     "mce_enumerate": ([_vp, _P(Opts), _P(ResultC)], _i32),
     "mce_features": ([_vp, _vp, _vp], _i32),
+    "mce_features_kind": ([_vp, _i32, _vp, _vp], _i32),
+    "mce_model_set_features": ([_vp, _i32], _i32),
     "mce_model_create": ([_i32, _u64, _P(_vp)], _i32),
     "mce_model_free": ([_vp], None),
     "mce_model_num_params": ([_vp], _i64),
@@ -364,7 +367,8 @@ class Graph:
 def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, stream=None, list_buf=None,
               per_vertex=None, split=True, order_by_model=False, warps_per_block=0, blocks_per_sm=0,
               time_limit_ms=0, subset=None, subproblem_budget=0, shared_words=0, split_nodes=0,
-              queue_capacity=0, warp_small_search=False, whole_graph=False, sm_limit=0) -> Opts:
+              queue_capacity=0, warp_small_search=False, whole_graph=False, sm_limit=0,
+              lane_search_words=0) -> Opts:
     o = Opts()
     load().mce_opts_init(ctypes.byref(o))
     o.rank_kind = RANKS[rank] if isinstance(rank, str) else int(rank)
@@ -394,6 +398,7 @@ def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, s
     o.warp_small_search = int(warp_small_search)
     o.whole_graph = int(whole_graph)
     o.sm_limit = sm_limit
+    o.lane_search_words = lane_search_words
     return o
 
 
@@ -448,10 +453,13 @@ def rank(g: Graph, **kw):
     return out[: g.n]
 
 
-def features(g: Graph, stream=None):
+FEATURES = {"full": 0, "light": 1}
+
+
+def features(g: Graph, stream=None, kind="full"):
     import torch
     f = torch.empty((max(g.n, 1), 8), dtype=torch.float32, device="cuda")
-    _check(load().mce_features(g._h, _stream_ptr(stream), _ptr(f)), "mce_features")
+    _check(load().mce_features_kind(g._h, FEATURES[kind], _stream_ptr(stream), _ptr(f)), "mce_features_kind")
     return f[: g.n]
 
 
@@ -469,10 +477,12 @@ def decode_list(off, vtx, n_cliques):
 class Model:
     """MLP cost model (mce_model_*)."""
 
-    def __init__(self, hidden: int = 64, seed: int = 0):
+    def __init__(self, hidden: int = 64, seed: int = 0, features: str = "full"):
         h = ctypes.c_void_p()
         _check(load().mce_model_create(hidden, seed, ctypes.byref(h)), "mce_model_create")
         self._h, self.hidden = h, hidden
+        _check(load().mce_model_set_features(h, FEATURES[features]), "mce_model_set_features")
+        self.features = features
 
     def close(self):
         if getattr(self, "_h", None):

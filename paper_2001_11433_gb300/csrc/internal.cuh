@@ -132,7 +132,8 @@ mce_status rank_from_key_f32(const float *key, int32_t n, int32_t id_bits, cudaS
 mce_status build_up_lists(const mce_graph *g, const int32_t *rank, cudaStream_t s, DevBuf &up_ptr, DevBuf &up_col,
                           int64_t *up_nnz);
 // Features (mce_features).
-mce_status features(const mce_graph *g, cudaStream_t s, float *feat);
+mce_status features(const mce_graph *g, int32_t kind, cudaStream_t s, float *feat);
+int32_t model_feature_kind(const mce_model *m);
 
 // ------------------------------------------------------------------ device helpers
 

@@ -222,6 +222,7 @@ LaunchShape launch_shape(const mce_opts *o) {
     if (!o || !o->warp_small_search) {
         int64_t lp = (per_block - 2048) / 4 / ls.warps_per_block - BK_PIV_WORDS - ls.smem_words;
         if (lp > 4096) lp = 4096;
+        if (o && o->lane_search_words > 0 && o->lane_search_words < lp) lp = o->lane_search_words;
         lp &= ~int64_t(1);
         ls.lp_words = lp >= 512 ? (int32_t)lp : 0;
     }
@@ -295,7 +296,7 @@ mce_status compute_rank(const mce_graph *g, const mce_opts *o, cudaStream_t s, i
             DevBuf feat, score;
             MCE_TRY(feat.alloc((size_t)n * 8 * 4, s));
             MCE_TRY(score.alloc((size_t)n * 4, s));
-            MCE_TRY(features(g, s, feat.as<float>()));
+            MCE_TRY(features(g, model_feature_kind(o->model), s, feat.as<float>()));
             MCE_TRY(model_predict(o->model, feat.as<float>(), n, 1, s, score.as<float>()));
             return rank_from_key_f32(score.as<float>(), n, g->id_bits, s, rank);
         }
@@ -406,7 +407,7 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         DevBuf feat;
         MCE_TRY(feat.alloc((size_t)n * 8 * 4 + 16, s));
         MCE_TRY(cost.alloc((size_t)n * 4 + 16, s));
-        MCE_TRY(features(g, s, feat.as<float>()));
+        MCE_TRY(features(g, model_feature_kind(o->model), s, feat.as<float>()));
         MCE_TRY(model_predict(o->model, feat.as<float>(), n, 1, s, cost.as<float>()));
         costp = cost.as<float>();
     }

@@ -21,6 +21,7 @@
 
 struct mce_model {
     int32_t H = 64;
+    int32_t feature_kind = 0;   // MCE_FEATURES_* the model reads
     int64_t np = 0;
     float *w = nullptr;       // parameters, device
     float *m = nullptr;       // Adam first moment
@@ -88,6 +89,53 @@ __global__ void k_features(const int32_t *__restrict__ row_ptr, const int32_t *_
             f[5] = mx;
             f[6] = log1pf((float)(up_ptr[v + 1] - up_ptr[v]));
             f[7] = d >= 2 ? (float)(2.0 * (double)tri[v] / ((double)d * (d - 1))) : 0.f;
+        }
+    }
+}
+
+// One-pass features (MCE_FEATURES_LIGHT): degrees of the vertex and its
+// neighbours only.  A neighbour w ranks higher than v by degree when
+// (d(w), w) > (d(v), v).
+__global__ void k_features_light(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
+                                 float *feat) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        const int32_t e0 = row_ptr[v], e1 = row_ptr[v + 1], d = e1 - e0;
+        float s = 0.f, s2 = 0.f, mx = 0.f, mins = 0.f, dsum = 0.f;
+        int hi = 0;
+        for (int32_t e = e0 + lane; e < e1; e += 32) {
+            const int32_t w = col[e];
+            const int32_t dw = row_ptr[w + 1] - row_ptr[w];
+            const float x = log1pf((float)dw);
+            s += x;
+            s2 += x * x;
+            mx = fmaxf(mx, x);
+            mins += (float)min(dw, d);
+            dsum += (float)dw;
+            hi += (dw > d || (dw == d && w > (int32_t)v)) ? 1 : 0;
+        }
+        for (int o = 16; o; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            mins += __shfl_xor_sync(0xffffffffu, mins, o);
+            dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+            hi += __shfl_xor_sync(0xffffffffu, hi, o);
+        }
+        if (lane == 0) {
+            float *f = feat + v * kFeat;
+            const float mean = d ? s / d : 0.f;
+            const float var = d ? fmaxf(s2 / d - mean * mean, 0.f) : 0.f;
+            f[0] = log1pf((float)d);
+            f[1] = mean;
+            f[2] = sqrtf(var);
+            f[3] = mx;
+            f[4] = log1pf((float)hi);
+            f[5] = log1pf(mins * 0.5f);
+            f[6] = d ? (float)hi / (float)d : 0.f;
+            f[7] = log1pf(dsum);
         }
     }
 }
@@ -264,9 +312,15 @@ size_t grad_smem(int H) {
 
 }  // namespace
 
-mce_status features(const mce_graph *g, cudaStream_t s, float *feat) {
+int32_t model_feature_kind(const mce_model *m) { return m ? m->feature_kind : 0; }
+
+mce_status features(const mce_graph *g, int32_t kind, cudaStream_t s, float *feat) {
     const int32_t n = g->n;
     if (n == 0) return MCE_OK;
+    if (kind == MCE_FEATURES_LIGHT) {
+        MCE_LAUNCH(k_features_light, grid_for((int64_t)n * 32, 256), 256, 0, s, g->row_ptr, g->col, n, feat);
+        return MCE_OK;
+    }
     DevBuf core, tri, deg, drank, up_ptr, up_col;
     MCE_TRY(core.alloc((size_t)n * 8, s));
     MCE_TRY(tri.alloc((size_t)n * 8, s));
@@ -313,10 +367,26 @@ using namespace mce;
 extern "C" {
 
 mce_status mce_features(const mce_graph *g, void *stream, float *feat) {
-    if (!g || !feat) return MCE_EINVAL;
+    return mce_features_kind(g, MCE_FEATURES_FULL, stream, feat);
+}
+
+mce_status mce_features_kind(const mce_graph *g, int32_t kind, void *stream, float *feat) {
+    if (!g || !feat || (kind != MCE_FEATURES_FULL && kind != MCE_FEATURES_LIGHT)) {
+        g_last_error = "mce_features_kind: bad arguments";
+        return MCE_EINVAL;
+    }
     cudaStream_t s = (cudaStream_t)stream;
-    MCE_TRY(features(g, s, feat));
+    MCE_TRY(features(g, kind, s, feat));
     MCE_CUDA(cudaStreamSynchronize(s));
+    return MCE_OK;
+}
+
+mce_status mce_model_set_features(mce_model *m, int32_t kind) {
+    if (!m || (kind != MCE_FEATURES_FULL && kind != MCE_FEATURES_LIGHT)) {
+        g_last_error = "mce_model_set_features: bad arguments";
+        return MCE_EINVAL;
+    }
+    m->feature_kind = kind;
     return MCE_OK;
 }
 

@@ -45,6 +45,20 @@ def test_features_match_reference(gpu_lib, case):
     assert np.allclose(F, R, rtol=1e-4, atol=2e-3)
 
 
+@pytest.mark.parametrize("case", ["er2000", "rmat12"])
+def test_light_features_match_reference(gpu_lib, case):
+    """The one-pass feature set (degrees only) against its float64 restatement."""
+    mce = gpu_lib
+    if case == "er2000":
+        w = graphgen.er_2000()
+        n, u, v = w.n, w.u, w.v
+    else:
+        n, u, v = rmat(12)
+    F = mce.features(mce.Graph(n, _t(u), _t(v)), kind="light").cpu().numpy()
+    R = mlp.features_light(O.Graph(n, u, v))
+    assert np.allclose(F, R, rtol=1e-4, atol=2e-3)
+
+
 def test_loss_and_gradient_match_reference(gpu_lib):
     """FP32 GPU gradient within 1e-4 of the float64 reference (relative to the
     largest gradient component)."""

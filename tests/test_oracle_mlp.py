@@ -56,3 +56,21 @@ def test_features_er_shapes():
     F = mlp.features(g)
     assert F.shape == (200, 8) and np.isfinite(F).all()
     assert (F[:, 7] >= 0).all() and (F[:, 7] <= 1).all()
+
+
+def test_light_features_closed_forms():
+    """One-pass features on a star K_{1,4} (centre 0) and a triangle."""
+    import oracle as O
+    from oracle import mlp
+    g = O.Graph(5, np.zeros(4, np.int32), np.arange(1, 5, dtype=np.int32))
+    F = mlp.features_light(g)
+    # centre: d = 4, every neighbour has degree 1 (lower degree rank)
+    assert np.allclose(F[0], [np.log1p(4), np.log1p(1), 0, np.log1p(1), 0, np.log1p(4 * 1 / 2), 0, np.log1p(4)])
+    # leaf: d = 1, its one neighbour has degree 4 (higher)
+    assert np.allclose(F[1], [np.log1p(1), np.log1p(4), 0, np.log1p(4), np.log1p(1), np.log1p(0.5), 1.0,
+                              np.log1p(4)])
+    t = O.Graph(3, np.array([0, 1, 0], np.int32), np.array([1, 2, 2], np.int32))
+    Ft = mlp.features_light(t)
+    # equal degrees: the higher id ranks higher, so vertex 0 has 2 higher neighbours, vertex 2 none
+    assert np.allclose(Ft[:, 4], np.log1p([2, 1, 0])) and np.allclose(Ft[:, 6], [1.0, 0.5, 0.0])
+    assert np.allclose(Ft[:, 5], np.log1p(2.0))
