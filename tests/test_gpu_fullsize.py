@@ -60,6 +60,39 @@ def test_rmat18_sampled_subproblems(gpu_lib):
     assert r2.incomplete == 0 and r2.complete
 
 
+def test_rmat18_every_subproblem_against_oracle(gpu_lib):
+    """The whole R-MAT 18 benchmark set against the oracle's run of every
+    subproblem (tests/golden/rmat_18_capped.json, written by
+    tests/golden/make_golden.py from oracle.parmce with the 2^24-node cap):
+    the same subproblems pass the cap, and every other subproblem's count,
+    hash and tree nodes agree (SHA-256 of the per-subproblem arrays), as do
+    the totals and the size histogram of the benchmark set."""
+    import hashlib
+    import json
+    import os
+    import torch
+    mce = gpu_lib
+    with open(os.path.join(os.path.dirname(__file__), "golden", "rmat_18_capped.json")) as f:
+        gold = json.load(f)
+    w = graphgen.rmat_18()
+    g = mce.Graph(w.n, _t(w.u), _t(w.v))
+    pv = tuple(torch.zeros(w.n, dtype=torch.int64, device="cuda") for _ in range(3))
+    mce.enumerate_cliques(g, per_vertex=pv, subproblem_budget=TREE_CAP)
+    cnt, hsh, nodes = u64(pv[0]), u64(pv[1]), u64(pv[2])
+    over = nodes > TREE_CAP
+    assert np.nonzero(over)[0].tolist() == gold["capped_vertices"]
+    parts = []
+    for a in (cnt, hsh, nodes):
+        a = a.astype("<u8").copy()
+        a[over] = 0
+        parts.append(a.tobytes())
+    assert hashlib.sha256(b"".join(parts)).hexdigest() == gold["per_vertex_sha256"]
+    keep = np.nonzero(~over)[0].astype(np.int32)
+    r = mce.enumerate_cliques(g, subset=_t(keep), blocks_per_sm=3, split_nodes=4096)
+    assert (r.count, r.hash, r.tree_nodes, list(r.hist)) == \
+        (gold["count"], int(gold["hash"]), gold["tree_nodes"], gold["hist"])
+
+
 def test_chung_lu_planted_full_enumeration(gpu_lib):
     """The whole Chung-Lu graph (1.7M vertices, ~11M edges, 200 planted
     cliques): count, set hash and size histogram equal the oracle's stored
