@@ -643,10 +643,16 @@ def neighbourhood_cost_labels(mce, g, rounds=4, seed=5):
 
 
 def train_learned_model(mce):
-    """MLP 8-64-64-1 trained (FP32, on the GPU, the library's own kernels) on
-    a smaller Chung-Lu graph of the C3 family (n = 200,000, another seed) to
-    predict log(1 + search-tree nodes) of a vertex's whole neighbourhood
-    (neighbourhood_cost_labels).  Returns (model, info)."""
+    """Two MLPs 8-64-64-1 on the one-pass features (degrees only), trained
+    (FP32, on the GPU, the library's own kernels) on a smaller Chung-Lu graph
+    of the C3 family (n = 200,000, another seed):
+      rank model  - log(1 + search-tree nodes) of a vertex's whole
+                    neighbourhood (neighbourhood_cost_labels); its prediction
+                    is the rank key (Section 4.2: costlier ranks higher);
+      split model - log(1 + search-tree nodes) of each subproblem under the
+                    learned rank, recorded by the search itself; it orders the
+                    subproblems and marks the heavy ones for early splitting.
+    Returns (rank model, split model, info)."""
     import torch
     import graphgen
     tu, tv, _ = graphgen.chung_lu(200_000, 2.2, 35_000.0 * (200_000 / 1_700_000) ** 0.5, 200_000 * 6.47,
@@ -654,14 +660,22 @@ def train_learned_model(mce):
     tg = mce.Graph(200_000, torch.from_numpy(tu).cuda(), torch.from_numpy(tv).cuda())
     t0 = time.perf_counter()
     lab_v, lab = neighbourhood_cost_labels(mce, tg, rounds=4, seed=5)
-    feat = mce.features(tg)[torch.from_numpy(lab_v).cuda().long()].contiguous()
-    model = mce.Model(64, seed=3)
-    loss = model.train(feat, torch.from_numpy(lab).cuda(), epochs=60, batch=2048, lr=3e-3, seed=4)
+    feat = mce.features(tg, kind="light")
+    model = mce.Model(64, seed=3, features="light")
+    loss = model.train(feat[torch.from_numpy(lab_v).cuda().long()].contiguous(), torch.from_numpy(lab).cuda(),
+                       epochs=60, batch=2048, lr=3e-3, seed=4)
+    pv = tuple(torch.zeros(200_000, dtype=torch.int64, device="cuda") for _ in range(3))
+    mce.enumerate_cliques(tg, rank="learned", model=model, per_vertex=pv)
+    sub_lab = torch.log1p(pv[2].double()).float()
+    split_model = mce.Model(64, seed=5, features="light")
+    loss2 = split_model.train(feat.contiguous(), sub_lab.contiguous(), epochs=30, batch=4096, lr=3e-3, seed=6)
     train_s = time.perf_counter() - t0
     tg.close()
-    return model, {"graph": "chung-lu n=200000, other seed", "labels": int(len(lab)),
-                   "label": "log1p(tree nodes of the whole neighbourhood)", "epochs": 60, "final_mse": loss,
-                   "seconds": train_s}
+    return model, split_model, {"graph": "chung-lu n=200000, other seed", "features": "one pass (degrees only)",
+                                "rank_labels": int(len(lab)),
+                                "rank_label": "log1p(tree nodes of the whole neighbourhood)", "rank_final_mse": loss,
+                                "split_label": "log1p(tree nodes of the subproblem under the learned rank)",
+                                "split_final_mse": loss2, "seconds": train_s}
 
 
 def balance_stats(r):
@@ -686,10 +700,12 @@ def measure_ranks(mce, steps=3, warmup=1, kinds=("degree", "degen", "triangle", 
     import graphgen
     w = graphgen.chung_lu_planted()
     g = mce.Graph(w.n, torch.from_numpy(w.u).cuda(), torch.from_numpy(w.v).cuda())
-    model, train = train_learned_model(mce) if "learned" in kinds else (None, None)
+    model, split_model, train = train_learned_model(mce) if "learned" in kinds else (None, None, None)
     out, ref = {}, None
     for kind in kinds:
-        kw = {"rank": kind, "model": model} if kind == "learned" else {"rank": kind}
+        # the learned configuration: the rank model's key, and the split model
+        # ordering the subproblems and marking predicted-heavy ones (Section 4.2)
+        kw = ({"rank": kind, "model": model, "split_model": split_model} if kind == "learned" else {"rank": kind})
         runs = []
         for it in range(warmup + steps):
             r = mce.enumerate_cliques(g, **kw)

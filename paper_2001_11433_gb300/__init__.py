@@ -63,6 +63,9 @@ class Opts(ctypes.Structure):
         ("whole_graph", ctypes.c_int32),
         ("sm_limit", ctypes.c_int32),
         ("lane_search_words", ctypes.c_int32),
+        ("split_model", ctypes.c_void_p),
+        ("heavy_nodes", ctypes.c_uint32),
+        ("heavy_split_nodes", ctypes.c_uint32),
     ]
 
 
@@ -368,7 +371,7 @@ def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, s
               per_vertex=None, split=True, order_by_model=False, warps_per_block=0, blocks_per_sm=0,
               time_limit_ms=0, subset=None, subproblem_budget=0, shared_words=0, split_nodes=0,
               queue_capacity=0, warp_small_search=False, whole_graph=False, sm_limit=0,
-              lane_search_words=0) -> Opts:
+              lane_search_words=0, split_model=None, heavy_nodes=0, heavy_split_nodes=0) -> Opts:
     o = Opts()
     load().mce_opts_init(ctypes.byref(o))
     o.rank_kind = RANKS[rank] if isinstance(rank, str) else int(rank)
@@ -399,6 +402,9 @@ def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, s
     o.whole_graph = int(whole_graph)
     o.sm_limit = sm_limit
     o.lane_search_words = lane_search_words
+    o.split_model = split_model._h if split_model is not None else None
+    o.heavy_nodes = heavy_nodes
+    o.heavy_split_nodes = heavy_split_nodes
     return o
 
 

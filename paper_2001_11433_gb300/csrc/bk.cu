@@ -663,11 +663,15 @@ __device__ int poll(const BkParams &P, Acc &acc, int lane, int32_t root, uint64_
             // warp, whose frames can be handed over
             lph = hungry > qlen;
             if (qlen >= hungry) hungry = 0;
-            // a task hands over again only after 2048 more nodes of its own:
-            // pieces cut too small cost their receivers more than they hold
-            if (acc.t_nodes - cold().t_split < 2048ULL) hungry = 0;
+            // a subproblem predicted heavy spreads its subtree from the start
+            const bool heavy = P.heavy && P.heavy[P.mode == BK_MCE ? root : 0];
+            const unsigned long long every = heavy ? P.heavy_split_nodes : P.split_nodes;
+            // a task hands over again only after 2048 more nodes of its own
+            // (fewer for a heavy one): pieces cut too small cost their receivers
+            // more than they hold
+            if (acc.t_nodes - cold().t_split < (heavy && every < 2048ULL ? every : 2048ULL)) hungry = 0;
             // a long-running task spreads its subtree before anybody waits
-            if (!hungry && P.split_nodes && acc.t_nodes - cold().t_split >= P.split_nodes &&
+            if (!hungry && every && acc.t_nodes - cold().t_split >= every &&
                 qlen < (unsigned long long)P.qcap / 2) hungry = 1;
         }
     }
@@ -1243,14 +1247,13 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
 // operations and cliques are those of search_small.
 //
 // Universe of a small node with cn candidates and xn fini vertices (arena
-// words): h(C_k) as uint64 [2 cn], then rows adjC [cn], the columns of adjX
-// (adjXT[k] = {x : X_x ~ C_k}) [cn], rows adjX [xn], then the tie keys as
-// bytes (C members, then X members).  Root record (4 words): arena offset,
+// words): h(C_k) as uint64 [2 cn]; per C member its row adjC and tie key
+// [2 cn]; per X member its row adjX and tie key [2 xn] (a row and its key are
+// read together as one 8-byte word); the columns of adjX (adjXT[k] =
+// {x : X_x ~ C_k}) [cn].  Root record (4 words): arena offset,
 // cn | xn << 8 | (clique size at the node) << 16, hash sum at the node.
 
-__device__ __forceinline__ int lp_universe_words(int cn, int xn) {
-    return (4 * cn + xn + ((cn + xn + 3) >> 2) + 1) & ~1;
-}
+__device__ __forceinline__ int lp_universe_words(int cn, int xn) { return (5 * cn + 2 * xn + 1) & ~1; }
 
 struct LpSums {
     unsigned long long hash, wops;
@@ -1260,8 +1263,8 @@ struct LpSums {
 // A small-subtree node for one lane: its universe and its state.
 struct LpNode {
     const uint64_t *hC;
-    const uint32_t *adjC, *adjXT, *adjX;
-    const uint8_t *key;
+    const uint2 *akC, *akX;   // (row, tie key) per C / X member
+    const uint32_t *adjXT;
     int cn;
     uint32_t base;     // clique size at the universe's root
     uint32_t cand, finc, xs;
@@ -1287,21 +1290,19 @@ __device__ __forceinline__ uint32_t lp_pivot_ext(const LpNode &u, LpSums &o) {
     const uint32_t cf = u.cand | u.finc;
     uint32_t best = 0u, badj = 0u;
     for (uint32_t m = cf; m; m &= m - 1u) {
-        const int k = __ffs(m) - 1;
-        const uint32_t a = u.adjC[k];
-        const uint32_t kk = ((uint32_t)(__popc(u.cand & a) + 1) << 7) | u.key[k];
+        const uint2 ak = u.akC[__ffs(m) - 1];
+        const uint32_t kk = ((uint32_t)(__popc(u.cand & ak.x) + 1) << 7) | ak.y;
         if (kk > best) {
             best = kk;
-            badj = a;
+            badj = ak.x;
         }
     }
     for (uint32_t m = u.xs; m; m &= m - 1u) {
-        const int x = __ffs(m) - 1;
-        const uint32_t a = u.adjX[x];
-        const uint32_t kk = ((uint32_t)(__popc(u.cand & a) + 1) << 7) | u.key[u.cn + x];
+        const uint2 ak = u.akX[__ffs(m) - 1];
+        const uint32_t kk = ((uint32_t)(__popc(u.cand & ak.x) + 1) << 7) | ak.y;
         if (kk > best) {
             best = kk;
-            badj = a;
+            badj = ak.x;
         }
     }
     const uint32_t ext = u.cand & ~badj;
@@ -1316,7 +1317,7 @@ __device__ __forceinline__ uint32_t lp_pivot_ext(const LpNode &u, LpSums &o) {
 // operations follow search_small.
 __device__ __forceinline__ bool lp_child(const BkParams &P, unsigned long long *shist, const LpNode &u, int q,
                                          LpSums &o, uint32_t &cc, uint32_t &cf, uint32_t &cx, uint64_t &hq) {
-    const uint32_t aq = u.adjC[q];
+    const uint32_t aq = u.akC[q].x;
     cc = u.cand & aq;
     cf = u.finc & aq;
     cx = u.xs & u.adjXT[q];
@@ -1332,7 +1333,7 @@ __device__ __forceinline__ bool lp_child(const BkParams &P, unsigned long long *
         // vertex adjacent to c is the pivot (then no child)
         const int c = __ffs(cc) - 1;
         const uint32_t t = 1u + (uint32_t)(__popc(cf) + __popc(cx));
-        if ((cf & u.adjC[c]) != 0u || (cx & u.adjXT[c]) != 0u) {
+        if ((cf & u.akC[c].x) != 0u || (cx & u.adjXT[c]) != 0u) {
             ++o.nodes;
             o.wops += t;
         } else {
@@ -1408,10 +1409,9 @@ __device__ __forceinline__ LpNode lp_root_node(const uint32_t *lp, int r) {
     u.base = meta >> 16;
     const uint32_t *uni = lp + BK_LP_TABLE_WORDS + rec[0];
     u.hC = reinterpret_cast<const uint64_t *>(uni);
-    u.adjC = uni + 2 * u.cn;
-    u.adjXT = uni + 3 * u.cn;
-    u.adjX = uni + 4 * u.cn;
-    u.key = reinterpret_cast<const uint8_t *>(uni + 4 * u.cn + xn);
+    u.akC = reinterpret_cast<const uint2 *>(uni + 2 * u.cn);
+    u.akX = reinterpret_cast<const uint2 *>(uni + 4 * u.cn);
+    u.adjXT = uni + 4 * u.cn + 2 * xn;
     u.cand = u.cn == 32 ? FULL : ((1u << u.cn) - 1u);
     u.xs = xn == 32 ? FULL : ((1u << xn) - 1u);
     u.finc = 0u;
@@ -1471,8 +1471,8 @@ __device__ void lp_expand(const BkParams &P, unsigned long long *shist, LpNode u
 }
 
 // The buffered small subtrees, one lane per task.  The roots are expanded
-// breadth first (one level, and a second while the tasks number fewer than
-// four per lane) so that the heavy-tailed subtree sizes spread over the lanes;
+// breadth first (one level, and up to two more while the tasks number fewer
+// than eight per lane) so that the heavy-tailed subtree sizes spread over the lanes;
 // the last list is then taken task by task, each searched depth first.
 __device__ __noinline__ LpSums lp_run(const BkParams &P, uint32_t *lp, int nroots, unsigned long long *shist,
                                       uint32_t *tasks, int lane) {
@@ -1484,15 +1484,20 @@ __device__ __noinline__ LpSums lp_run(const BkParams &P, uint32_t *lp, int nroot
     for (int r = lane; r < nroots; r += 32) lp_expand(P, shist, lp_root_node(lp, r), r, o, la, &ctr[0]);
     __syncwarp();
     uint32_t n = min(ctr[0], (uint32_t)P.lp_task_cap);
-    uint32_t *list = la;
-    if (n > 0u && n < 128u) {
+    uint32_t *list = la, *other = lb;
+    // up to two more levels while the tasks number fewer than eight per lane
+    for (int round = 0; round < 2 && n > 0u && n < 256u; ++round) {
+        if (lane == 0) ctr[1] = 0u;
+        __syncwarp();
         for (uint32_t i = (uint32_t)lane; i < n; i += 32u) {
-            const uint32_t *t = la + (int64_t)i * BK_LP_TASK_WORDS;
-            lp_expand(P, shist, lp_task_get(lp, t), (int)(t[0] & 0xffu), o, lb, &ctr[1]);
+            const uint32_t *t = list + (int64_t)i * BK_LP_TASK_WORDS;
+            lp_expand(P, shist, lp_task_get(lp, t), (int)(t[0] & 0xffu), o, other, &ctr[1]);
         }
         __syncwarp();
         n = min(ctr[1], (uint32_t)P.lp_task_cap);
-        list = lb;
+        uint32_t *tmp = list;
+        list = other;
+        other = tmp;
     }
     for (uint32_t i = atomicAdd(&ctr[2], 1u); i < n; i = atomicAdd(&ctr[2], 1u)) {
         const uint32_t *t = list + (int64_t)i * BK_LP_TASK_WORDS;
@@ -1548,17 +1553,12 @@ __device__ void lp_enqueue(const BkParams &P, Ws &s, Acc &acc, unsigned long lon
         if (lane == k) adjXT = b;
     }
     uint32_t *uni = s.lp + BK_LP_TABLE_WORDS + s.lp_top;
-    uint8_t *key = reinterpret_cast<uint8_t *>(uni + 4 * u.cn + u.xn);
     if (lane < u.cn) {
         reinterpret_cast<uint64_t *>(uni)[lane] = vertex_hash(gC, P.seed);
-        uni[2 * u.cn + lane] = u.adjC;
-        uni[3 * u.cn + lane] = adjXT;
-        key[lane] = (uint8_t)u.tC;
+        reinterpret_cast<uint2 *>(uni + 2 * u.cn)[lane] = make_uint2(u.adjC, u.tC);
+        uni[4 * u.cn + 2 * u.xn + lane] = adjXT;
     }
-    if (lane < u.xn) {
-        uni[4 * u.cn + lane] = u.adjX;
-        key[u.cn + lane] = (uint8_t)u.tX;
-    }
+    if (lane < u.xn) reinterpret_cast<uint2 *>(uni + 4 * u.cn)[lane] = make_uint2(u.adjX, u.tX);
     if (lane == 0) {
         uint32_t *rec = s.lp + 4 * s.lp_n;
         rec[0] = (uint32_t)s.lp_top;

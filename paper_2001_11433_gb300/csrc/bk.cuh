@@ -102,6 +102,8 @@ struct BkParams {
     uint32_t *lp_tasks;       // per warp: two lists of lp_task_cap node records (BK_LP_TASK_WORDS each)
     int32_t lp_task_cap;
     int32_t sm_limit;         // SMs the persistent grid covers (0 = all)
+    const uint8_t *heavy;     // per vertex: 1 = predicted heavy, splits every heavy_split_nodes (or null)
+    uint32_t heavy_split_nodes;
 };
 
 // Words of the read-only part of a built subproblem with w local vertices of

@@ -134,6 +134,12 @@ __global__ void k_order_from_keys(const uint64_t *keys, int32_t m, int32_t idb, 
 
 __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
 
+// heavy[v] = 1 when the predicted log(1 + tree nodes) reaches thr
+__global__ void k_heavy_flags(const float *cost, int32_t n, float thr, uint8_t *heavy) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        heavy[v] = cost[v] >= thr ? 1 : 0;
+}
+
 // Whole-graph TTT (Algorithm 3 from K = ∅, cand = V): the root's pivot is a
 // vertex of largest degree (|V ∩ Γ(u)| = deg u), smallest id among ties.
 __global__ void k_whole_pivot(const int32_t *row_ptr, int32_t n, unsigned long long *best) {
@@ -403,13 +409,20 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
     int64_t up_nnz = 0;
     MCE_TRY(build_up_lists(g, rank.as<int32_t>(), s, up_ptr, up_col, &up_nnz));
     const float *costp = nullptr;
-    if (o->order_by_model && o->model) {
+    const mce_model *cost_model = o->split_model ? o->split_model : (o->order_by_model ? o->model : nullptr);
+    DevBuf heavy;
+    if (cost_model && n > 0) {
         DevBuf feat;
         MCE_TRY(feat.alloc((size_t)n * 8 * 4 + 16, s));
         MCE_TRY(cost.alloc((size_t)n * 4 + 16, s));
-        MCE_TRY(features(g, model_feature_kind(o->model), s, feat.as<float>()));
-        MCE_TRY(model_predict(o->model, feat.as<float>(), n, 1, s, cost.as<float>()));
+        MCE_TRY(features(g, model_feature_kind(cost_model), s, feat.as<float>()));
+        MCE_TRY(model_predict(cost_model, feat.as<float>(), n, 1, s, cost.as<float>()));
         costp = cost.as<float>();
+        if (o->split_model) {
+            MCE_TRY(heavy.alloc((size_t)n + 16, s));
+            const float thr = logf(1.0f + (float)(o->heavy_nodes ? o->heavy_nodes : 65536u));
+            MCE_LAUNCH(k_heavy_flags, grid_for(n, 256), 256, 0, s, costp, n, thr, heavy.as<uint8_t>());
+        }
     }
     MCE_TRY(out.alloc(OUT_WORDS * 8, s));
     MCE_CUDA(cudaMemsetAsync(out.p, 0, OUT_WORDS * 8, s));
@@ -506,6 +519,10 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         P.split = o->split;
         P.split_nodes = o->split ? (o->split_nodes ? o->split_nodes : 4096u) : 0u;
         P.sm_limit = o->sm_limit;
+        if (heavy.p && o->split) {
+            P.heavy = heavy.as<uint8_t>();
+            P.heavy_split_nodes = o->heavy_split_nodes ? o->heavy_split_nodes : 256u;
+        }
         P.max_run_ns = (uint64_t)o->time_limit_ms * 1000000ULL;
         // build cache for every subproblem (up to 2^30 words); when it holds them
         // all, a warp's own workspace only needs the private search state

@@ -140,3 +140,24 @@ def test_learned_rank_and_order_keep_the_clique_set(gpu_lib):
     # the learned rank is the rank of the network's BF16 prediction
     pred = m.predict(mce.features(g), bf16=True).cpu().numpy().astype(np.float64)
     assert np.array_equal(mce.rank(g, rank="learned", model=m).cpu().numpy(), O.rank_from_key(pred))
+
+
+def test_model_driven_splits_keep_results(gpu_lib):
+    """Learned heavy-subtree splitting (a model's predicted tree sizes mark
+    subproblems that hand over pieces every 64 nodes) changes the schedule
+    only: clique set, tree-node total and every subproblem's count, hash and
+    node count stay the oracle's."""
+    import torch
+    mce = gpu_lib
+    n, u, v = rmat(13, seed=21)
+    og = O.Graph(n, u, v)
+    ref = O.parmce(og, O.rank(og, "degen"), per_vertex=True, threads=4)
+    g = mce.Graph(n, _t(u), _t(v))
+    m = mce.Model(64, seed=8, features="light")
+    # a model that calls many subproblems heavy: predictions are around 0..1 before training
+    pv = tuple(torch.zeros(n, dtype=torch.int64, device="cuda") for _ in range(3))
+    r = mce.enumerate_cliques(g, rank="degen", split_model=m, heavy_nodes=1, heavy_split_nodes=64, per_vertex=pv)
+    assert r.tasks_split > 0
+    assert (r.count, r.hash, r.tree_nodes, list(r.hist)) == (ref.count, ref.hash, ref.nodes, list(ref.hist))
+    for k, name in enumerate(("count", "hash", "nodes")):
+        assert np.array_equal(pv[k].cpu().numpy().view(np.uint64), ref.per_vertex[name])
