@@ -243,6 +243,23 @@ mce_status mce_rank(const mce_graph *g, const mce_opts *opts, int32_t *rank_out)
  * clique list and per-subproblem outputs through opts. */
 mce_status mce_enumerate(const mce_graph *g, const mce_opts *opts, mce_result *res);
 
+/* All maximal cliques of g streamed to the host, for outputs larger than
+ * device memory.  The rank is computed once; the subproblems (Algorithm 5)
+ * then run a chunk of vertices at a time with their clique list in one of two
+ * device buffers of buf_words words, and while the next chunk runs, the last
+ * one's list is copied to pinned host memory and passed to sink(ctx, off, vtx,
+ * n_cliques, n_words): clique i starts at vtx[off[i]] with its size, then its
+ * vertex ids (host memory owned by the library, valid during the call).  A
+ * chunk whose list does not fit is split and run again, so every clique
+ * reaches the sink exactly once.  *res is the summary over all chunks.
+ * opts->subset, lists, per-subproblem outputs and whole_graph are not
+ * offered here (MCE_EINVAL); a single subproblem with more output than
+ * buf_words returns MCE_EOVERFLOW.  The sink runs on the calling thread. */
+typedef void (*mce_clique_sink)(void *ctx, const int64_t *off, const int32_t *vtx, int64_t n_cliques,
+                                int64_t n_words);
+mce_status mce_enumerate_stream(const mce_graph *g, const mce_opts *opts, int64_t buf_words, mce_clique_sink sink,
+                                void *ctx, mce_result *res);
+
 /* ---------------------------------------------------------------- learned cost model */
 
 /* Per-vertex features, device float[n*8], row-major (MCE_FEATURES_FULL):

@@ -206,6 +206,7 @@ SIGNATURES = {
     "imce_graph": ([_vp], _vp),
     "imce_cliques": ([_vp, _vp, _vp, _i64, _i64, _P(_i64), _P(_i64)], _i32),
     "imce_close": ([_vp], None),
+    "mce_enumerate_stream": ([_vp, _P(Opts), _i64, _vp, _vp, _P(ResultC)], _i32),
     "mce_enumerate_noalloc": ([_vp, _vp, _i32, _i64, _vp, _u64, _vp, _P(ResultC)], _i32),
 }
 
@@ -416,6 +417,29 @@ def enumerate_cliques(g: Graph, allow=(MCE_OK,), **kw) -> Result:
     st = lib.mce_enumerate(g._h, ctypes.byref(o), ctypes.byref(r))
     if st not in allow:
         _check(st, "mce_enumerate")
+    return _result(r, st)
+
+
+SINK = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                        ctypes.c_int64, ctypes.c_int64)
+
+
+def enumerate_stream(g: Graph, on_chunk, buf_words: int = 1 << 24, allow=(MCE_OK,), **kw) -> Result:
+    """mce_enumerate_stream: on_chunk(off, vtx) gets each chunk's clique list
+    as numpy arrays (copies), clique i at vtx[off[i]] (size, then ids)."""
+    lib = load()
+    o = make_opts(**kw)
+
+    def tramp(_ctx, off, vtx, nc, nw):
+        on_chunk(np.ctypeslib.as_array(off, shape=(nc,)).copy() if nc else np.zeros(0, np.int64),
+                 np.ctypeslib.as_array(vtx, shape=(nw,)).copy() if nw else np.zeros(0, np.int32))
+
+    cb = SINK(tramp)
+    r = ResultC()
+    st = lib.mce_enumerate_stream(g._h, ctypes.byref(o), int(buf_words), ctypes.cast(cb, ctypes.c_void_p), None,
+                                  ctypes.byref(r))
+    if st not in allow:
+        _check(st, "mce_enumerate_stream")
     return _result(r, st)
 
 

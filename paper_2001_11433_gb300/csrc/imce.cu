@@ -60,7 +60,7 @@ namespace mce {
 namespace {
 
 constexpr uint32_t FULL = 0xffffffffu;
-constexpr int kSubMaxWords = 4;          // cliques up to 256 vertices in Algorithm 8
+constexpr int kSubMaxWords = 4;          // Algorithm 8 masks: up to 256 endpoints of new edges in a clique
 constexpr int kSubCap = 4096;            // candidates per new clique
 
 __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t x) {
@@ -278,29 +278,103 @@ struct SubParams {
     int64_t *list_off;             // optional Λdel list
     int32_t *list_vtx;
     int64_t list_max_cliques, list_max_words;
-    int32_t *status;               // 1 = a clique too large, 2 = too many candidates
+    int32_t *status;               // 1 = more than 256 endpoints of new edges inside one clique
+    int64_t *big;                  // new cliques left to the enumerating fallback
+    unsigned long long *n_big;
+    unsigned long long *bk_scratch;   // fallback: per thread kBkWords words
+};
+
+// The members of a split candidate: every position of c that is no endpoint
+// of a new edge inside c (the core), and the endpoints whose R index is set
+// in the mask (ep: bitmap of endpoint positions).
+struct SubCand {
+    const int32_t *cv;
+    int32_t s;
+    const uint32_t *ep;
+    const unsigned long long *m;
+    __device__ __forceinline__ bool member(int p, int &r) const {
+        if (!((ep[p >> 5] >> (p & 31)) & 1u)) return true;
+        const bool in = (m[r >> 6] >> (r & 63)) & 1ULL;
+        ++r;
+        return in;
+    }
+};
+
+// Probe the index for the candidate (hash h, size) and claim it if alive;
+// the index keeps dead entries (a clique that died and was created again
+// after an edge deletion has a later alive copy).  Reports a claim.
+template <class Members>
+__device__ void sub_probe_claim(const SubParams &P, uint64_t h, int32_t size, const Members &mem) {
+    int64_t slot = (int64_t)(h & (uint64_t)P.tmask), found = -1;
+    for (int64_t probe = 0; probe <= P.tmask; ++probe) {
+        const int32_t id1 = P.tid[slot];
+        if (id1 == 0) break;
+        if (P.tkey[slot] == h) {
+            const int32_t *pl = P.pool + P.off[id1 - 1];
+            bool eq = pl[0] == size;
+            if (eq) eq = mem.equal(pl + 1);
+            if (eq && atomicCAS(&P.alive[id1 - 1], 1, 0) == 1) {
+                found = id1 - 1;
+                break;
+            }
+        }
+        slot = (slot + 1) & P.tmask;
+    }
+    if (found < 0) return;
+    const unsigned long long k = atomicAdd(P.n_claimed, 1ULL);
+    if ((int64_t)k < P.claimed_cap) P.claimed[k] = found;
+    atomicAdd(&P.out[OUT_COUNT], 1ULL);
+    atomicAdd(&P.out[OUT_HASH], h);
+    if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
+    atomicMax(&P.out[OUT_MAXSIZE], (unsigned long long)size);
+    if (P.list_off) {
+        const unsigned long long li = atomicAdd(&P.out[OUT_LIST_CLIQUES], 1ULL);
+        const unsigned long long lp = atomicAdd(&P.out[OUT_LIST_WORDS], (unsigned long long)size + 1);
+        if ((int64_t)li < P.list_max_cliques && (int64_t)(lp + size + 1) <= P.list_max_words) {
+            P.list_off[li] = (int64_t)lp;
+            const int32_t *pl = P.pool + P.off[found];
+            for (int q = 0; q <= size; ++q) P.list_vtx[lp + q] = pl[q];
+        } else {
+            atomicOr(&P.out[OUT_FLAGS], 1ULL);
+        }
+    }
+}
+
+struct MaskMembers {
+    SubCand c;
+    __device__ bool equal(const int32_t *sorted) const {
+        int k = 0, r = 0;
+        for (int p = 0; p < c.s; ++p)
+            if (c.member(p, r) && sorted[k++] != c.cv[p]) return false;
+        return true;
+    }
 };
 
 // One warp per new clique c: E(c) ∩ H in lexicographic order, then S is
 // refined edge by edge (c' containing both endpoints is replaced by c' \ {u}
 // and c' \ {v}); S stays a set.  Every c' ∈ S found alive in the index is
-// claimed once and reported (Algorithm 8, lines 13-16).
+// claimed once and reported (Algorithm 8, lines 13-16).  Vertices of c that
+// are no endpoint of a new edge inside c belong to every candidate, so the
+// masks run over the endpoints only (at most 256).  A clique with more than
+// 512 new edges inside, or whose S outgrows kSubCap, goes to k_imce_sub_bk.
 __global__ void __launch_bounds__(256) k_imce_sub(SubParams P) {
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     constexpr int MW = kSubMaxWords;
     unsigned long long *S = P.scratch + gw * (int64_t)2 * kSubCap * MW;
     unsigned long long *S2 = S + (int64_t)kSubCap * MW;
     __shared__ int32_t edges_s[8][2 * 512];
-    int32_t *edges = edges_s[threadIdx.x >> 5];
+    __shared__ uint32_t ep_s[8][MCE_HIST_CAP / 32];
+    int32_t *edges = edges_s[wib];
+    uint32_t *ep = ep_s[wib];
     for (int64_t c = gw; c < P.n_new; c += nw) {
         const int32_t *cv = P.nvtx + P.noff[c] + 1;
         const int32_t s = cv[-1];
-        if (s > 64 * MW) {
-            if (lane == 0) atomicOr(P.status, 1);
-            continue;
-        }
+        const int sw = (s + 31) >> 5;
+        for (int k = lane; k < sw; k += 32) ep[k] = 0u;
+        __syncwarp();
         // new edges inside c: (i, j) positions, i < j, lexicographic
         int ne = 0;
         for (int i = 0; i < s; ++i) {
@@ -323,20 +397,42 @@ __global__ void __launch_bounds__(256) k_imce_sub(SubParams P) {
                         edges[2 * slot] = i;
                         edges[2 * slot + 1] = j;
                     }
+                    atomicOr(&ep[i >> 5], 1u << (i & 31));
+                    atomicOr(&ep[j >> 5], 1u << (j & 31));
                 }
                 ne += __popc(b);
             }
         }
         __syncwarp();
-        if (ne > 512) {
-            if (lane == 0) atomicOr(P.status, 2);
+        int nr = 0;
+        for (int k = lane; k < sw; k += 32) nr += __popc(ep[k]);
+        nr = __reduce_add_sync(FULL, nr);
+        if (nr > 64 * MW) {
+            if (lane == 0) atomicOr(P.status, 1);
             continue;
         }
+        if (ne > 512) {
+            if (lane == 0) P.big[atomicAdd(P.n_big, 1ULL)] = c;
+            continue;
+        }
+        // endpoint positions -> R indices (rank among the endpoints)
+        for (int e = lane; e < 2 * ne; e += 32) {
+            const int p = edges[e];
+            int r = 0;
+            for (int k = 0; k < (p >> 5); ++k) r += __popc(ep[k]);
+            edges[e] = r + __popc(ep[p >> 5] & ((1u << (p & 31)) - 1u));
+        }
+        // hash and size of the core
+        uint64_t hcore = 0;
+        for (int p = lane; p < s; p += 32)
+            if (!((ep[p >> 5] >> (p & 31)) & 1u)) hcore += vertex_hash(cv[p], P.seed);
+        for (int o = 16; o; o >>= 1) hcore += __shfl_xor_sync(FULL, hcore, o);
+        __syncwarp();
         // S = {c}
         int ns = 1;
         if (lane < MW) {
             const int lo = lane * 64;
-            const int nb = s - lo;
+            const int nb = nr - lo;
             S[lane] = nb >= 64 ? ~0ULL : (nb > 0 ? ((1ULL << nb) - 1) : 0ULL);
         }
         __syncwarp();
@@ -405,79 +501,195 @@ __global__ void __launch_bounds__(256) k_imce_sub(SubParams P) {
             __syncwarp();
         }
         if (overflow) {
-            if (lane == 0) atomicOr(P.status, 2);
+            if (lane == 0) P.big[atomicAdd(P.n_big, 1ULL)] = c;
             continue;
         }
         // probe the index for each candidate
         for (int t0 = 0; t0 < ns; t0 += 32) {
             const int t = t0 + lane;
-            int64_t found = -1;
-            int32_t size = 0;
-            uint64_t h = 0;
             if (t < ns) {
-                unsigned long long m[MW];
-#pragma unroll
-                for (int w = 0; w < MW; ++w) m[w] = S[(int64_t)t * MW + w];
-                uint64_t hs = 0;
-                for (int w = 0; w < MW; ++w) {
-                    unsigned long long x = m[w];
-                    while (x) {
-                        const int b = __ffsll((long long)x) - 1;
-                        x &= x - 1;
-                        hs += vertex_hash(cv[w * 64 + b], P.seed);
+                const unsigned long long *m = S + (int64_t)t * MW;
+                uint64_t hs = hcore;
+                int32_t size = s - nr;
+                int r = 0;
+                for (int p = 0; p < s; ++p) {
+                    if (!((ep[p >> 5] >> (p & 31)) & 1u)) continue;
+                    if ((m[r >> 6] >> (r & 63)) & 1ULL) {
+                        hs += vertex_hash(cv[p], P.seed);
                         ++size;
                     }
+                    ++r;
                 }
-                h = clique_hash_from_sum(hs, (uint32_t)size);
-                int64_t slot = (int64_t)(h & (uint64_t)P.tmask);
-                for (;;) {
-                    const int32_t id1 = P.tid[slot];
-                    if (id1 == 0) break;
-                    if (P.tkey[slot] == h) {
-                        const int32_t *pl = P.pool + P.off[id1 - 1];
-                        bool eq = pl[0] == size;
-                        if (eq) {
-                            int k = 1;
-                            for (int w = 0; w < MW && eq; ++w) {
-                                unsigned long long x = m[w];
-                                while (x && eq) {
-                                    const int b = __ffsll((long long)x) - 1;
-                                    x &= x - 1;
-                                    eq = pl[k++] == cv[w * 64 + b];
-                                }
-                            }
-                        }
-                        // the index keeps dead entries: a clique that died and was
-                        // created again (after an edge deletion) has a later alive copy
-                        if (eq && atomicCAS(&P.alive[id1 - 1], 1, 0) == 1) {
-                            found = id1 - 1;
-                            break;
-                        }
-                    }
-                    slot = (slot + 1) & P.tmask;
-                }
-                if (found >= 0) {
-                    const unsigned long long k = atomicAdd(P.n_claimed, 1ULL);
-                    if ((int64_t)k < P.claimed_cap) P.claimed[k] = found;
-                    atomicAdd(&P.out[OUT_COUNT], 1ULL);
-                    atomicAdd(&P.out[OUT_HASH], h);
-                    if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
-                    atomicMax(&P.out[OUT_MAXSIZE], (unsigned long long)size);
-                    if (P.list_off) {
-                        const unsigned long long li = atomicAdd(&P.out[OUT_LIST_CLIQUES], 1ULL);
-                        const unsigned long long lp = atomicAdd(&P.out[OUT_LIST_WORDS], (unsigned long long)size + 1);
-                        if ((int64_t)li < P.list_max_cliques && (int64_t)(lp + size + 1) <= P.list_max_words) {
-                            P.list_off[li] = (int64_t)lp;
-                            const int32_t *pl = P.pool + P.off[found];
-                            for (int q = 0; q <= size; ++q) P.list_vtx[lp + q] = pl[q];
-                        } else {
-                            atomicOr(&P.out[OUT_FLAGS], 1ULL);
-                        }
-                    }
-                }
+                const MaskMembers mm{SubCand{cv, s, ep, m}};
+                sub_probe_claim(P, clique_hash_from_sum(hs, (uint32_t)size), size, mm);
             }
         }
         __syncwarp();
+    }
+}
+
+// Enumerating fallback of Algorithm 8 for a new clique whose split set S
+// would outgrow kSubCap (or that holds more than 512 new edges): the
+// candidates that can be old maximal cliques are exactly the maximal cliques
+// of G[c] (c without its new edges), which are the core of c plus a maximal
+// clique of G[R] on the endpoints R.  One thread per such clique enumerates
+// those with Bron-Kerbosch (Tomita pivot) on 256-bit sets and probes each.
+constexpr int kBkWords = 256 * 4 + 258 * 12;   // rows of G[R], then frames (cand, fini, ext)
+
+struct BkMembers {
+    const int32_t *cv;
+    int32_t s;
+    const int32_t *rpos;   // position in c of each endpoint, ascending
+    int32_t nr;
+    const unsigned long long *q;   // the chosen endpoints (R indices)
+    __device__ bool equal(const int32_t *sorted) const {
+        int k = 0, r = 0;
+        for (int p = 0; p < s; ++p) {
+            bool in = true;
+            if (r < nr && rpos[r] == p) {
+                in = (q[r >> 6] >> (r & 63)) & 1ULL;
+                ++r;
+            }
+            if (in && sorted[k++] != cv[p]) return false;
+        }
+        return true;
+    }
+};
+
+__global__ void k_imce_sub_bk(SubParams P, int64_t n_big) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long *adj = P.bk_scratch + tid * (int64_t)kBkWords;   // 256 rows of 4 words
+    unsigned long long *fr = adj + 256 * 4;                                // frames of 12 words
+    int32_t rpos[256];
+    for (int64_t bi = tid; bi < n_big; bi += nth) {
+        const int64_t c = P.big[bi];
+        const int32_t *cv = P.nvtx + P.noff[c] + 1;
+        const int32_t s = cv[-1];
+        // endpoints of new edges inside c, ascending position
+        int nr = 0;
+        bool too_many = false;
+        for (int p = 0; p < s && !too_many; ++p) {
+            const int32_t a = cv[p];
+            bool hit = false;
+            for (int32_t e = P.h_ptr[a]; e < P.h_ptr[a + 1] && !hit; ++e) {
+                const int q = lower_bound_i32(cv, s, P.h_adj[e]);
+                hit = q < s && cv[q] == P.h_adj[e];
+            }
+            if (hit) {
+                if (nr == 256) too_many = true;
+                else rpos[nr++] = p;
+            }
+        }
+        if (too_many) {
+            atomicOr(P.status, 1);
+            continue;
+        }
+        // rows of G[R]: every other endpoint not joined by a new edge
+        for (int r = 0; r < nr; ++r) {
+            unsigned long long *row = adj + r * 4;
+            for (int w = 0; w < 4; ++w) {
+                const int lo = w * 64, nb = nr - lo;
+                row[w] = nb >= 64 ? ~0ULL : (nb > 0 ? ((1ULL << nb) - 1) : 0ULL);
+            }
+            row[r >> 6] &= ~(1ULL << (r & 63));
+            const int32_t a = cv[rpos[r]];
+            for (int32_t e = P.h_ptr[a]; e < P.h_ptr[a + 1]; ++e) {
+                const int q = lower_bound_i32(cv, s, P.h_adj[e]);
+                if (!(q < s && cv[q] == P.h_adj[e])) continue;
+                int lo = 0, hi = nr;   // R index of position q
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (rpos[mid] < q) lo = mid + 1; else hi = mid;
+                }
+                row[lo >> 6] &= ~(1ULL << (lo & 63));
+            }
+        }
+        uint64_t hcore = 0;
+        {
+            int r = 0;
+            for (int p = 0; p < s; ++p) {
+                if (r < nr && rpos[r] == p) {
+                    ++r;
+                    continue;
+                }
+                hcore += vertex_hash(cv[p], P.seed);
+            }
+        }
+        // Bron-Kerbosch over R: frame d = (cand, fini, ext) at depth d; K = chosen
+        unsigned long long K[4] = {0, 0, 0, 0};
+        int d = 0;
+        unsigned long long *f0 = fr;
+        for (int w = 0; w < 4; ++w) {
+            const int lo = w * 64, nb = nr - lo;
+            f0[w] = nb >= 64 ? ~0ULL : (nb > 0 ? ((1ULL << nb) - 1) : 0ULL);
+            f0[4 + w] = 0ULL;
+        }
+        bool enter = true;
+        int qd[258];
+        for (;;) {
+            unsigned long long *f = fr + (int64_t)d * 12;
+            if (enter) {
+                bool any_c = false, any_f = false;
+                for (int w = 0; w < 4; ++w) {
+                    any_c |= f[w] != 0ULL;
+                    any_f |= f[4 + w] != 0ULL;
+                }
+                if (!any_c) {
+                    if (!any_f) {
+                        uint64_t hs = hcore;
+                        int32_t size = s - nr;
+                        for (int w = 0; w < 4; ++w)
+                            for (unsigned long long x = K[w]; x; x &= x - 1) {
+                                hs += vertex_hash(cv[rpos[w * 64 + __ffsll((long long)x) - 1]], P.seed);
+                                ++size;
+                            }
+                        const BkMembers bm{cv, s, rpos, nr, K};
+                        sub_probe_claim(P, clique_hash_from_sum(hs, (uint32_t)size), size, bm);
+                    }
+                    goto pop;
+                }
+                // pivot: the member of cand ∪ fini with most candidate neighbours
+                int best = -1, bc = -1;
+                for (int w = 0; w < 4; ++w)
+                    for (unsigned long long x = f[w] | f[4 + w]; x; x &= x - 1) {
+                        const int u = w * 64 + __ffsll((long long)x) - 1;
+                        int cnt = 0;
+                        for (int v = 0; v < 4; ++v) cnt += __popcll(f[v] & adj[u * 4 + v]);
+                        if (cnt > bc) {
+                            bc = cnt;
+                            best = u;
+                        }
+                    }
+                for (int w = 0; w < 4; ++w) f[8 + w] = f[w] & ~adj[best * 4 + w];
+                enter = false;
+            }
+            {
+                int q = -1;
+                for (int w = 0; w < 4 && q < 0; ++w)
+                    if (f[8 + w]) q = w * 64 + __ffsll((long long)f[8 + w]) - 1;
+                if (q < 0) goto pop;
+                const unsigned long long qb = 1ULL << (q & 63);
+                f[8 + (q >> 6)] &= ~qb;
+                unsigned long long *g = f + 12;
+                for (int w = 0; w < 4; ++w) {
+                    g[w] = f[w] & adj[q * 4 + w];
+                    g[4 + w] = f[4 + w] & adj[q * 4 + w];
+                }
+                f[q >> 6] &= ~qb;
+                f[4 + (q >> 6)] |= qb;
+                K[q >> 6] |= qb;
+                qd[d] = q;
+                ++d;
+                enter = true;
+                continue;
+            }
+        pop:
+            if (d == 0) break;
+            --d;
+            K[qd[d] >> 6] &= ~(1ULL << (qd[d] & 63));
+            enter = false;
+        }
     }
 }
 
@@ -1201,7 +1413,7 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
     MCE_TRY(batch_cliques(S, gg.g, bt, nloff, nlvtx, hn));
     const int64_t n_new = (int64_t)hn[OUT_LIST_CLIQUES];
     // ---- 4. Λdel (Algorithm 8)
-    DevBuf sout, scratch, claimed, nclaimed, sstat;
+    DevBuf sout, scratch, claimed, nclaimed, sstat, big, nbig, bkscr;
     MCE_TRY(sout.alloc(OUT_WORDS * 8, s));
     MCE_CUDA(cudaMemsetAsync(sout.p, 0, OUT_WORDS * 8, s));
     const unsigned sub_blocks = (unsigned)num_sms() * 2;
@@ -1211,8 +1423,11 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
     MCE_TRY(claimed.alloc((size_t)claimed_cap * 8, s));
     MCE_TRY(nclaimed.alloc(8, s));
     MCE_TRY(sstat.alloc(4, s));
+    MCE_TRY(big.alloc((size_t)(n_new + 1) * 8, s));
+    MCE_TRY(nbig.alloc(8, s));
     MCE_CUDA(cudaMemsetAsync(nclaimed.p, 0, 8, s));
     MCE_CUDA(cudaMemsetAsync(sstat.p, 0, 4, s));
+    MCE_CUDA(cudaMemsetAsync(nbig.p, 0, 8, s));
     unsigned long long hs[OUT_WORDS];
     memset(hs, 0, sizeof(hs));
     unsigned long long ncl = 0;
@@ -1237,7 +1452,19 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
         Q.n_claimed = nclaimed.as<unsigned long long>();
         Q.claimed_cap = claimed_cap;
         Q.status = sstat.as<int32_t>();
+        Q.big = big.as<int64_t>();
+        Q.n_big = nbig.as<unsigned long long>();
         MCE_LAUNCH(k_imce_sub, sub_blocks, 256, 0, s, Q);
+        // new cliques whose split set outgrew the warp's buffer: enumerating fallback
+        unsigned long long hbig = 0;
+        MCE_CUDA(cudaMemcpyAsync(&hbig, nbig.p, 8, cudaMemcpyDeviceToHost, s));
+        MCE_CUDA(cudaStreamSynchronize(s));
+        if (hbig) {
+            const int64_t threads = (int64_t)hbig < 4096 ? (int64_t)hbig : 4096;
+            MCE_TRY(bkscr.alloc((size_t)threads * kBkWords * 8, s));
+            Q.bk_scratch = bkscr.as<unsigned long long>();
+            MCE_LAUNCH(k_imce_sub_bk, (unsigned)((threads + 63) / 64), 64, 0, s, Q, (int64_t)hbig);
+        }
         MCE_CUDA(cudaMemcpyAsync(hs, sout.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
         MCE_CUDA(cudaMemcpyAsync(&ncl, nclaimed.p, 8, cudaMemcpyDeviceToHost, s));
         MCE_CUDA(cudaMemcpyAsync(&hst, sstat.p, 4, cudaMemcpyDeviceToHost, s));
@@ -1246,7 +1473,8 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
             const int64_t nr = (int64_t)ncl < claimed_cap ? (int64_t)ncl : claimed_cap;
             if (nr) MCE_LAUNCH(k_restore_alive, grid_for(nr, 256), 256, 0, s, claimed.as<int64_t>(), nr, S->idx.alive);
             MCE_CUDA(cudaStreamSynchronize(s));
-            g_last_error = hst & 1 ? "imce: new clique larger than 256 vertices" : "imce: too many subsumed candidates";
+            g_last_error = hst & 1 ? "imce: more than 256 endpoints of new edges inside one new clique"
+                                   : "imce: more subsumed cliques than the claim buffer holds";
             return MCE_ESTATE;
         }
     }

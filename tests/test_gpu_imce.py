@@ -147,3 +147,51 @@ def test_chung_lu_stream_prefix(gpu_lib):
         assert d.applied == rho
         check_delta(d, onew.cliques, odel.cliques)
     assert d.alive == ost.alive
+
+
+# ---------------------------------------------------------------- Algorithm 8 beyond the warp's buffers
+
+def _imce_vs_oracle(mce, n, pairs, add):
+    u = np.array([a for a, b in pairs], np.int32)
+    v = np.array([b for a, b in pairs], np.int32)
+    st = mce.Imce(mce.Graph(n, _t(u), _t(v)))
+    ost = O.Imce(O.Graph(n, u, v))
+    au = np.array([a for a, b in add], np.int32)
+    av = np.array([b for a, b in add], np.int32)
+    rho, onew, odel = ost.add(au, av)
+    d = st.add_edges(au, av)
+    assert d.applied == rho
+    check_delta(d, onew.cliques, odel.cliques)
+    assert st.cliques(1 << 16, 1 << 20) == ost.cliques().cliques
+    return d
+
+
+def test_new_clique_over_256_vertices(gpu_lib):
+    """K_300 minus (0, 1), then (0, 1) added: one new clique of 300 vertices
+    subsumes K_300 - 0 and K_300 - 1 (the masks of Algorithm 8 run over the
+    two endpoints only)."""
+    n = 300
+    pairs = [(i, j) for i in range(n) for j in range(i + 1, n) if (i, j) != (0, 1)]
+    d = _imce_vs_oracle(gpu_lib, n, pairs, [(0, 1)])
+    assert (d.new_count, d.sub_count) == (1, 2)
+
+
+def test_split_set_beyond_the_warp_buffer(gpu_lib):
+    """Moon-Moser graph K_{3,...,3} with 8 parts plus every edge inside the
+    parts: the graph becomes complete, and the one new clique subsumes all
+    3^8 = 6,561 old cliques, more than Algorithm 8's split set holds in a
+    warp's buffer (4,096), so the enumerating fallback finds them."""
+    k = 8
+    parts = [list(range(3 * i, 3 * i + 3)) for i in range(k)]
+    pairs = [(a, b) for i in range(k) for j in range(i + 1, k) for a in parts[i] for b in parts[j]]
+    add = [(p[0], p[1]) for p in parts] + [(p[0], p[2]) for p in parts] + [(p[1], p[2]) for p in parts]
+    d = _imce_vs_oracle(gpu_lib, 3 * k, pairs, add)
+    assert (d.new_count, d.sub_count) == (1, 3 ** k)
+
+
+def test_more_than_512_new_edges_in_one_clique(gpu_lib):
+    """40 isolated vertices, then all 780 edges among them: K_40 is new and
+    subsumes the 40 singletons."""
+    n = 40
+    d = _imce_vs_oracle(gpu_lib, n, [], [(i, j) for i in range(n) for j in range(i + 1, n)])
+    assert (d.new_count, d.sub_count) == (1, 40)

@@ -394,3 +394,46 @@ def test_whole_graph_tree_equals_oracle(gpu_lib, case):
     for split_nodes in (0, 64):
         r = mce.enumerate_cliques(g, whole_graph=True, split_nodes=split_nodes)
         assert (r.count, r.hash, list(r.hist), r.tree_nodes) == (ref.count, ref.hash, list(ref.hist), ref.nodes)
+
+
+# ---------------------------------------------------------------- clique lists streamed to the host
+
+@pytest.mark.parametrize("buf_words", [4096, 1 << 20])
+def test_stream_er2000_full_list(gpu_lib, buf_words):
+    """The ER 2000 workload's cliques streamed to the host through two small
+    device buffers (many chunks, some split after overflowing): every clique
+    arrives once and the list equals the oracle's."""
+    mce = gpu_lib
+    w = graphgen.er_2000()
+    g = gpu_graph(mce, w.n, w.u, w.v)
+    got = []
+    chunks = []
+
+    def sink(off, vtx):
+        chunks.append(len(off))
+        for p in off.tolist():
+            k = int(vtx[p])
+            got.append(tuple(sorted(int(x) for x in vtx[p + 1:p + 1 + k])))
+
+    r = mce.enumerate_stream(g, sink, buf_words=buf_words, rank="degen")
+    ref = O.parmce(O.Graph(w.n, w.u, w.v), O.rank(O.Graph(w.n, w.u, w.v), "degen"), want_list=True)
+    assert sorted(got) == ref.cliques
+    assert (r.count, r.hash, list(r.hist), r.tree_nodes) == (ref.count, ref.hash, list(ref.hist), ref.nodes)
+    if buf_words == 4096:
+        assert len(chunks) > 4
+
+
+def test_stream_rmat13_summary(gpu_lib):
+    mce = gpu_lib
+    n, u, v = rmat(13)
+    g = gpu_graph(mce, n, u, v)
+    total = [0, 0]
+
+    def sink(off, vtx):
+        total[0] += len(off)
+        total[1] += len(vtx)
+
+    r = mce.enumerate_stream(g, sink, buf_words=1 << 16, rank="degree")
+    ref = mce.enumerate_cliques(g, rank="degree")
+    assert (r.count, r.hash, list(r.hist), r.tree_nodes) == (ref.count, ref.hash, list(ref.hist), ref.tree_nodes)
+    assert total[0] == r.count and total[1] == r.count + sum(i * int(c) for i, c in enumerate(r.hist))
