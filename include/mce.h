@@ -144,10 +144,11 @@ typedef struct {
     int32_t lane_search_words;
     /* Learned heavy-subtree splitting: a model that predicts log(1 + search-
      * tree nodes) of each subproblem under the rank in use.  When set, the
-     * subproblems run in decreasing predicted cost, and those predicted to
-     * pass heavy_nodes (0 = 65536) tree nodes hand pieces of their subtree to
-     * other warps every heavy_split_nodes (0 = 256) nodes from the start,
-     * instead of every split_nodes.  Results do not depend on it. */
+     * subproblems predicted to pass heavy_nodes (0 = 65536) tree nodes hand
+     * pieces of their subtree to other warps every heavy_split_nodes (0 =
+     * 256) nodes from the start, instead of every split_nodes; with
+     * order_by_model the subproblems also run in decreasing predicted cost
+     * (this model's, else `model`'s).  Results do not depend on it. */
     const mce_model *split_model;
     uint32_t heavy_nodes;
     uint32_t heavy_split_nodes;

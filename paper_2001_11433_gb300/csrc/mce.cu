@@ -417,11 +417,11 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         MCE_TRY(cost.alloc((size_t)n * 4 + 16, s));
         MCE_TRY(features(g, model_feature_kind(cost_model), s, feat.as<float>()));
         MCE_TRY(model_predict(cost_model, feat.as<float>(), n, 1, s, cost.as<float>()));
-        costp = cost.as<float>();
+        if (o->order_by_model) costp = cost.as<float>();
         if (o->split_model) {
             MCE_TRY(heavy.alloc((size_t)n + 16, s));
             const float thr = logf(1.0f + (float)(o->heavy_nodes ? o->heavy_nodes : 65536u));
-            MCE_LAUNCH(k_heavy_flags, grid_for(n, 256), 256, 0, s, costp, n, thr, heavy.as<uint8_t>());
+            MCE_LAUNCH(k_heavy_flags, grid_for(n, 256), 256, 0, s, cost.as<float>(), n, thr, heavy.as<uint8_t>());
         }
     }
     MCE_TRY(out.alloc(OUT_WORDS * 8, s));
