@@ -144,6 +144,7 @@ TREE_CAP = 1 << 24          # nodes per subproblem search tree in the benchmark 
 BLOCKS_PER_SM = 3
 SPLIT_NODES = 4096
 LANE_SEARCH_WORDS = 0
+LANE_HOLD_WAITING = 0
 
 # DRAM bytes (read + write) of one k_bk launch from an ncu capture of this
 # workload (a 10 % sample of its subproblems), scaled by
@@ -300,7 +301,8 @@ def run_ours(args):
         g = mce.Graph(w.n, dev_u, dev_v)
         r = mce.enumerate_cliques(g, rank="degen", subset=dev_subset, blocks_per_sm=args.blocks_per_sm,
                                   split_nodes=SPLIT_NODES, warp_small_search=args.warp_small_search,
-                                  lane_search_words=args.lane_search_words)
+                                  lane_search_words=args.lane_search_words,
+                                  lane_hold_waiting=args.lane_hold_waiting)
         g.close()
         return r
 
@@ -339,7 +341,8 @@ def run_ours(args):
         g = mce.Graph(w.n, pin_u.numpy(), pin_v.numpy())
         r2 = mce.enumerate_cliques(g, rank="degen", subset=pin_subset.numpy(), blocks_per_sm=args.blocks_per_sm,
                                    split_nodes=SPLIT_NODES, warp_small_search=args.warp_small_search,
-                                  lane_search_words=args.lane_search_words)
+                                  lane_search_words=args.lane_search_words,
+                                  lane_hold_waiting=args.lane_hold_waiting)
         g.close()
         e2e_times.append((time.perf_counter() - t0) * 1000.0)
     clocks = sampler.stop()
@@ -373,7 +376,8 @@ def run_ours(args):
         gpu_runs = [mce.enumerate_cliques(gs, rank="degen", subset=torch.from_numpy(sample).cuda(),
                                           blocks_per_sm=args.blocks_per_sm, split_nodes=SPLIT_NODES,
                                           warp_small_search=args.warp_small_search,
-                                          lane_search_words=args.lane_search_words) for _ in range(3)]
+                                          lane_search_words=args.lane_search_words,
+                                  lane_hold_waiting=args.lane_hold_waiting) for _ in range(3)]
         gs.close()
         assert all(x.count == base["all_threads"]["cliques"] for x in gpu_runs)
         assert all(f"{x.hash:#018x}" == base["single_thread"]["hash"] for x in gpu_runs)
@@ -404,7 +408,8 @@ def run_ours(args):
                    "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{world}",
                    "launch": {"blocks_per_sm": args.blocks_per_sm, "warps_per_block": 8, "split_nodes": SPLIT_NODES,
                               "small_search": "warp" if args.warp_small_search else "lane-parallel",
-                              "lane_search_words": args.lane_search_words}},
+                              "lane_search_words": args.lane_search_words,
+                              "lane_hold_waiting": args.lane_hold_waiting}},
         "phases_ms": {"rank": res.ms_rank, "enumerate": res.ms_enum, "search_kernel": float(np.mean(search_ms))},
         "roofline": {"bound": "alu", "kernel": "k_bk (persistent search)", "achieved": achieved, "peak": peak_ops,
                      "unit": "word-ops/s", "frac": achieved / peak_ops if peak_ops else None,
@@ -757,6 +762,8 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=BLOCKS_PER_SM, help="rmat18: resident search blocks per SM")
     ap.add_argument("--lane-search-words", type=int, default=LANE_SEARCH_WORDS,
                     help="rmat18: per-warp shared words of the lane-parallel small search (0 = automatic)")
+    ap.add_argument("--lane-hold-waiting", type=int, default=LANE_HOLD_WAITING,
+                    help="rmat18: waiting warps from which small subtrees stay with the whole warp")
     ap.add_argument("--warp-small-search", action="store_true",
                     help="rmat18: search small subtrees with the whole warp (the lane-parallel search is the default)")
     ap.add_argument("--graph-budget", type=int, default=1 << 20, help="batched: tree nodes per graph")

@@ -152,6 +152,10 @@ typedef struct {
     const mce_model *split_model;
     uint32_t heavy_nodes;
     uint32_t heavy_split_nodes;
+    /* While at least this many warps wait for work (0 = 1), small subtrees
+     * are searched by the whole warp, whose pending children can be handed
+     * over, instead of one per lane. */
+    uint32_t lane_hold_waiting;
 } mce_opts;
 
 typedef struct {

@@ -66,6 +66,7 @@ class Opts(ctypes.Structure):
         ("split_model", ctypes.c_void_p),
         ("heavy_nodes", ctypes.c_uint32),
         ("heavy_split_nodes", ctypes.c_uint32),
+        ("lane_hold_waiting", ctypes.c_uint32),
     ]
 
 
@@ -372,7 +373,8 @@ def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, s
               per_vertex=None, split=True, order_by_model=False, warps_per_block=0, blocks_per_sm=0,
               time_limit_ms=0, subset=None, subproblem_budget=0, shared_words=0, split_nodes=0,
               queue_capacity=0, warp_small_search=False, whole_graph=False, sm_limit=0,
-              lane_search_words=0, split_model=None, heavy_nodes=0, heavy_split_nodes=0) -> Opts:
+              lane_search_words=0, split_model=None, heavy_nodes=0, heavy_split_nodes=0,
+              lane_hold_waiting=0) -> Opts:
     o = Opts()
     load().mce_opts_init(ctypes.byref(o))
     o.rank_kind = RANKS[rank] if isinstance(rank, str) else int(rank)
@@ -406,6 +408,7 @@ def make_opts(rank="degen", user_rank=None, model=None, node_budget=0, seed=0, s
     o.split_model = split_model._h if split_model is not None else None
     o.heavy_nodes = heavy_nodes
     o.heavy_split_nodes = heavy_split_nodes
+    o.lane_hold_waiting = lane_hold_waiting
     return o
 
 

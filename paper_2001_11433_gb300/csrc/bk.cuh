@@ -104,6 +104,7 @@ struct BkParams {
     int32_t sm_limit;         // SMs the persistent grid covers (0 = all)
     const uint8_t *heavy;     // per vertex: 1 = predicted heavy, splits every heavy_split_nodes (or null)
     uint32_t heavy_split_nodes;
+    uint32_t lp_hold_waiting; // waiting warps from which small subtrees stay with the whole warp (0 = 1)
 };
 
 // Words of the read-only part of a built subproblem with w local vertices of

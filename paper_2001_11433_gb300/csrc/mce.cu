@@ -519,6 +519,7 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
         P.split = o->split;
         P.split_nodes = o->split ? (o->split_nodes ? o->split_nodes : 4096u) : 0u;
         P.sm_limit = o->sm_limit;
+        P.lp_hold_waiting = o->lane_hold_waiting;
         if (heavy.p && o->split) {
             P.heavy = heavy.as<uint8_t>();
             P.heavy_split_nodes = o->heavy_split_nodes ? o->heavy_split_nodes : 256u;
