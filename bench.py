@@ -695,7 +695,7 @@ def balance_stats(r):
             "endgame_ms": st[7] / 1e6, "pieces": st[4], "builds": st[3]}
 
 
-def measure_ranks(mce, steps=3, warmup=1, kinds=("degree", "degen", "triangle", "learned")):
+def measure_ranks(mce, steps=3, warmup=1, kinds=("degree", "degen", "triangle", "learned", "learned_split")):
     """Chung-Lu n = 1.7M (exponent 2.2, w_max 35,000, about 11M edges) plus
     200 planted cliques of size U[20, 60].  Per rank: rank time (RT) and
     enumeration time (ET), CUDA events inside the library, median of the timed
@@ -705,12 +705,18 @@ def measure_ranks(mce, steps=3, warmup=1, kinds=("degree", "degen", "triangle", 
     import graphgen
     w = graphgen.chung_lu_planted()
     g = mce.Graph(w.n, torch.from_numpy(w.u).cuda(), torch.from_numpy(w.v).cuda())
-    model, split_model, train = train_learned_model(mce) if "learned" in kinds else (None, None, None)
+    model, split_model, train = (train_learned_model(mce) if any(k.startswith("learned") for k in kinds)
+                                 else (None, None, None))
     out, ref = {}, None
     for kind in kinds:
-        # the learned configuration: the rank model's key, and the split model
-        # ordering the subproblems and marking predicted-heavy ones (Section 4.2)
-        kw = ({"rank": kind, "model": model, "split_model": split_model} if kind == "learned" else {"rank": kind})
+        # the learned configuration: the rank model's key (Section 4.2); the
+        # split model's heavy-subtree marking is measured beside it
+        kw = {"rank": kind}
+        if kind == "learned":
+            kw = {"rank": "learned", "model": model}
+        elif kind == "learned_split":
+            kw = {"rank": "learned", "model": model, "split_model": split_model, "heavy_nodes": 4096,
+                  "heavy_split_nodes": 256}
         runs = []
         for it in range(warmup + steps):
             r = mce.enumerate_cliques(g, **kw)

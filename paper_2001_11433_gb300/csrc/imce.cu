@@ -1419,7 +1419,8 @@ mce_status add_edges(imce_state *S, const int32_t *u, const int32_t *v, int64_t 
     const unsigned sub_blocks = (unsigned)num_sms() * 2;
     const int64_t sub_warps = (int64_t)sub_blocks * 8;
     MCE_TRY(scratch.alloc((size_t)sub_warps * 2 * kSubCap * kSubMaxWords * 8, s));
-    const int64_t claimed_cap = n_new * 4 + 1024;
+    // every claim takes an alive clique of the index, each at most once
+    const int64_t claimed_cap = S->idx.n_alive + 16;
     MCE_TRY(claimed.alloc((size_t)claimed_cap * 8, s));
     MCE_TRY(nclaimed.alloc(8, s));
     MCE_TRY(sstat.alloc(4, s));
