@@ -29,6 +29,7 @@ batch latency, per-batch latency against change size: key "c5_serving").
   python bench.py --workload serve     # IMCE serving loop, Chung-Lu 500k + 1M stream edges
   python bench.py --workload ranks     # Chung-Lu 1.7M + planted cliques: rank and enumeration
                                        # time per rank (degree, degeneracy, triangles, learned)
+  python bench.py --workload scaling   # search time against SMs covered; split on / off ablation
 
 Under torchrun every rank runs the same workload as an independent replica
 (the per-vertex subproblems need no exchange), the slowest
@@ -562,7 +563,26 @@ def measure_serve(mce, slots=4, load=0.7):
         "device_ms_total": float(sum(i.delta.ms for i in infos)), "gpu_launches": int(launches),
         "batch_latency": [{"edges": int(sizes[i]), "new": int(x.delta.new_count), "subsumed": int(x.delta.sub_count),
                            "device_ms": float(x.delta.ms)} for i, x in enumerate(sat_infos)],
+        "latency_vs_change": latency_vs_change([int(sizes[i]) for i in range(len(sizes))],
+                                               [int(x.delta.new_count + x.delta.sub_count) for x in sat_infos],
+                                               [float(x.delta.ms) for x in sat_infos]),
     }
+
+
+def latency_vs_change(edges, changes, ms):
+    """Device time of a batch against its size and its change |Λnew| + |Λdel|
+    (the analogue of the paper's latency-against-change-size figure): least-
+    squares line ms = a + b * x for each, with the correlation."""
+    out = {}
+    for name, x in (("per_edge", np.asarray(edges, float)), ("per_changed_clique", np.asarray(changes, float))):
+        y = np.asarray(ms, float)
+        if len(x) < 2 or np.ptp(x) == 0:
+            out[name] = None
+            continue
+        b, a = np.polyfit(x, y, 1)
+        out[name] = {"intercept_ms": float(a), "ms_per_1000": float(b * 1000.0),
+                     "correlation": float(np.corrcoef(x, y)[0, 1])}
+    return out
 
 
 def run_serve(args):
@@ -754,6 +774,48 @@ def run_ranks(args):
     print(json.dumps(line), flush=True)
 
 
+def run_scaling(args):
+    """Search time of the R-MAT 18 benchmark set against the number of SMs
+    the persistent grid covers (the analogue of the paper's thread-scaling
+    figures), and the split ablation (hand-over of subtrees on / off, the
+    PECO-style comparison of Section 4.2) on R-MAT 18 and on the Chung-Lu
+    1.7M graph (degree rank)."""
+    import torch
+    import graphgen
+    import paper_2001_11433_gb300 as mce
+    mce.load(build_if_missing=False)
+    props = torch.cuda.get_device_properties(0)
+    w = workload()
+    capped = capped_vertices()
+    keep = np.setdiff1d(np.arange(w.n, dtype=np.int32), capped if capped is not None else [])
+    g = mce.Graph(w.n, torch.from_numpy(w.u).cuda(), torch.from_numpy(w.v).cuda())
+    sub = torch.from_numpy(keep).cuda()
+
+    def timed(gr, reps=2, **kw):
+        rs = [mce.enumerate_cliques(gr, **kw) for _ in range(reps + 1)][1:]
+        r = min(rs, key=lambda x: x.ms_search)
+        return {"search_ms": r.ms_search, "enumerate_ms": r.ms_enum, "cliques": r.count, "hash": f"{r.hash:#018x}",
+                "tree_nodes": r.tree_nodes, "splits": r.tasks_split, **balance_stats(r)}
+
+    sms = props.multi_processor_count
+    scaling = {}
+    for k in (sms // 8, sms // 4, sms // 2, sms):
+        scaling[str(k)] = timed(g, rank="degen", subset=sub, blocks_per_sm=BLOCKS_PER_SM, split_nodes=SPLIT_NODES,
+                                sm_limit=k)
+        print(json.dumps({"sms": k, **scaling[str(k)]}), flush=True)
+    ablation = {"rmat18_split_on": scaling[str(sms)],
+                "rmat18_split_off": timed(g, reps=1, rank="degen", subset=sub, blocks_per_sm=BLOCKS_PER_SM, split=False)}
+    c3 = graphgen.chung_lu_planted()
+    g3 = mce.Graph(c3.n, torch.from_numpy(c3.u).cuda(), torch.from_numpy(c3.v).cuda())
+    ablation["chunglu_split_on"] = timed(g3, rank="degree")
+    ablation["chunglu_split_off"] = timed(g3, rank="degree", split=False)
+    line = {"metric": "search time against SMs covered, and the split ablation", "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"{w.name} benchmark set (degeneracy rank) and {c3.name} (degree rank)"},
+            "sm_scaling": scaling, "split_ablation": ablation}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -764,7 +826,7 @@ def main():
     ap.add_argument("--no-secondary", action="store_true",
                     help="rmat18: skip the Chung-Lu rank comparison and the serving loop after the timed region")
     ap.add_argument("--sample", type=float, default=1.0, help="rmat18: timed fraction of the subproblem set")
-    ap.add_argument("--workload", choices=["rmat18", "batched", "serve", "ranks"], default="rmat18")
+    ap.add_argument("--workload", choices=["rmat18", "batched", "serve", "ranks", "scaling"], default="rmat18")
     ap.add_argument("--blocks-per-sm", type=int, default=BLOCKS_PER_SM, help="rmat18: resident search blocks per SM")
     ap.add_argument("--lane-search-words", type=int, default=LANE_SEARCH_WORDS,
                     help="rmat18: per-warp shared words of the lane-parallel small search (0 = automatic)")
@@ -782,6 +844,8 @@ def main():
         run_serve(args)
     elif args.workload == "ranks":
         run_ranks(args)
+    elif args.workload == "scaling":
+        run_scaling(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -51,3 +51,13 @@ def test_cpu_sample_is_a_plain_prefix():
     k = len(s1)
     assert np.array_equal(np.sort(perm[:k]), s1)
     assert nodes[s1].sum() <= 50_000 < nodes[perm[:k + 1]].sum()
+
+
+def test_latency_vs_change_fit():
+    """The serving line's latency-against-change summary recovers a line."""
+    x = np.array([1000, 5000, 20000, 80000])
+    ms = 1.5 + 0.002 * x
+    out = bench.latency_vs_change(x.tolist(), (2 * x).tolist(), ms.tolist())
+    assert abs(out["per_edge"]["intercept_ms"] - 1.5) < 1e-9 and abs(out["per_edge"]["ms_per_1000"] - 2.0) < 1e-9
+    assert abs(out["per_changed_clique"]["ms_per_1000"] - 1.0) < 1e-9
+    assert out["per_edge"]["correlation"] > 0.999
