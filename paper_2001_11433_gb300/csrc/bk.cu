@@ -1311,6 +1311,82 @@ __device__ __forceinline__ uint32_t lp_pivot_ext(const LpNode &u, LpSums &o) {
     return ext;
 }
 
+// Child N = K + q with two candidates a < b (fini cf, cx), settled in closed
+// form with the node counts, word operations and cliques of the search:
+//   - a fini vertex adjacent to both is the pivot (count 2): N has no child;
+//   - a ~ b: the pivot has count 1 and N has one child, whose one candidate
+//     gives the clique N + a + b (two more nodes);
+//   - a !~ b and a fini vertex adjacent to one of them: it is the pivot, and
+//     N's one child (the other candidate) is a leaf, a clique unless a fini
+//     vertex is adjacent to it;
+//   - otherwise every count is 0: both candidates are leaf children and both
+//     N + a and N + b are cliques.
+__device__ __forceinline__ void lp_two(const BkParams &P, unsigned long long *shist, const LpNode &u, int q, LpSums &o,
+                                       uint32_t cc, uint32_t cf, uint32_t cx, uint64_t hq) {
+    const int a = __ffs(cc) - 1, b = __ffs(cc & (cc - 1u)) - 1;
+    const uint2 ka = u.akC[a], kb = u.akC[b];
+    const uint32_t xa = u.adjXT[a], xb = u.adjXT[b];
+    const uint32_t t = 2u + (uint32_t)(__popc(cf) + __popc(cx));
+    const uint32_t sz = u.base + (uint32_t)u.depth + 1u;   // |N|
+    const uint64_t hn = u.hs + hq;                         // hash sum of N
+    ++o.nodes;                                             // N
+    if ((cf & ka.x & kb.x) != 0u || (cx & xa & xb) != 0u) {
+        o.wops += t;
+        return;
+    }
+    const uint32_t wt = 2u * ((t + 31u) >> 5);
+    const uint32_t f1c = cf & (ka.x ^ kb.x), f1x = cx & (xa ^ xb);   // fini adjacent to exactly one
+    // the fini member of f1 with the highest tie key, and whether it touches a
+    uint32_t fk = 0u;
+    bool f_on_a = false;
+    for (uint32_t m = f1c; m; m &= m - 1u) {
+        const int k = __ffs(m) - 1;
+        const uint32_t kk = u.akC[k].y;
+        if (kk >= fk) {
+            fk = kk + 1u;
+            f_on_a = (ka.x >> k) & 1u;
+        }
+    }
+    for (uint32_t m = f1x; m; m &= m - 1u) {
+        const int x = __ffs(m) - 1;
+        const uint32_t kk = u.akX[x].y;
+        if (kk >= fk) {
+            fk = kk + 1u;
+            f_on_a = (xa >> x) & 1u;
+        }
+    }
+    if ((ka.x >> b) & 1u) {
+        // a ~ b: pivot among a, b and f1 by tie key; the child is a if the pivot is
+        // a or a fini vertex on b only, else b
+        const uint32_t best = max(max(ka.y, kb.y) + 1u, fk);
+        int qq;
+        if (best == ka.y + 1u) qq = a;
+        else if (best == kb.y + 1u) qq = b;
+        else qq = f_on_a ? b : a;
+        const uint32_t rq = qq == a ? ka.x : kb.x, xq = qq == a ? xa : xb;
+        o.wops += t + wt;
+        const uint32_t tg = 1u + (uint32_t)(__popc(cf & rq) + __popc(cx & xq));
+        o.nodes += 2;
+        o.wops += tg + 2u * ((tg + 31u) >> 5);
+        lp_emit(P, shist, o, sz + 2u, hn + u.hC[a] + u.hC[b]);
+        return;
+    }
+    if (fk) {
+        // a !~ b: the pivot is the fini vertex; its other candidate is the child
+        const int qq = f_on_a ? b : a;
+        const uint32_t rq = qq == a ? ka.x : kb.x, xq = qq == a ? xa : xb;
+        o.wops += t + wt;
+        ++o.nodes;
+        if ((cf & rq) == 0u && (cx & xq) == 0u) lp_emit(P, shist, o, sz + 1u, hn + u.hC[qq]);
+        return;
+    }
+    // all counts 0: both candidates are children, both leaves and cliques
+    o.wops += t + 2u * wt;
+    o.nodes += 2;
+    lp_emit(P, shist, o, sz + 1u, hn + u.hC[a]);
+    lp_emit(P, shist, o, sz + 1u, hn + u.hC[b]);
+}
+
 // Child q of a node whose cand / finc already exclude / include q: leaves
 // and one-candidate children are settled here (returns false); otherwise the
 // child's sets are returned for a push (returns true).  Node counts and word
@@ -1341,6 +1417,10 @@ __device__ __forceinline__ bool lp_child(const BkParams &P, unsigned long long *
             o.wops += t + 2u * ((t + 31u) >> 5);
             lp_emit(P, shist, o, u.base + (uint32_t)u.depth + 2u, u.hs + hq + u.hC[c]);
         }
+        return false;
+    }
+    if (__popc(cc) == 2) {
+        lp_two(P, shist, u, q, o, cc, cf, cx, hq);
         return false;
     }
     ++o.nodes;

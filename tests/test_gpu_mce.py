@@ -433,7 +433,28 @@ def test_stream_rmat13_summary(gpu_lib):
         total[0] += len(off)
         total[1] += len(vtx)
 
-    r = mce.enumerate_stream(g, sink, buf_words=1 << 16, rank="degree")
+    r = mce.enumerate_stream(g, sink, buf_words=1 << 22, rank="degree")
     ref = mce.enumerate_cliques(g, rank="degree")
     assert (r.count, r.hash, list(r.hist), r.tree_nodes) == (ref.count, ref.hash, list(ref.hist), ref.tree_nodes)
     assert total[0] == r.count and total[1] == r.count + sum(i * int(c) for i, c in enumerate(r.hist))
+
+
+@pytest.mark.parametrize("rank", ["degen", "degree"])
+def test_lane_search_equals_warp_search(gpu_lib, rank):
+    """The lane-parallel small search (one small subtree per lane, closed
+    forms for one- and two-candidate children) and the whole-warp small
+    search visit the same trees: equal per-subproblem counts, hashes and node
+    counts, and equal algorithmic word operations."""
+    mce = gpu_lib
+    n, u, v = rmat(13, seed=8)
+    g = gpu_graph(mce, n, u, v)
+    outs = []
+    for warp in (False, True):
+        pv = per_vertex_bufs(n)
+        r = mce.enumerate_cliques(g, rank=rank, per_vertex=pv, warp_small_search=warp)
+        outs.append((r, [u64(t) for t in pv]))
+    (a, pa), (b, pb) = outs
+    assert (a.count, a.hash, list(a.hist), a.tree_nodes, a.word_ops) == \
+        (b.count, b.hash, list(b.hist), b.tree_nodes, b.word_ops)
+    for x, y in zip(pa, pb):
+        assert np.array_equal(x, y)
