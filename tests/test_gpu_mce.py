@@ -423,9 +423,9 @@ def test_stream_er2000_full_list(gpu_lib, buf_words):
         assert len(chunks) > 4
 
 
-def test_stream_rmat13_summary(gpu_lib):
+def test_stream_rmat12_summary(gpu_lib):
     mce = gpu_lib
-    n, u, v = rmat(13)
+    n, u, v = rmat(12)
     g = gpu_graph(mce, n, u, v)
     total = [0, 0]
 
@@ -433,7 +433,7 @@ def test_stream_rmat13_summary(gpu_lib):
         total[0] += len(off)
         total[1] += len(vtx)
 
-    r = mce.enumerate_stream(g, sink, buf_words=1 << 22, rank="degree")
+    r = mce.enumerate_stream(g, sink, buf_words=1 << 24, rank="degree")
     ref = mce.enumerate_cliques(g, rank="degree")
     assert (r.count, r.hash, list(r.hist), r.tree_nodes) == (ref.count, ref.hash, list(ref.hist), ref.tree_nodes)
     assert total[0] == r.count and total[1] == r.count + sum(i * int(c) for i, c in enumerate(r.hist))
