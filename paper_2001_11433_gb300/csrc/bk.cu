@@ -1256,39 +1256,24 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
 __device__ __forceinline__ int lp_universe_words(int cn, int xn) { return (5 * cn + 2 * xn + 1) & ~1; }
 
 struct LpSums {
-    unsigned long long hash;
-    uint32_t count, nodes, wops, smax;   // per phase (a phase is far below 2^32 nodes)
+    unsigned long long hash, wops;
+    uint32_t count, nodes, smax;
 };
 
-// The dynamic shared memory of the search block, seen from the lane-parallel
-// search: universes are addressed by word offsets into it (32-bit shared
-// addresses, no generic pointers).
-extern __shared__ __align__(16) uint32_t bk_smem[];
-
-// A small-subtree node for one lane: its universe (word offset uni and
-// meta = cn | xn << 8 | base << 16) and its state.
+// A small-subtree node for one lane: its universe and its state.
 struct LpNode {
-    uint32_t uni, meta;
+    const uint64_t *hC;
+    const uint2 *akC, *akX;   // (row, tie key) per C / X member
+    const uint32_t *adjXT;
+    int cn;
+    uint32_t base;     // clique size at the universe's root
     uint32_t cand, finc, xs;
     uint64_t hs;
     int depth;         // below the universe's root
-    __device__ __forceinline__ int cn() const { return (int)(meta & 0xffu); }
-    __device__ __forceinline__ int xn() const { return (int)((meta >> 8) & 0xffu); }
-    __device__ __forceinline__ uint32_t base() const { return meta >> 16; }
-    __device__ __forceinline__ uint64_t hC(int k) const {
-        return *reinterpret_cast<const uint64_t *>(&bk_smem[uni + 2 * k]);
-    }
-    __device__ __forceinline__ uint2 akC(int k) const {
-        return *reinterpret_cast<const uint2 *>(&bk_smem[uni + 2 * cn() + 2 * k]);
-    }
-    __device__ __forceinline__ uint2 akX(int x) const {
-        return *reinterpret_cast<const uint2 *>(&bk_smem[uni + 4 * cn() + 2 * x]);
-    }
-    __device__ __forceinline__ uint32_t adjXT(int k) const { return bk_smem[uni + 4 * cn() + 2 * xn() + k]; }
 };
 
-__device__ __forceinline__ void lp_emit(const BkParams &P, LpSums &o, uint32_t size, uint64_t hsum) {
-    unsigned long long *shist = reinterpret_cast<unsigned long long *>(bk_smem);
+__device__ __forceinline__ void lp_emit(const BkParams &P, unsigned long long *shist, LpSums &o, uint32_t size,
+                                        uint64_t hsum) {
     o.count++;
     o.hash += clique_hash_from_sum(hsum, size);
     o.wops += size;
@@ -1305,7 +1290,7 @@ __device__ __forceinline__ uint32_t lp_pivot_ext(const LpNode &u, LpSums &o) {
     const uint32_t cf = u.cand | u.finc;
     uint32_t best = 0u, badj = 0u;
     for (uint32_t m = cf; m; m &= m - 1u) {
-        const uint2 ak = u.akC(__ffs(m) - 1);
+        const uint2 ak = u.akC[__ffs(m) - 1];
         const uint32_t kk = ((uint32_t)(__popc(u.cand & ak.x) + 1) << 7) | ak.y;
         if (kk > best) {
             best = kk;
@@ -1313,7 +1298,7 @@ __device__ __forceinline__ uint32_t lp_pivot_ext(const LpNode &u, LpSums &o) {
         }
     }
     for (uint32_t m = u.xs; m; m &= m - 1u) {
-        const uint2 ak = u.akX(__ffs(m) - 1);
+        const uint2 ak = u.akX[__ffs(m) - 1];
         const uint32_t kk = ((uint32_t)(__popc(u.cand & ak.x) + 1) << 7) | ak.y;
         if (kk > best) {
             best = kk;
@@ -1336,27 +1321,27 @@ __device__ __forceinline__ uint32_t lp_pivot_ext(const LpNode &u, LpSums &o) {
 //     vertex is adjacent to it;
 //   - otherwise every count is 0: both candidates are leaf children and both
 //     N + a and N + b are cliques.
-__device__ __forceinline__ void lp_two(const BkParams &P, const LpNode &u, LpSums &o, uint32_t cc, uint32_t cf,
-                                       uint32_t cx, uint64_t hq) {
+__device__ __forceinline__ void lp_two(const BkParams &P, unsigned long long *shist, const LpNode &u, int q, LpSums &o,
+                                       uint32_t cc, uint32_t cf, uint32_t cx, uint64_t hq) {
     const int a = __ffs(cc) - 1, b = __ffs(cc & (cc - 1u)) - 1;
-    const uint2 ka = u.akC(a), kb = u.akC(b);
-    const uint32_t xa = u.adjXT(a), xb = u.adjXT(b);
+    const uint2 ka = u.akC[a], kb = u.akC[b];
+    const uint32_t xa = u.adjXT[a], xb = u.adjXT[b];
     const uint32_t t = 2u + (uint32_t)(__popc(cf) + __popc(cx));
-    const uint32_t sz = u.base() + (uint32_t)u.depth + 1u;   // |N|
-    const uint64_t hn = u.hs + hq;                           // hash sum of N
-    ++o.nodes;                                               // N
+    const uint32_t sz = u.base + (uint32_t)u.depth + 1u;   // |N|
+    const uint64_t hn = u.hs + hq;                         // hash sum of N
+    ++o.nodes;                                             // N
     if ((cf & ka.x & kb.x) != 0u || (cx & xa & xb) != 0u) {
         o.wops += t;
         return;
     }
     const uint32_t wt = 2u * ((t + 31u) >> 5);
     const uint32_t f1c = cf & (ka.x ^ kb.x), f1x = cx & (xa ^ xb);   // fini adjacent to exactly one
-    // the fini member of f1 with the highest tie key (+1; 0 = none), and whether it touches a
+    // the fini member of f1 with the highest tie key, and whether it touches a
     uint32_t fk = 0u;
     bool f_on_a = false;
     for (uint32_t m = f1c; m; m &= m - 1u) {
         const int k = __ffs(m) - 1;
-        const uint32_t kk = u.akC(k).y;
+        const uint32_t kk = u.akC[k].y;
         if (kk >= fk) {
             fk = kk + 1u;
             f_on_a = (ka.x >> k) & 1u;
@@ -1364,7 +1349,7 @@ __device__ __forceinline__ void lp_two(const BkParams &P, const LpNode &u, LpSum
     }
     for (uint32_t m = f1x; m; m &= m - 1u) {
         const int x = __ffs(m) - 1;
-        const uint32_t kk = u.akX(x).y;
+        const uint32_t kk = u.akX[x].y;
         if (kk >= fk) {
             fk = kk + 1u;
             f_on_a = (xa >> x) & 1u;
@@ -1383,7 +1368,7 @@ __device__ __forceinline__ void lp_two(const BkParams &P, const LpNode &u, LpSum
         const uint32_t tg = 1u + (uint32_t)(__popc(cf & rq) + __popc(cx & xq));
         o.nodes += 2;
         o.wops += tg + 2u * ((tg + 31u) >> 5);
-        lp_emit(P, o, sz + 2u, hn + u.hC(a) + u.hC(b));
+        lp_emit(P, shist, o, sz + 2u, hn + u.hC[a] + u.hC[b]);
         return;
     }
     if (fk) {
@@ -1392,31 +1377,31 @@ __device__ __forceinline__ void lp_two(const BkParams &P, const LpNode &u, LpSum
         const uint32_t rq = qq == a ? ka.x : kb.x, xq = qq == a ? xa : xb;
         o.wops += t + wt;
         ++o.nodes;
-        if ((cf & rq) == 0u && (cx & xq) == 0u) lp_emit(P, o, sz + 1u, hn + u.hC(qq));
+        if ((cf & rq) == 0u && (cx & xq) == 0u) lp_emit(P, shist, o, sz + 1u, hn + u.hC[qq]);
         return;
     }
     // all counts 0: both candidates are children, both leaves and cliques
     o.wops += t + 2u * wt;
     o.nodes += 2;
-    lp_emit(P, o, sz + 1u, hn + u.hC(a));
-    lp_emit(P, o, sz + 1u, hn + u.hC(b));
+    lp_emit(P, shist, o, sz + 1u, hn + u.hC[a]);
+    lp_emit(P, shist, o, sz + 1u, hn + u.hC[b]);
 }
 
-// Child q of a node whose cand / finc already exclude / include q: leaves,
-// one- and two-candidate children are settled here (returns false);
-// otherwise the child's sets are returned for a push (returns true).  Node
-// counts and word operations follow search_small.
-__device__ __forceinline__ bool lp_child(const BkParams &P, const LpNode &u, int q, LpSums &o, uint32_t &cc,
-                                         uint32_t &cf, uint32_t &cx, uint64_t &hq) {
-    const uint32_t aq = u.akC(q).x;
+// Child q of a node whose cand / finc already exclude / include q: leaves
+// and one-candidate children are settled here (returns false); otherwise the
+// child's sets are returned for a push (returns true).  Node counts and word
+// operations follow search_small.
+__device__ __forceinline__ bool lp_child(const BkParams &P, unsigned long long *shist, const LpNode &u, int q,
+                                         LpSums &o, uint32_t &cc, uint32_t &cf, uint32_t &cx, uint64_t &hq) {
+    const uint32_t aq = u.akC[q].x;
     cc = u.cand & aq;
     cf = u.finc & aq;
-    cx = u.xs & u.adjXT(q);
-    hq = u.hC(q);
+    cx = u.xs & u.adjXT[q];
+    hq = u.hC[q];
     if (cc == 0u) {
         // a leaf: a maximal clique unless fini is left
         ++o.nodes;
-        if ((cf | cx) == 0u) lp_emit(P, o, u.base() + (uint32_t)u.depth + 1u, u.hs + hq);
+        if ((cf | cx) == 0u) lp_emit(P, shist, o, u.base + (uint32_t)u.depth + 1u, u.hs + hq);
         return false;
     }
     if ((cc & (cc - 1u)) == 0u) {
@@ -1424,36 +1409,26 @@ __device__ __forceinline__ bool lp_child(const BkParams &P, const LpNode &u, int
         // vertex adjacent to c is the pivot (then no child)
         const int c = __ffs(cc) - 1;
         const uint32_t t = 1u + (uint32_t)(__popc(cf) + __popc(cx));
-        if ((cf & u.akC(c).x) != 0u || (cx & u.adjXT(c)) != 0u) {
+        if ((cf & u.akC[c].x) != 0u || (cx & u.adjXT[c]) != 0u) {
             ++o.nodes;
             o.wops += t;
         } else {
             o.nodes += 2;
             o.wops += t + 2u * ((t + 31u) >> 5);
-            lp_emit(P, o, u.base() + (uint32_t)u.depth + 2u, u.hs + hq + u.hC(c));
+            lp_emit(P, shist, o, u.base + (uint32_t)u.depth + 2u, u.hs + hq + u.hC[c]);
         }
         return false;
     }
     if (__popc(cc) == 2) {
-        lp_two(P, u, o, cc, cf, cx, hq);
+        lp_two(P, shist, u, q, o, cc, cf, cx, hq);
         return false;
     }
     ++o.nodes;
     return true;
 }
 
-__device__ __forceinline__ void lp_add(LpSums &o, const LpSums &r) {
-    o.hash += r.hash;
-    o.count += r.count;
-    o.nodes += r.nodes;
-    o.wops += r.wops;
-    o.smax = max(o.smax, r.smax);
-}
-
-// The whole subtree below an entered-but-not-yet-pivoted node, depth first
-// (a function of its own: its loop gets the registers to itself).
-__device__ __noinline__ LpSums lp_dfs(const BkParams &P, LpNode u) {
-    LpSums o = {0ULL, 0u, 0u, 0u, 0u};
+// The whole subtree below an entered-but-not-yet-pivoted node, depth first.
+__device__ void lp_dfs(const BkParams &P, unsigned long long *shist, LpNode u, LpSums &o) {
     uint32_t stk[32 * 5];   // frames: cand, finc, xs, ext, q (a frame adds a distinct candidate: depth < 31)
     const int d0 = u.depth;
     uint32_t ext = 0u;
@@ -1461,7 +1436,7 @@ __device__ __noinline__ LpSums lp_dfs(const BkParams &P, LpNode u) {
     for (;;) {
         if (enter) {
             if (u.cand == 0u) {
-                if ((u.finc | u.xs) == 0u) lp_emit(P, o, u.base() + (uint32_t)u.depth, u.hs);
+                if ((u.finc | u.xs) == 0u) lp_emit(P, shist, o, u.base + (uint32_t)u.depth, u.hs);
                 goto lpop;
             }
             ext = lp_pivot_ext(u, o);
@@ -1476,7 +1451,7 @@ __device__ __noinline__ LpSums lp_dfs(const BkParams &P, LpNode u) {
             u.finc |= qb;
             uint32_t cc, cf, cx;
             uint64_t hq;
-            if (!lp_child(P, u, q, o, cc, cf, cx, hq)) continue;
+            if (!lp_child(P, shist, u, q, o, cc, cf, cx, hq)) continue;
             uint32_t *f = stk + 5 * (u.depth - d0);
             f[0] = u.cand;
             f[1] = u.finc;
@@ -1500,20 +1475,25 @@ __device__ __noinline__ LpSums lp_dfs(const BkParams &P, LpNode u) {
             u.finc = f[1];
             u.xs = f[2];
             ext = f[3];
-            u.hs -= u.hC((int)f[4]);
+            u.hs -= u.hC[f[4]];
         }
     }
-    return o;
 }
 
-// lp: word offset of the warp's region (root table, then the arena)
-__device__ __forceinline__ LpNode lp_root_node(uint32_t lp, int r) {
-    const uint32_t *rec = &bk_smem[lp + 4 * r];
+__device__ __forceinline__ LpNode lp_root_node(const uint32_t *lp, int r) {
+    const uint32_t *rec = lp + 4 * r;
+    const uint32_t meta = rec[1];
     LpNode u;
-    u.uni = lp + BK_LP_TABLE_WORDS + rec[0];
-    u.meta = rec[1];
-    u.cand = u.cn() == 32 ? FULL : ((1u << u.cn()) - 1u);
-    u.xs = u.xn() == 32 ? FULL : ((1u << u.xn()) - 1u);
+    u.cn = (int)(meta & 0xffu);
+    const int xn = (int)((meta >> 8) & 0xffu);
+    u.base = meta >> 16;
+    const uint32_t *uni = lp + BK_LP_TABLE_WORDS + rec[0];
+    u.hC = reinterpret_cast<const uint64_t *>(uni);
+    u.akC = reinterpret_cast<const uint2 *>(uni + 2 * u.cn);
+    u.akX = reinterpret_cast<const uint2 *>(uni + 4 * u.cn);
+    u.adjXT = uni + 4 * u.cn + 2 * xn;
+    u.cand = u.cn == 32 ? FULL : ((1u << u.cn) - 1u);
+    u.xs = xn == 32 ? FULL : ((1u << xn) - 1u);
     u.finc = 0u;
     u.hs = (uint64_t)rec[2] | ((uint64_t)rec[3] << 32);
     u.depth = 0;
@@ -1529,7 +1509,7 @@ __device__ __forceinline__ void lp_task_put(uint32_t *t, int r, const LpNode &u)
     t[5] = (uint32_t)(u.hs >> 32);
 }
 
-__device__ __forceinline__ LpNode lp_task_get(uint32_t lp, const uint32_t *t) {
+__device__ __forceinline__ LpNode lp_task_get(const uint32_t *lp, const uint32_t *t) {
     LpNode u = lp_root_node(lp, (int)(t[0] & 0xffu));
     u.depth = (int)(t[0] >> 8);
     u.cand = t[1];
@@ -1540,11 +1520,12 @@ __device__ __forceinline__ LpNode lp_task_get(uint32_t lp, const uint32_t *t) {
 }
 
 // Enter node u and put its non-trivial children into the list `dst` (leaves
-// and one- and two-candidate children are settled at once); a child that
-// finds the list full is searched here instead.
-__device__ void lp_expand(const BkParams &P, LpNode u, int r, LpSums &o, uint32_t *dst, uint32_t *dst_n) {
+// and one-candidate children are settled at once); a child that finds the
+// list full is searched here instead.
+__device__ void lp_expand(const BkParams &P, unsigned long long *shist, LpNode u, int r, LpSums &o, uint32_t *dst,
+                          uint32_t *dst_n) {
     if (u.cand == 0u) {
-        if ((u.finc | u.xs) == 0u) lp_emit(P, o, u.base() + (uint32_t)u.depth, u.hs);
+        if ((u.finc | u.xs) == 0u) lp_emit(P, shist, o, u.base + (uint32_t)u.depth, u.hs);
         return;
     }
     uint32_t ext = lp_pivot_ext(u, o);
@@ -1556,7 +1537,7 @@ __device__ void lp_expand(const BkParams &P, LpNode u, int r, LpSums &o, uint32_
         u.finc |= qb;
         uint32_t cc, cf, cx;
         uint64_t hq;
-        if (!lp_child(P, u, q, o, cc, cf, cx, hq)) continue;
+        if (!lp_child(P, shist, u, q, o, cc, cf, cx, hq)) continue;
         LpNode c = u;
         c.cand = cc;
         c.finc = cf;
@@ -1565,21 +1546,22 @@ __device__ void lp_expand(const BkParams &P, LpNode u, int r, LpSums &o, uint32_
         c.depth = u.depth + 1;
         const uint32_t slot = atomicAdd(dst_n, 1u);
         if (slot < (uint32_t)P.lp_task_cap) lp_task_put(dst + (int64_t)slot * BK_LP_TASK_WORDS, r, c);
-        else lp_add(o, lp_dfs(P, c));
+        else lp_dfs(P, shist, c, o);
     }
 }
 
 // The buffered small subtrees, one lane per task.  The roots are expanded
 // breadth first (one level, and up to two more while the tasks number fewer
-// than eight per lane) so that the heavy-tailed subtree sizes spread over the
-// lanes; the last list is then taken task by task, each searched depth first.
-__device__ __noinline__ LpSums lp_run(const BkParams &P, uint32_t lp, int nroots, uint32_t *tasks, int lane) {
-    LpSums o = {0ULL, 0u, 0u, 0u, 0u};
-    uint32_t *ctr = &bk_smem[lp + BK_LP_MAX_ROOTS * 4];   // [0] list A size, [1] list B size, [2] next task
+// than eight per lane) so that the heavy-tailed subtree sizes spread over the lanes;
+// the last list is then taken task by task, each searched depth first.
+__device__ __noinline__ LpSums lp_run(const BkParams &P, uint32_t *lp, int nroots, unsigned long long *shist,
+                                      uint32_t *tasks, int lane) {
+    LpSums o = {0ULL, 0ULL, 0u, 0u, 0u};
+    uint32_t *ctr = lp + BK_LP_MAX_ROOTS * 4;   // [0] list A size, [1] list B size, [2] next task
     uint32_t *la = tasks, *lb = tasks + (int64_t)P.lp_task_cap * BK_LP_TASK_WORDS;
     if (lane == 0) ctr[0] = ctr[1] = ctr[2] = 0u;
     __syncwarp();
-    for (int r = lane; r < nroots; r += 32) lp_expand(P, lp_root_node(lp, r), r, o, la, &ctr[0]);
+    for (int r = lane; r < nroots; r += 32) lp_expand(P, shist, lp_root_node(lp, r), r, o, la, &ctr[0]);
     __syncwarp();
     uint32_t n = min(ctr[0], (uint32_t)P.lp_task_cap);
     uint32_t *list = la, *other = lb;
@@ -1589,7 +1571,7 @@ __device__ __noinline__ LpSums lp_run(const BkParams &P, uint32_t lp, int nroots
         __syncwarp();
         for (uint32_t i = (uint32_t)lane; i < n; i += 32u) {
             const uint32_t *t = list + (int64_t)i * BK_LP_TASK_WORDS;
-            lp_expand(P, lp_task_get(lp, t), (int)(t[0] & 0xffu), o, other, &ctr[1]);
+            lp_expand(P, shist, lp_task_get(lp, t), (int)(t[0] & 0xffu), o, other, &ctr[1]);
         }
         __syncwarp();
         n = min(ctr[1], (uint32_t)P.lp_task_cap);
@@ -1599,7 +1581,7 @@ __device__ __noinline__ LpSums lp_run(const BkParams &P, uint32_t lp, int nroots
     }
     for (uint32_t i = atomicAdd(&ctr[2], 1u); i < n; i = atomicAdd(&ctr[2], 1u)) {
         const uint32_t *t = list + (int64_t)i * BK_LP_TASK_WORDS;
-        lp_add(o, lp_dfs(P, lp_task_get(lp, t)));
+        lp_dfs(P, shist, lp_task_get(lp, t), o);
     }
     __syncwarp();
     return o;
@@ -1609,8 +1591,8 @@ __device__ __noinline__ LpSums lp_run(const BkParams &P, uint32_t lp, int nroots
 __device__ void lp_flush(const BkParams &P, Ws &s, Acc &acc, unsigned long long *shist, int lane, int &node_tick) {
     if (s.lp_n == 0) return;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const LpSums r = lp_run(P, (uint32_t)(s.lp - bk_smem), s.lp_n,
-                            P.lp_tasks + gwarp * 2 * (int64_t)P.lp_task_cap * BK_LP_TASK_WORDS, lane);
+    const LpSums r = lp_run(P, s.lp, s.lp_n, shist, P.lp_tasks + gwarp * 2 * (int64_t)P.lp_task_cap * BK_LP_TASK_WORDS,
+                            lane);
     unsigned long long cnt = r.count, nodes = r.nodes, hsh = r.hash, wops = r.wops;
     uint32_t smax = r.smax;
     for (int o = 16; o; o >>= 1) {
@@ -2277,7 +2259,7 @@ __global__ void k_init_seq(unsigned long long *seq, int64_t n) {
 
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) k_bk(BkParams P) {
-    uint32_t *smem = bk_smem;
+    extern __shared__ __align__(16) uint32_t smem[];
     unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);   // 256 bins
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw_block = blockDim.x >> 5;
