@@ -155,14 +155,35 @@ K_BK_TRAFFIC = {"bytes": 80_302_848 + 119_014_400, "tree_nodes": 437_700_333,
                            "bk.cuh": "4f0536c7e58b1fa2d93c8fbfb6d1239c9d7f1ea953402c032d8caea9ecda0be9"}}
 
 
-def k_bk_traffic(tree_nodes: int):
+def _same_sources(digests) -> bool:
     import hashlib
     csrc = os.path.join(ROOT, "paper_2001_11433_gb300", "csrc")
-    for name, digest in K_BK_TRAFFIC["sha256"].items():
+    for name, digest in digests.items():
         with open(os.path.join(csrc, name), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != digest:
-                return None        # the kernel changed since the counters were taken
+                return False       # the kernel changed since the counters were taken
+    return True
+
+
+def k_bk_traffic(tree_nodes: int):
+    if not _same_sources(K_BK_TRAFFIC["sha256"]):
+        return None
     return K_BK_TRAFFIC["bytes"] * tree_nodes / K_BK_TRAFFIC["tree_nodes"]
+
+
+def issue_roofline(tree_nodes: int, kernel_s: float, sms: int, sm_mhz: float):
+    """Issue-rate roofline of the search kernel: warp instructions per tree
+    node (from the ncu capture K_BK_TRAFFIC was taken with) times the tree
+    nodes per second, against 4 schedulers x SMs x clock (one warp
+    instruction per scheduler per clock)."""
+    if not _same_sources(K_BK_TRAFFIC["sha256"]) or kernel_s <= 0:
+        return None
+    per_node = K_BK_TRAFFIC["warp_inst"] / K_BK_TRAFFIC["tree_nodes"]
+    achieved = per_node * tree_nodes / kernel_s
+    peak = 4 * sms * sm_mhz * 1e6
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak, "warp_inst_per_tree_node": per_node,
+            "peak_source": f"4 schedulers x {sms} SMs x {sm_mhz:.0f} MHz"}
 CPU_NODE_BUDGET = 2_000_000   # tree nodes of the subproblem sample the CPU baseline times
 
 
@@ -424,6 +445,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 8 * (16 + 1024) + 8 * 8},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "issue_roofline": issue_roofline(res.tree_nodes, kern_s, props.multi_processor_count, sm_mhz),
         "cpu_baseline": cpu,
         "capped_set_matches_oracle": capped_match,
         "balance": balance_stats(res),
