@@ -258,6 +258,232 @@ __global__ void k_index_rehash(const int32_t *pool, const int64_t *off, int64_t 
 
 // ------------------------------------------------------------------ Algorithm 8
 
+constexpr int kEpBits = MCE_HIST_CAP;   // cliques up to this size take the split loop
+constexpr int kSubMaxEdges = 512;       // batch edges inside one clique taken by the split loop
+
+// Batch edges inside the clique cv[0..s) (sorted, s <= kEpBits), one warp:
+// edges[] gets them as position pairs (i < j, lexicographic order; the first
+// kSubMaxEdges are kept) and ep[] the bitmap of their endpoints' positions.
+// Returns the number of such edges.
+__device__ int clique_batch_edges(const int32_t *cv, int32_t s, const int32_t *h_ptr, const int32_t *h_adj,
+                                  int32_t *edges, uint32_t *ep, int lane) {
+    const int sw = (s + 31) >> 5;
+    for (int k = lane; k < sw; k += 32) ep[k] = 0u;
+    __syncwarp();
+    int ne = 0;
+    for (int i = 0; i < s; ++i) {
+        const int32_t a = cv[i];
+        const int32_t h0 = h_ptr[a], hd = h_ptr[a + 1] - h0;
+        for (int t0 = 0; t0 < hd; t0 += 32) {
+            int j = -1;
+            if (t0 + lane < hd) {
+                const int32_t y = h_adj[h0 + t0 + lane];
+                if (y > a) {
+                    const int p = lower_bound_i32(cv, s, y);
+                    if (p < s && cv[p] == y) j = p;
+                }
+            }
+            const uint32_t b = __ballot_sync(FULL, j >= 0);
+            // h_adj rows are sorted, so positions j come out ascending
+            if (j >= 0) {
+                const int slot = ne + __popc(b & lanemask_lt());
+                if (slot < kSubMaxEdges) {
+                    edges[2 * slot] = i;
+                    edges[2 * slot + 1] = j;
+                }
+                atomicOr(&ep[i >> 5], 1u << (i & 31));
+                atomicOr(&ep[j >> 5], 1u << (j & 31));
+            }
+            ne += __popc(b);
+        }
+    }
+    __syncwarp();
+    return ne;
+}
+
+// number of endpoints (set bits of ep over s positions), one warp
+__device__ __forceinline__ int count_endpoints(const uint32_t *ep, int32_t s, int lane) {
+    int nr = 0;
+    for (int k = lane; k < ((s + 31) >> 5); k += 32) nr += __popc(ep[k]);
+    return __reduce_add_sync(FULL, nr);
+}
+
+// R index (rank among the endpoints) of endpoint position p
+__device__ __forceinline__ int endpoint_index(const uint32_t *ep, int p) {
+    int r = 0;
+    for (int k = 0; k < (p >> 5); ++k) r += __popc(ep[k]);
+    return r + __popc(ep[p >> 5] & ((1u << (p & 31)) - 1u));
+}
+
+// Sum of h(v) over the core (positions that are no endpoint), one warp
+__device__ __forceinline__ uint64_t core_hash_sum(const int32_t *cv, int32_t s, const uint32_t *ep, uint64_t seed,
+                                                  int lane) {
+    uint64_t h = 0;
+    for (int p = lane; p < s; p += 32)
+        if (!((ep[p >> 5] >> (p & 31)) & 1u)) h += vertex_hash(cv[p], seed);
+    for (int o = 16; o; o >>= 1) h += __shfl_xor_sync(FULL, h, o);
+    return h;
+}
+
+// Algorithm 8's split set over the endpoints' R indices, one warp: S starts
+// as {c} (all nr endpoints); each edge (ei, ej) in turn replaces every member
+// holding both ends by that member without ei and that member without ej,
+// and S keeps the first occurrence of each set.  edges[] holds R indices.
+// Returns |S| (masks of kSubMaxWords words in S), or -1 when S would pass
+// kSubCap members.
+__device__ int split_set(const int32_t *edges, int ne, int nr, unsigned long long *S, unsigned long long *S2,
+                         int lane) {
+    constexpr int MW = kSubMaxWords;
+    int ns = 1;
+    if (lane < MW) {
+        const int lo = lane * 64;
+        const int nb = nr - lo;
+        S[lane] = nb >= 64 ? ~0ULL : (nb > 0 ? ((1ULL << nb) - 1) : 0ULL);
+    }
+    __syncwarp();
+    for (int e = 0; e < ne; ++e) {
+        const int ei = edges[2 * e], ej = edges[2 * e + 1];
+        const int wi = ei >> 6, wj = ej >> 6;
+        const unsigned long long bi = 1ULL << (ei & 63), bj = 1ULL << (ej & 63);
+        int n2 = 0;
+        for (int t0 = 0; t0 < ns; t0 += 32) {
+            const int t = t0 + lane;
+            bool both = false, valid = t < ns;
+            unsigned long long m[MW];
+            if (valid) {
+#pragma unroll
+                for (int w = 0; w < MW; ++w) m[w] = S[(int64_t)t * MW + w];
+                both = (m[wi] & bi) && (m[wj] & bj);
+            }
+            const uint32_t bb = __ballot_sync(FULL, valid && both);
+            const uint32_t bv = __ballot_sync(FULL, valid);
+            // outputs: 2 for split ones, 1 otherwise
+            const int before = 2 * __popc(bb & lanemask_lt()) + __popc(bv & ~bb & lanemask_lt());
+            const int total = 2 * __popc(bb) + __popc(bv & ~bb);
+            if (n2 + total > kSubCap) return -1;
+            if (valid) {
+                unsigned long long *d0 = S2 + (int64_t)(n2 + before) * MW;
+                if (both) {
+#pragma unroll
+                    for (int w = 0; w < MW; ++w) {
+                        d0[w] = m[w] & ~(w == wi ? bi : 0ULL);
+                        d0[MW + w] = m[w] & ~(w == wj ? bj : 0ULL);
+                    }
+                } else {
+#pragma unroll
+                    for (int w = 0; w < MW; ++w) d0[w] = m[w];
+                }
+            }
+            n2 += total;
+        }
+        __syncwarp();
+        // S = set of S2 (drop repeats, keep first occurrences)
+        ns = 0;
+        for (int t = 0; t < n2; ++t) {
+            const unsigned long long *cand = S2 + (int64_t)t * MW;
+            bool dup = false;
+            for (int q0 = 0; q0 < ns && !dup; q0 += 32) {
+                const int q = q0 + lane;
+                bool eq = false;
+                if (q < ns) {
+                    eq = true;
+#pragma unroll
+                    for (int w = 0; w < MW; ++w) eq &= S[(int64_t)q * MW + w] == cand[w];
+                }
+                dup = __any_sync(FULL, eq);
+            }
+            if (!dup) {
+                if (lane < MW) S[(int64_t)ns * MW + lane] = cand[lane];
+                ++ns;
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+    }
+    return ns;
+}
+
+// Hash and size of split candidate m: the core's (hcore, s - nr) plus its endpoints
+__device__ __forceinline__ uint64_t split_cand_hash(const int32_t *cv, int32_t s, const uint32_t *ep, int nr,
+                                                   const unsigned long long *m, uint64_t hcore, uint64_t seed,
+                                                   int32_t &size) {
+    uint64_t hs = hcore;
+    size = s - nr;
+    int r = 0;
+    for (int p = 0; p < s; ++p) {
+        if (!((ep[p >> 5] >> (p & 31)) & 1u)) continue;
+        if ((m[r >> 6] >> (r & 63)) & 1ULL) {
+            hs += vertex_hash(cv[p], seed);
+            ++size;
+        }
+        ++r;
+    }
+    return clique_hash_from_sum(hs, (uint32_t)size);
+}
+
+// Members of a split candidate: every position of c that is no endpoint (the
+// core), and the endpoints whose R index is set in the mask m.
+struct SplitMembers {
+    const int32_t *cv;
+    int32_t s;
+    const uint32_t *ep;
+    const unsigned long long *m;
+    // f(v) for each member v in ascending order while f returns true
+    template <class F> __device__ bool each(F f) const {
+        int r = 0;
+        for (int p = 0; p < s; ++p) {
+            if ((ep[p >> 5] >> (p & 31)) & 1u) {
+                const bool in = (m[r >> 6] >> (r & 63)) & 1ULL;
+                ++r;
+                if (!in) continue;
+            }
+            if (!f(cv[p])) return false;
+        }
+        return true;
+    }
+    __device__ bool has_pos(int p) const {
+        if (!((ep[p >> 5] >> (p & 31)) & 1u)) return true;
+        const int r = endpoint_index(ep, p);
+        return (m[r >> 6] >> (r & 63)) & 1ULL;
+    }
+};
+
+// Members core ∪ {cv[rpos[r]] : r ∈ K}, rpos = the endpoints' positions, ascending
+struct RposMembers {
+    const int32_t *cv;
+    int32_t s;
+    const int32_t *rpos;
+    int32_t nr;
+    const unsigned long long *K;
+    template <class F> __device__ bool each(F f) const {
+        int r = 0;
+        for (int p = 0; p < s; ++p) {
+            if (r < nr && rpos[r] == p) {
+                const bool in = (K[r >> 6] >> (r & 63)) & 1ULL;
+                ++r;
+                if (!in) continue;
+            }
+            if (!f(cv[p])) return false;
+        }
+        return true;
+    }
+    __device__ bool has_pos(int p) const {
+        int lo = 0, hi = nr;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (rpos[mid] < p) lo = mid + 1; else hi = mid;
+        }
+        if (lo == nr || rpos[lo] != p) return true;
+        return (K[lo >> 6] >> (lo & 63)) & 1ULL;
+    }
+};
+
+// are the members, ascending, the sorted list a (of their number of entries)?
+template <class M> __device__ __forceinline__ bool members_equal(const M &mem, const int32_t *a) {
+    int k = 0;
+    return mem.each([&](int32_t v) { return a[k++] == v; });
+}
+
 struct SubParams {
     const int64_t *noff;      // new cliques (sorted lists)
     const int32_t *nvtx;
@@ -284,22 +510,6 @@ struct SubParams {
     unsigned long long *bk_scratch;   // fallback: per thread kBkWords words
 };
 
-// The members of a split candidate: every position of c that is no endpoint
-// of a new edge inside c (the core), and the endpoints whose R index is set
-// in the mask (ep: bitmap of endpoint positions).
-struct SubCand {
-    const int32_t *cv;
-    int32_t s;
-    const uint32_t *ep;
-    const unsigned long long *m;
-    __device__ __forceinline__ bool member(int p, int &r) const {
-        if (!((ep[p >> 5] >> (p & 31)) & 1u)) return true;
-        const bool in = (m[r >> 6] >> (r & 63)) & 1ULL;
-        ++r;
-        return in;
-    }
-};
-
 // Probe the index for the candidate (hash h, size) and claim it if alive;
 // the index keeps dead entries (a clique that died and was created again
 // after an edge deletion has a later alive copy).  Reports a claim.
@@ -312,7 +522,7 @@ __device__ void sub_probe_claim(const SubParams &P, uint64_t h, int32_t size, co
         if (P.tkey[slot] == h) {
             const int32_t *pl = P.pool + P.off[id1 - 1];
             bool eq = pl[0] == size;
-            if (eq) eq = mem.equal(pl + 1);
+            if (eq) eq = members_equal(mem, pl + 1);
             if (eq && atomicCAS(&P.alive[id1 - 1], 1, 0) == 1) {
                 found = id1 - 1;
                 break;
@@ -340,23 +550,14 @@ __device__ void sub_probe_claim(const SubParams &P, uint64_t h, int32_t size, co
     }
 }
 
-struct MaskMembers {
-    SubCand c;
-    __device__ bool equal(const int32_t *sorted) const {
-        int k = 0, r = 0;
-        for (int p = 0; p < c.s; ++p)
-            if (c.member(p, r) && sorted[k++] != c.cv[p]) return false;
-        return true;
-    }
-};
-
 // One warp per new clique c: E(c) ∩ H in lexicographic order, then S is
 // refined edge by edge (c' containing both endpoints is replaced by c' \ {u}
 // and c' \ {v}); S stays a set.  Every c' ∈ S found alive in the index is
-// claimed once and reported (Algorithm 8, lines 13-16).  Vertices of c that
-// are no endpoint of a new edge inside c belong to every candidate, so the
-// masks run over the endpoints only (at most 256).  A clique with more than
-// 512 new edges inside, or whose S outgrows kSubCap, goes to k_imce_sub_bk.
+// claimed once and reported (Algorithm 8).  Vertices of c that are no
+// endpoint of a new edge inside c belong to every candidate, so the masks run
+// over the endpoints only (at most 256).  A clique larger than kEpBits, with
+// more than kSubMaxEdges new edges inside, or whose S outgrows kSubCap goes
+// to k_imce_sub_bk.
 __global__ void __launch_bounds__(256) k_imce_sub(SubParams P) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -365,142 +566,33 @@ __global__ void __launch_bounds__(256) k_imce_sub(SubParams P) {
     constexpr int MW = kSubMaxWords;
     unsigned long long *S = P.scratch + gw * (int64_t)2 * kSubCap * MW;
     unsigned long long *S2 = S + (int64_t)kSubCap * MW;
-    __shared__ int32_t edges_s[8][2 * 512];
-    __shared__ uint32_t ep_s[8][MCE_HIST_CAP / 32];
+    __shared__ int32_t edges_s[8][2 * kSubMaxEdges];
+    __shared__ uint32_t ep_s[8][kEpBits / 32];
     int32_t *edges = edges_s[wib];
     uint32_t *ep = ep_s[wib];
     for (int64_t c = gw; c < P.n_new; c += nw) {
         const int32_t *cv = P.nvtx + P.noff[c] + 1;
         const int32_t s = cv[-1];
-        const int sw = (s + 31) >> 5;
-        for (int k = lane; k < sw; k += 32) ep[k] = 0u;
-        __syncwarp();
-        // new edges inside c: (i, j) positions, i < j, lexicographic
-        int ne = 0;
-        for (int i = 0; i < s; ++i) {
-            const int32_t a = cv[i];
-            const int32_t h0 = P.h_ptr[a], hd = P.h_ptr[a + 1] - h0;
-            for (int t0 = 0; t0 < hd; t0 += 32) {
-                int j = -1;
-                if (t0 + lane < hd) {
-                    const int32_t y = P.h_adj[h0 + t0 + lane];
-                    if (y > a) {
-                        const int p = lower_bound_i32(cv, s, y);
-                        if (p < s && cv[p] == y) j = p;
-                    }
-                }
-                const uint32_t b = __ballot_sync(FULL, j >= 0);
-                // h_adj rows are sorted, so positions j come out ascending
-                if (j >= 0) {
-                    const int slot = ne + __popc(b & lanemask_lt());
-                    if (slot < 512) {
-                        edges[2 * slot] = i;
-                        edges[2 * slot + 1] = j;
-                    }
-                    atomicOr(&ep[i >> 5], 1u << (i & 31));
-                    atomicOr(&ep[j >> 5], 1u << (j & 31));
-                }
-                ne += __popc(b);
-            }
+        if (s > kEpBits) {
+            if (lane == 0) P.big[atomicAdd(P.n_big, 1ULL)] = c;
+            continue;
         }
-        __syncwarp();
-        int nr = 0;
-        for (int k = lane; k < sw; k += 32) nr += __popc(ep[k]);
-        nr = __reduce_add_sync(FULL, nr);
+        const int ne = clique_batch_edges(cv, s, P.h_ptr, P.h_adj, edges, ep, lane);
+        const int nr = count_endpoints(ep, s, lane);
         if (nr > 64 * MW) {
             if (lane == 0) atomicOr(P.status, 1);
             continue;
         }
-        if (ne > 512) {
+        if (ne > kSubMaxEdges) {
             if (lane == 0) P.big[atomicAdd(P.n_big, 1ULL)] = c;
             continue;
         }
-        // endpoint positions -> R indices (rank among the endpoints)
-        for (int e = lane; e < 2 * ne; e += 32) {
-            const int p = edges[e];
-            int r = 0;
-            for (int k = 0; k < (p >> 5); ++k) r += __popc(ep[k]);
-            edges[e] = r + __popc(ep[p >> 5] & ((1u << (p & 31)) - 1u));
-        }
-        // hash and size of the core
-        uint64_t hcore = 0;
-        for (int p = lane; p < s; p += 32)
-            if (!((ep[p >> 5] >> (p & 31)) & 1u)) hcore += vertex_hash(cv[p], P.seed);
-        for (int o = 16; o; o >>= 1) hcore += __shfl_xor_sync(FULL, hcore, o);
+        // endpoint positions -> R indices
+        for (int e = lane; e < 2 * ne; e += 32) edges[e] = endpoint_index(ep, edges[e]);
+        const uint64_t hcore = core_hash_sum(cv, s, ep, P.seed, lane);
         __syncwarp();
-        // S = {c}
-        int ns = 1;
-        if (lane < MW) {
-            const int lo = lane * 64;
-            const int nb = nr - lo;
-            S[lane] = nb >= 64 ? ~0ULL : (nb > 0 ? ((1ULL << nb) - 1) : 0ULL);
-        }
-        __syncwarp();
-        bool overflow = false;
-        for (int e = 0; e < ne && !overflow; ++e) {
-            const int ei = edges[2 * e], ej = edges[2 * e + 1];
-            const int wi = ei >> 6, wj = ej >> 6;
-            const unsigned long long bi = 1ULL << (ei & 63), bj = 1ULL << (ej & 63);
-            int n2 = 0;
-            for (int t0 = 0; t0 < ns; t0 += 32) {
-                const int t = t0 + lane;
-                bool both = false, valid = t < ns;
-                unsigned long long m[MW];
-                if (valid) {
-#pragma unroll
-                    for (int w = 0; w < MW; ++w) m[w] = S[(int64_t)t * MW + w];
-                    both = (m[wi] & bi) && (m[wj] & bj);
-                }
-                const uint32_t bb = __ballot_sync(FULL, valid && both);
-                const uint32_t bv = __ballot_sync(FULL, valid);
-                // outputs: 2 for split ones, 1 otherwise
-                const int before = 2 * __popc(bb & lanemask_lt()) + __popc(bv & ~bb & lanemask_lt());
-                const int total = 2 * __popc(bb) + __popc(bv & ~bb);
-                if (n2 + total > kSubCap) {
-                    overflow = true;
-                    break;
-                }
-                if (valid) {
-                    unsigned long long *d0 = S2 + (int64_t)(n2 + before) * MW;
-                    if (both) {
-#pragma unroll
-                        for (int w = 0; w < MW; ++w) {
-                            d0[w] = m[w] & ~(w == wi ? bi : 0ULL);
-                            d0[MW + w] = m[w] & ~(w == wj ? bj : 0ULL);
-                        }
-                    } else {
-#pragma unroll
-                        for (int w = 0; w < MW; ++w) d0[w] = m[w];
-                    }
-                }
-                n2 += total;
-            }
-            __syncwarp();
-            if (overflow) break;
-            // S = set of S2 (drop repeats, keep first occurrences)
-            ns = 0;
-            for (int t = 0; t < n2; ++t) {
-                const unsigned long long *cand = S2 + (int64_t)t * MW;
-                bool dup = false;
-                for (int q0 = 0; q0 < ns && !dup; q0 += 32) {
-                    const int q = q0 + lane;
-                    bool eq = false;
-                    if (q < ns) {
-                        eq = true;
-#pragma unroll
-                        for (int w = 0; w < MW; ++w) eq &= S[(int64_t)q * MW + w] == cand[w];
-                    }
-                    dup = __any_sync(FULL, eq);
-                }
-                if (!dup) {
-                    if (lane < MW) S[(int64_t)ns * MW + lane] = cand[lane];
-                    ++ns;
-                    __syncwarp();
-                }
-            }
-            __syncwarp();
-        }
-        if (overflow) {
+        const int ns = split_set(edges, ne, nr, S, S2, lane);
+        if (ns < 0) {
             if (lane == 0) P.big[atomicAdd(P.n_big, 1ULL)] = c;
             continue;
         }
@@ -509,52 +601,147 @@ __global__ void __launch_bounds__(256) k_imce_sub(SubParams P) {
             const int t = t0 + lane;
             if (t < ns) {
                 const unsigned long long *m = S + (int64_t)t * MW;
-                uint64_t hs = hcore;
-                int32_t size = s - nr;
-                int r = 0;
-                for (int p = 0; p < s; ++p) {
-                    if (!((ep[p >> 5] >> (p & 31)) & 1u)) continue;
-                    if ((m[r >> 6] >> (r & 63)) & 1ULL) {
-                        hs += vertex_hash(cv[p], P.seed);
-                        ++size;
-                    }
-                    ++r;
-                }
-                const MaskMembers mm{SubCand{cv, s, ep, m}};
-                sub_probe_claim(P, clique_hash_from_sum(hs, (uint32_t)size), size, mm);
+                int32_t size;
+                const uint64_t h = split_cand_hash(cv, s, ep, nr, m, hcore, P.seed, size);
+                sub_probe_claim(P, h, size, SplitMembers{cv, s, ep, m});
             }
         }
         __syncwarp();
     }
 }
 
-// Enumerating fallback of Algorithm 8 for a new clique whose split set S
-// would outgrow kSubCap (or that holds more than 512 new edges): the
-// candidates that can be old maximal cliques are exactly the maximal cliques
-// of G[c] (c without its new edges), which are the core of c plus a maximal
-// clique of G[R] on the endpoints R.  One thread per such clique enumerates
-// those with Bron-Kerbosch (Tomita pivot) on 256-bit sets and probes each.
-constexpr int kBkWords = 256 * 4 + 258 * 12;   // rows of G[R], then frames (cand, fini, ext)
+// Enumerating fallback of Algorithm 8, one thread per clique c: the split
+// candidates that can be maximal cliques (of the old graph for additions, of
+// G - H for deletions) are exactly the maximal cliques of c without its batch
+// edges, i.e. the core of c plus a maximal clique of the graph on the
+// endpoints R whose edges are the pairs that are no batch edge.  Those are
+// enumerated with Bron-Kerbosch (Tomita pivot) on 256-bit sets, and act(h,
+// size, members) is called for each.  Returns false when R has more than 256
+// vertices.
+constexpr int kBkWords = 256 * 4 + 258 * 12;   // rows of the graph on R, then frames (cand, fini, ext)
 
-struct BkMembers {
-    const int32_t *cv;
-    int32_t s;
-    const int32_t *rpos;   // position in c of each endpoint, ascending
-    int32_t nr;
-    const unsigned long long *q;   // the chosen endpoints (R indices)
-    __device__ bool equal(const int32_t *sorted) const {
-        int k = 0, r = 0;
-        for (int p = 0; p < s; ++p) {
-            bool in = true;
-            if (r < nr && rpos[r] == p) {
-                in = (q[r >> 6] >> (r & 63)) & 1ULL;
-                ++r;
-            }
-            if (in && sorted[k++] != cv[p]) return false;
+template <class Act>
+__device__ bool split_bk(const int32_t *cv, int32_t s, const int32_t *h_ptr, const int32_t *h_adj, uint64_t seed,
+                         unsigned long long *adj, unsigned long long *fr, int32_t *rpos, int32_t *qd, Act act) {
+    // endpoints of batch edges inside c, ascending position
+    int nr = 0;
+    for (int p = 0; p < s; ++p) {
+        const int32_t a = cv[p];
+        bool hit = false;
+        for (int32_t e = h_ptr[a]; e < h_ptr[a + 1] && !hit; ++e) {
+            const int q = lower_bound_i32(cv, s, h_adj[e]);
+            hit = q < s && cv[q] == h_adj[e];
         }
-        return true;
+        if (hit) {
+            if (nr == 256) return false;
+            rpos[nr++] = p;
+        }
     }
-};
+    // rows of the graph on R: every other endpoint not joined by a batch edge
+    for (int r = 0; r < nr; ++r) {
+        unsigned long long *row = adj + r * 4;
+        for (int w = 0; w < 4; ++w) {
+            const int lo = w * 64, nb = nr - lo;
+            row[w] = nb >= 64 ? ~0ULL : (nb > 0 ? ((1ULL << nb) - 1) : 0ULL);
+        }
+        row[r >> 6] &= ~(1ULL << (r & 63));
+        const int32_t a = cv[rpos[r]];
+        for (int32_t e = h_ptr[a]; e < h_ptr[a + 1]; ++e) {
+            const int q = lower_bound_i32(cv, s, h_adj[e]);
+            if (!(q < s && cv[q] == h_adj[e])) continue;
+            int lo = 0, hi = nr;   // R index of position q
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (rpos[mid] < q) lo = mid + 1; else hi = mid;
+            }
+            row[lo >> 6] &= ~(1ULL << (lo & 63));
+        }
+    }
+    uint64_t hcore = 0;
+    {
+        int r = 0;
+        for (int p = 0; p < s; ++p) {
+            if (r < nr && rpos[r] == p) {
+                ++r;
+                continue;
+            }
+            hcore += vertex_hash(cv[p], seed);
+        }
+    }
+    // Bron-Kerbosch over R: frame d = (cand, fini, ext) at depth d; K = chosen
+    unsigned long long K[4] = {0, 0, 0, 0};
+    int d = 0;
+    unsigned long long *f0 = fr;
+    for (int w = 0; w < 4; ++w) {
+        const int lo = w * 64, nb = nr - lo;
+        f0[w] = nb >= 64 ? ~0ULL : (nb > 0 ? ((1ULL << nb) - 1) : 0ULL);
+        f0[4 + w] = 0ULL;
+    }
+    bool enter = true;
+    for (;;) {
+        unsigned long long *f = fr + (int64_t)d * 12;
+        if (enter) {
+            bool any_c = false, any_f = false;
+            for (int w = 0; w < 4; ++w) {
+                any_c |= f[w] != 0ULL;
+                any_f |= f[4 + w] != 0ULL;
+            }
+            if (!any_c) {
+                if (!any_f) {
+                    uint64_t hs = hcore;
+                    int32_t size = s - nr;
+                    for (int w = 0; w < 4; ++w)
+                        for (unsigned long long x = K[w]; x; x &= x - 1) {
+                            hs += vertex_hash(cv[rpos[w * 64 + __ffsll((long long)x) - 1]], seed);
+                            ++size;
+                        }
+                    act(clique_hash_from_sum(hs, (uint32_t)size), size, RposMembers{cv, s, rpos, nr, K});
+                }
+                goto pop;
+            }
+            // pivot: the member of cand ∪ fini with most candidate neighbours
+            int best = -1, bc = -1;
+            for (int w = 0; w < 4; ++w)
+                for (unsigned long long x = f[w] | f[4 + w]; x; x &= x - 1) {
+                    const int u = w * 64 + __ffsll((long long)x) - 1;
+                    int cnt = 0;
+                    for (int v = 0; v < 4; ++v) cnt += __popcll(f[v] & adj[u * 4 + v]);
+                    if (cnt > bc) {
+                        bc = cnt;
+                        best = u;
+                    }
+                }
+            for (int w = 0; w < 4; ++w) f[8 + w] = f[w] & ~adj[best * 4 + w];
+            enter = false;
+        }
+        {
+            int q = -1;
+            for (int w = 0; w < 4 && q < 0; ++w)
+                if (f[8 + w]) q = w * 64 + __ffsll((long long)f[8 + w]) - 1;
+            if (q < 0) goto pop;
+            const unsigned long long qb = 1ULL << (q & 63);
+            f[8 + (q >> 6)] &= ~qb;
+            unsigned long long *g = f + 12;
+            for (int w = 0; w < 4; ++w) {
+                g[w] = f[w] & adj[q * 4 + w];
+                g[4 + w] = f[4 + w] & adj[q * 4 + w];
+            }
+            f[q >> 6] &= ~qb;
+            f[4 + (q >> 6)] |= qb;
+            K[q >> 6] |= qb;
+            qd[d] = q;
+            ++d;
+            enter = true;
+            continue;
+        }
+    pop:
+        if (d == 0) break;
+        --d;
+        K[qd[d] >> 6] &= ~(1ULL << (qd[d] & 63));
+        enter = false;
+    }
+    return true;
+}
 
 __global__ void k_imce_sub_bk(SubParams P, int64_t n_big) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -562,134 +749,14 @@ __global__ void k_imce_sub_bk(SubParams P, int64_t n_big) {
     unsigned long long *adj = P.bk_scratch + tid * (int64_t)kBkWords;   // 256 rows of 4 words
     unsigned long long *fr = adj + 256 * 4;                                // frames of 12 words
     int32_t rpos[256];
+    int32_t qd[258];
     for (int64_t bi = tid; bi < n_big; bi += nth) {
         const int64_t c = P.big[bi];
         const int32_t *cv = P.nvtx + P.noff[c] + 1;
         const int32_t s = cv[-1];
-        // endpoints of new edges inside c, ascending position
-        int nr = 0;
-        bool too_many = false;
-        for (int p = 0; p < s && !too_many; ++p) {
-            const int32_t a = cv[p];
-            bool hit = false;
-            for (int32_t e = P.h_ptr[a]; e < P.h_ptr[a + 1] && !hit; ++e) {
-                const int q = lower_bound_i32(cv, s, P.h_adj[e]);
-                hit = q < s && cv[q] == P.h_adj[e];
-            }
-            if (hit) {
-                if (nr == 256) too_many = true;
-                else rpos[nr++] = p;
-            }
-        }
-        if (too_many) {
-            atomicOr(P.status, 1);
-            continue;
-        }
-        // rows of G[R]: every other endpoint not joined by a new edge
-        for (int r = 0; r < nr; ++r) {
-            unsigned long long *row = adj + r * 4;
-            for (int w = 0; w < 4; ++w) {
-                const int lo = w * 64, nb = nr - lo;
-                row[w] = nb >= 64 ? ~0ULL : (nb > 0 ? ((1ULL << nb) - 1) : 0ULL);
-            }
-            row[r >> 6] &= ~(1ULL << (r & 63));
-            const int32_t a = cv[rpos[r]];
-            for (int32_t e = P.h_ptr[a]; e < P.h_ptr[a + 1]; ++e) {
-                const int q = lower_bound_i32(cv, s, P.h_adj[e]);
-                if (!(q < s && cv[q] == P.h_adj[e])) continue;
-                int lo = 0, hi = nr;   // R index of position q
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (rpos[mid] < q) lo = mid + 1; else hi = mid;
-                }
-                row[lo >> 6] &= ~(1ULL << (lo & 63));
-            }
-        }
-        uint64_t hcore = 0;
-        {
-            int r = 0;
-            for (int p = 0; p < s; ++p) {
-                if (r < nr && rpos[r] == p) {
-                    ++r;
-                    continue;
-                }
-                hcore += vertex_hash(cv[p], P.seed);
-            }
-        }
-        // Bron-Kerbosch over R: frame d = (cand, fini, ext) at depth d; K = chosen
-        unsigned long long K[4] = {0, 0, 0, 0};
-        int d = 0;
-        unsigned long long *f0 = fr;
-        for (int w = 0; w < 4; ++w) {
-            const int lo = w * 64, nb = nr - lo;
-            f0[w] = nb >= 64 ? ~0ULL : (nb > 0 ? ((1ULL << nb) - 1) : 0ULL);
-            f0[4 + w] = 0ULL;
-        }
-        bool enter = true;
-        int qd[258];
-        for (;;) {
-            unsigned long long *f = fr + (int64_t)d * 12;
-            if (enter) {
-                bool any_c = false, any_f = false;
-                for (int w = 0; w < 4; ++w) {
-                    any_c |= f[w] != 0ULL;
-                    any_f |= f[4 + w] != 0ULL;
-                }
-                if (!any_c) {
-                    if (!any_f) {
-                        uint64_t hs = hcore;
-                        int32_t size = s - nr;
-                        for (int w = 0; w < 4; ++w)
-                            for (unsigned long long x = K[w]; x; x &= x - 1) {
-                                hs += vertex_hash(cv[rpos[w * 64 + __ffsll((long long)x) - 1]], P.seed);
-                                ++size;
-                            }
-                        const BkMembers bm{cv, s, rpos, nr, K};
-                        sub_probe_claim(P, clique_hash_from_sum(hs, (uint32_t)size), size, bm);
-                    }
-                    goto pop;
-                }
-                // pivot: the member of cand ∪ fini with most candidate neighbours
-                int best = -1, bc = -1;
-                for (int w = 0; w < 4; ++w)
-                    for (unsigned long long x = f[w] | f[4 + w]; x; x &= x - 1) {
-                        const int u = w * 64 + __ffsll((long long)x) - 1;
-                        int cnt = 0;
-                        for (int v = 0; v < 4; ++v) cnt += __popcll(f[v] & adj[u * 4 + v]);
-                        if (cnt > bc) {
-                            bc = cnt;
-                            best = u;
-                        }
-                    }
-                for (int w = 0; w < 4; ++w) f[8 + w] = f[w] & ~adj[best * 4 + w];
-                enter = false;
-            }
-            {
-                int q = -1;
-                for (int w = 0; w < 4 && q < 0; ++w)
-                    if (f[8 + w]) q = w * 64 + __ffsll((long long)f[8 + w]) - 1;
-                if (q < 0) goto pop;
-                const unsigned long long qb = 1ULL << (q & 63);
-                f[8 + (q >> 6)] &= ~qb;
-                unsigned long long *g = f + 12;
-                for (int w = 0; w < 4; ++w) {
-                    g[w] = f[w] & adj[q * 4 + w];
-                    g[4 + w] = f[4 + w] & adj[q * 4 + w];
-                }
-                f[q >> 6] &= ~qb;
-                f[4 + (q >> 6)] |= qb;
-                K[q >> 6] |= qb;
-                qd[d] = q;
-                ++d;
-                enter = true;
-                continue;
-            }
-        pop:
-            if (d == 0) break;
-            --d;
-            K[qd[d] >> 6] &= ~(1ULL << (qd[d] & 63));
-            enter = false;
-        }
+        const bool ok = split_bk(cv, s, P.h_ptr, P.h_adj, P.seed, adj, fr, rpos, qd,
+                                 [&](uint64_t h, int32_t size, const RposMembers &mm) { sub_probe_claim(P, h, size, mm); });
+        if (!ok) atomicOr(P.status, 1);
     }
 }
 
@@ -726,31 +793,28 @@ __device__ __forceinline__ bool has_edge_csr(const int32_t *row_ptr, const int32
     return p < d && col[r0 + p] == b;
 }
 
-// The members of candidate m (bit j of the mask = cv[j]) form a maximal
-// clique of G (row_ptr, col) iff no vertex outside them is adjacent to all.
-__device__ bool cand_is_maximal(const int32_t *row_ptr, const int32_t *col, const int32_t *cv, int32_t s,
-                                const unsigned long long (&m)[kSubMaxWords]) {
+// Do the members (a subset of the clique cv[0..s)) form a maximal clique of
+// the graph (row_ptr, col)?  They are a clique there; it is maximal iff no
+// neighbour y of its member of least degree, outside it, is adjacent to all
+// of them.
+template <class M>
+__device__ bool is_maximal_in(const int32_t *row_ptr, const int32_t *col, const int32_t *cv, int32_t s,
+                              const M &mem) {
     int32_t best = -1, bd = 0x7fffffff;
-    for (int w = 0; w < kSubMaxWords; ++w)
-        for (unsigned long long x = m[w]; x; x &= x - 1) {
-            const int32_t v = cv[w * 64 + __ffsll((long long)x) - 1];
-            const int32_t dv = row_ptr[v + 1] - row_ptr[v];
-            if (dv < bd) {
-                bd = dv;
-                best = v;
-            }
+    mem.each([&](int32_t v) {
+        const int32_t dv = row_ptr[v + 1] - row_ptr[v];
+        if (dv < bd) {
+            bd = dv;
+            best = v;
         }
+        return true;
+    });
     if (best < 0) return false;
     for (int32_t e = row_ptr[best]; e < row_ptr[best + 1]; ++e) {
         const int32_t y = col[e];
         const int p = lower_bound_i32(cv, s, y);
-        if (p < s && cv[p] == y && ((m[p >> 6] >> (p & 63)) & 1ULL)) continue;   // a member
-        bool all = true;
-        for (int w = 0; w < kSubMaxWords && all; ++w)
-            for (unsigned long long x = m[w]; x && all; x &= x - 1) {
-                const int32_t v = cv[w * 64 + __ffsll((long long)x) - 1];
-                if (v != best && !has_edge_csr(row_ptr, col, y, v)) all = false;
-            }
+        if (p < s && cv[p] == y && mem.has_pos(p)) continue;   // a member
+        const bool all = mem.each([&](int32_t v) { return v == best || has_edge_csr(row_ptr, col, y, v); });
         if (all) return false;
     }
     return true;
@@ -764,238 +828,171 @@ struct DelParams {
     const int32_t *row_ptr, *col;   // G - H
     uint64_t seed;
     unsigned long long *scratch;   // per warp: 2 * kSubCap masks of kSubMaxWords words
-    // created cliques, each once: records (removed clique index, H(K), mask)
-    // and a table of record + 1 that keeps one record per distinct clique
-    int64_t *rec_c;
+    // created cliques, each once: records (H(K), member list [size, ids] in
+    // rec_pool) and a table of record + 1 that keeps one record per clique
     unsigned long long *rec_h;
-    unsigned long long *rec_m;     // kSubMaxWords words per record
+    int64_t *rec_off;
+    int32_t *rec_pool;
     int32_t *rec_win;              // 1 = the record that stands for its clique
-    unsigned long long *n_rec;
-    int64_t rec_cap;
+    unsigned long long *n_rec, *n_words;
+    int64_t rec_cap, pool_cap;
     int32_t *tid;
     int64_t tmask;
     unsigned long long *out;       // OUT block of the created cliques
-    int32_t *status;               // 1 = a clique too large, 2 = too many candidates, 4 = record space full
+    int32_t *status;               // 1 = more than 256 endpoints of deleted edges in a clique, 4 = record space full
+    int64_t *big;                  // removed cliques left to the enumerating fallback
+    unsigned long long *n_big;
+    unsigned long long *bk_scratch;   // fallback: per thread kBkWords words
 };
 
-// Do record b (written by another warp: read through L2) and the candidate
-// (clique ca, mask ma) have the same members?
-__device__ bool same_members(const DelParams &P, int64_t ca, const unsigned long long (&ma)[kSubMaxWords],
-                             int64_t b) {
-    unsigned long long mb[kSubMaxWords];
-#pragma unroll
-    for (int w = 0; w < kSubMaxWords; ++w) mb[w] = __ldcg(P.rec_m + b * kSubMaxWords + w);
-    const int64_t cb = __ldcg(P.rec_c + b);
-    const int32_t *va = P.rvtx + P.roff[ca] + 1, *vb = P.rvtx + P.roff[cb] + 1;
-    int wa = 0, wb = 0;
-    unsigned long long xa = ma[0], xb = mb[0];
-    for (;;) {
-        while (!xa && wa + 1 < kSubMaxWords) xa = ma[++wa];
-        while (!xb && wb + 1 < kSubMaxWords) xb = mb[++wb];
-        if (!xa || !xb) return !xa && !xb;
-        if (va[wa * 64 + __ffsll((long long)xa) - 1] != vb[wb * 64 + __ffsll((long long)xb) - 1]) return false;
-        xa &= xa - 1;
-        xb &= xb - 1;
+// Is record b's list (written by another thread: read through L2) the list a?
+__device__ bool same_list(const DelParams &P, const int32_t *a, int64_t b) {
+    const int32_t *lb = P.rec_pool + __ldcg(P.rec_off + b);
+    const int32_t n = __ldcg(lb);
+    if (n != a[0]) return false;
+    for (int i = 1; i <= n; ++i)
+        if (__ldcg(lb + i) != a[i]) return false;
+    return true;
+}
+
+// A created clique (hash h, size, members), recorded once however many
+// removed cliques split into it: the first record to take a table slot for
+// its members stands for it and is counted.
+template <class M>
+__device__ void record_created(const DelParams &P, uint64_t h, int32_t size, const M &mem) {
+    const unsigned long long r = atomicAdd(P.n_rec, 1ULL);
+    const unsigned long long w = atomicAdd(P.n_words, (unsigned long long)size + 1);
+    if ((int64_t)r >= P.rec_cap || (int64_t)(w + size + 1) > P.pool_cap) {
+        atomicOr(P.status, 4);
+        return;
     }
+    int32_t *dst = P.rec_pool + w;
+    dst[0] = size;
+    int k = 1;
+    mem.each([&](int32_t v) {
+        dst[k++] = v;
+        return true;
+    });
+    P.rec_off[r] = (int64_t)w;
+    P.rec_h[r] = h;
+    __threadfence();   // the record is complete before its slot is published
+    int64_t slot = (int64_t)(h & (uint64_t)P.tmask);
+    bool fresh = false;
+    for (int64_t probe = 0; probe <= P.tmask; ++probe) {
+        const int32_t prev = atomicCAS(&P.tid[slot], 0, (int32_t)(r + 1));
+        if (prev == 0) {
+            fresh = true;
+            break;
+        }
+        const int64_t o = prev - 1;
+        if (__ldcg(P.rec_h + o) == h && same_list(P, dst, o)) break;   // already there
+        slot = (slot + 1) & P.tmask;
+    }
+    if (!fresh) return;
+    P.rec_win[r] = 1;
+    atomicAdd(&P.out[OUT_COUNT], 1ULL);
+    atomicAdd(&P.out[OUT_HASH], h);
+    if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
+    atomicMax(&P.out[OUT_MAXSIZE], (unsigned long long)size);
 }
 
 // Edge deletions by reduction to additions: G = (G - H) + H, so the cliques
 // that the deletion creates are Algorithm 8's splits of the removed cliques
 // (those of G through an edge of H) that are maximal in G - H.  One warp per
-// removed clique splits it as k_imce_sub does; each split that is maximal in
-// G - H is inserted once into a table keyed by H(K) with member comparison.
+// removed clique splits it as k_imce_sub does (masks over the endpoints of
+// deleted edges inside it); each split that is maximal in G - H is recorded
+// once.  A clique larger than kEpBits, with more than kSubMaxEdges deleted
+// edges inside, or whose S outgrows kSubCap goes to k_dmce_created_bk.
 __global__ void __launch_bounds__(256) k_dmce_created(DelParams P) {
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     constexpr int MW = kSubMaxWords;
     unsigned long long *S = P.scratch + gw * (int64_t)2 * kSubCap * MW;
     unsigned long long *S2 = S + (int64_t)kSubCap * MW;
-    __shared__ int32_t edges_s[8][2 * 512];
-    int32_t *edges = edges_s[threadIdx.x >> 5];
+    __shared__ int32_t edges_s[8][2 * kSubMaxEdges];
+    __shared__ uint32_t ep_s[8][kEpBits / 32];
+    int32_t *edges = edges_s[wib];
+    uint32_t *ep = ep_s[wib];
     for (int64_t c = gw; c < P.n_rem; c += nw) {
         const int32_t *cv = P.rvtx + P.roff[c] + 1;
         const int32_t s = cv[-1];
-        if (s > 64 * MW) {
+        if (s > kEpBits) {
+            if (lane == 0) P.big[atomicAdd(P.n_big, 1ULL)] = c;
+            continue;
+        }
+        const int ne = clique_batch_edges(cv, s, P.h_ptr, P.h_adj, edges, ep, lane);
+        const int nr = count_endpoints(ep, s, lane);
+        if (nr > 64 * MW) {
             if (lane == 0) atomicOr(P.status, 1);
             continue;
         }
-        // deleted edges inside c: (i, j) positions, i < j, lexicographic
-        int ne = 0;
-        for (int i = 0; i < s; ++i) {
-            const int32_t a = cv[i];
-            const int32_t h0 = P.h_ptr[a], hd = P.h_ptr[a + 1] - h0;
-            for (int t0 = 0; t0 < hd; t0 += 32) {
-                int j = -1;
-                if (t0 + lane < hd) {
-                    const int32_t y = P.h_adj[h0 + t0 + lane];
-                    if (y > a) {
-                        const int p = lower_bound_i32(cv, s, y);
-                        if (p < s && cv[p] == y) j = p;
-                    }
-                }
-                const uint32_t b = __ballot_sync(FULL, j >= 0);
-                if (j >= 0) {
-                    const int slot = ne + __popc(b & lanemask_lt());
-                    if (slot < 512) {
-                        edges[2 * slot] = i;
-                        edges[2 * slot + 1] = j;
-                    }
-                }
-                ne += __popc(b);
-            }
-        }
-        __syncwarp();
-        if (ne > 512) {
-            if (lane == 0) atomicOr(P.status, 2);
+        if (ne > kSubMaxEdges) {
+            if (lane == 0) P.big[atomicAdd(P.n_big, 1ULL)] = c;
             continue;
         }
-        int ns = 1;
-        if (lane < MW) {
-            const int lo = lane * 64;
-            const int nb = s - lo;
-            S[lane] = nb >= 64 ? ~0ULL : (nb > 0 ? ((1ULL << nb) - 1) : 0ULL);
-        }
+        for (int e = lane; e < 2 * ne; e += 32) edges[e] = endpoint_index(ep, edges[e]);
+        const uint64_t hcore = core_hash_sum(cv, s, ep, P.seed, lane);
         __syncwarp();
-        bool overflow = false;
-        for (int e = 0; e < ne && !overflow; ++e) {
-            const int ei = edges[2 * e], ej = edges[2 * e + 1];
-            const int wi = ei >> 6, wj = ej >> 6;
-            const unsigned long long bi = 1ULL << (ei & 63), bj = 1ULL << (ej & 63);
-            int n2 = 0;
-            for (int t0 = 0; t0 < ns; t0 += 32) {
-                const int t = t0 + lane;
-                bool both = false, valid = t < ns;
-                unsigned long long m[MW];
-                if (valid) {
-#pragma unroll
-                    for (int w = 0; w < MW; ++w) m[w] = S[(int64_t)t * MW + w];
-                    both = (m[wi] & bi) && (m[wj] & bj);
-                }
-                const uint32_t bb = __ballot_sync(FULL, valid && both);
-                const uint32_t bv = __ballot_sync(FULL, valid);
-                const int before = 2 * __popc(bb & lanemask_lt()) + __popc(bv & ~bb & lanemask_lt());
-                const int total = 2 * __popc(bb) + __popc(bv & ~bb);
-                if (n2 + total > kSubCap) {
-                    overflow = true;
-                    break;
-                }
-                if (valid) {
-                    unsigned long long *d0 = S2 + (int64_t)(n2 + before) * MW;
-                    if (both) {
-#pragma unroll
-                        for (int w = 0; w < MW; ++w) {
-                            d0[w] = m[w] & ~(w == wi ? bi : 0ULL);
-                            d0[MW + w] = m[w] & ~(w == wj ? bj : 0ULL);
-                        }
-                    } else {
-#pragma unroll
-                        for (int w = 0; w < MW; ++w) d0[w] = m[w];
-                    }
-                }
-                n2 += total;
-            }
-            __syncwarp();
-            if (overflow) break;
-            ns = 0;
-            for (int t = 0; t < n2; ++t) {
-                const unsigned long long *cand = S2 + (int64_t)t * MW;
-                bool dup = false;
-                for (int q0 = 0; q0 < ns && !dup; q0 += 32) {
-                    const int q = q0 + lane;
-                    bool eq = false;
-                    if (q < ns) {
-                        eq = true;
-#pragma unroll
-                        for (int w = 0; w < MW; ++w) eq &= S[(int64_t)q * MW + w] == cand[w];
-                    }
-                    dup = __any_sync(FULL, eq);
-                }
-                if (!dup) {
-                    if (lane < MW) S[(int64_t)ns * MW + lane] = cand[lane];
-                    ++ns;
-                    __syncwarp();
-                }
-            }
-            __syncwarp();
-        }
-        if (overflow) {
-            if (lane == 0) atomicOr(P.status, 2);
+        const int ns = split_set(edges, ne, nr, S, S2, lane);
+        if (ns < 0) {
+            if (lane == 0) P.big[atomicAdd(P.n_big, 1ULL)] = c;
             continue;
         }
-        // every split maximal in G - H, inserted once
+        // every split maximal in G - H, recorded once
         for (int t0 = 0; t0 < ns; t0 += 32) {
             const int t = t0 + lane;
             if (t >= ns) continue;
-            unsigned long long m[MW];
-            int32_t size = 0;
-            uint64_t hs = 0;
-#pragma unroll
-            for (int w = 0; w < MW; ++w) {
-                m[w] = S[(int64_t)t * MW + w];
-                for (unsigned long long x = m[w]; x; x &= x - 1) {
-                    hs += vertex_hash(cv[w * 64 + __ffsll((long long)x) - 1], P.seed);
-                    ++size;
-                }
-            }
-            if (size == 0 || !cand_is_maximal(P.row_ptr, P.col, cv, s, m)) continue;
-            const uint64_t h = clique_hash_from_sum(hs, (uint32_t)size);
-            const unsigned long long r = atomicAdd(P.n_rec, 1ULL);
-            if ((int64_t)r >= P.rec_cap) {
-                atomicOr(P.status, 4);
-                continue;
-            }
-            P.rec_c[r] = c;
-            P.rec_h[r] = h;
-#pragma unroll
-            for (int w = 0; w < MW; ++w) P.rec_m[r * MW + w] = m[w];
-            __threadfence();   // the record is complete before its slot is published
-            int64_t slot = (int64_t)(h & (uint64_t)P.tmask);
-            bool fresh = false;
-            for (int64_t probe = 0; probe <= P.tmask; ++probe) {
-                const int32_t prev = atomicCAS(&P.tid[slot], 0, (int32_t)(r + 1));
-                if (prev == 0) {
-                    fresh = true;
-                    break;
-                }
-                const int64_t o = prev - 1;
-                if (__ldcg(P.rec_h + o) == h && same_members(P, c, m, o)) break;   // already there
-                slot = (slot + 1) & P.tmask;
-            }
-            if (!fresh) continue;
-            P.rec_win[r] = 1;
-            atomicAdd(&P.out[OUT_COUNT], 1ULL);
-            atomicAdd(&P.out[OUT_HASH], h);
-            if (size < MCE_HIST_CAP) atomicAdd(&P.out[OUT_HIST + size], 1ULL);
-            atomicMax(&P.out[OUT_MAXSIZE], (unsigned long long)size);
+            const unsigned long long *m = S + (int64_t)t * MW;
+            int32_t size;
+            const uint64_t h = split_cand_hash(cv, s, ep, nr, m, hcore, P.seed, size);
+            const SplitMembers mm{cv, s, ep, m};
+            if (size > 0 && is_maximal_in(P.row_ptr, P.col, cv, s, mm)) record_created(P, h, size, mm);
         }
         __syncwarp();
     }
 }
 
-__global__ void k_rec_words(const int32_t *win, const unsigned long long *rec_m, int64_t n, int32_t *flag,
-                            int64_t *words) {
+// Enumerating fallback of the created cliques (see split_bk), one thread per
+// removed clique.
+__global__ void k_dmce_created_bk(DelParams P, int64_t n_big) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long *adj = P.bk_scratch + tid * (int64_t)kBkWords;
+    unsigned long long *fr = adj + 256 * 4;
+    int32_t rpos[256];
+    int32_t qd[258];
+    for (int64_t bi = tid; bi < n_big; bi += nth) {
+        const int64_t c = P.big[bi];
+        const int32_t *cv = P.rvtx + P.roff[c] + 1;
+        const int32_t s = cv[-1];
+        const bool ok = split_bk(cv, s, P.h_ptr, P.h_adj, P.seed, adj, fr, rpos, qd,
+                                 [&](uint64_t h, int32_t size, const RposMembers &mm) {
+                                     if (size > 0 && is_maximal_in(P.row_ptr, P.col, cv, s, mm))
+                                         record_created(P, h, size, mm);
+                                 });
+        if (!ok) atomicOr(P.status, 1);
+    }
+}
+
+__global__ void k_rec_words(const int32_t *win, const int64_t *rec_off, const int32_t *rec_pool, int64_t n,
+                            int32_t *flag, int64_t *words) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        int32_t sz = 0;
-        for (int w = 0; w < kSubMaxWords; ++w) sz += __popcll(rec_m[r * kSubMaxWords + w]);
         flag[r] = win[r];
-        words[r] = win[r] ? sz + 1 : 0;
+        words[r] = win[r] ? (int64_t)rec_pool[rec_off[r]] + 1 : 0;
     }
 }
 
 // winning record r -> list entry flag_scan[r] at word offset wpos[r]: size, then the members ascending
-__global__ void k_rec_lists(const int32_t *flag_scan, const int64_t *wpos, const int64_t *rec_c,
-                            const unsigned long long *rec_m, int64_t n, const int64_t *roff, const int32_t *rvtx,
-                            int64_t *loff, int32_t *lvtx) {
+__global__ void k_rec_lists(const int32_t *flag_scan, const int64_t *wpos, const int64_t *rec_off,
+                            const int32_t *rec_pool, int64_t n, int64_t *loff, int32_t *lvtx) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         if (flag_scan[r + 1] == flag_scan[r]) continue;
-        const int32_t *cv = rvtx + roff[rec_c[r]] + 1;
-        int64_t p = wpos[r];
+        const int32_t *src = rec_pool + rec_off[r];
+        const int64_t p = wpos[r];
         loff[flag_scan[r]] = p;
-        int32_t sz = 0;
-        for (int w = 0; w < kSubMaxWords; ++w)
-            for (unsigned long long x = rec_m[r * kSubMaxWords + w]; x; x &= x - 1) lvtx[p + 1 + sz++] = cv[w * 64 + __ffsll((long long)x) - 1];
-        lvtx[p] = sz;
+        for (int32_t q = 0; q <= src[0]; ++q) lvtx[p + q] = src[q];
     }
 }
 
@@ -1539,7 +1536,7 @@ mce_status remove_edges(imce_state *S, const int32_t *u, const int32_t *v, int64
     GraphGuard gm;
     MCE_TRY(combine_graph(g, bt, false, s, gm));
     // ---- created cliques
-    DevBuf cout_, scratch, rc, rh, rm, rw, nrec, tid, sstat;
+    DevBuf cout_, scratch, roffr, rh, rpool, rw, nrec, nwords, tid, sstat, big, nbig, bkscr;
     MCE_TRY(cout_.alloc(OUT_WORDS * 8, s));
     MCE_CUDA(cudaMemsetAsync(cout_.p, 0, OUT_WORDS * 8, s));
     unsigned long long hc[OUT_WORDS];
@@ -1551,22 +1548,29 @@ mce_status remove_edges(imce_state *S, const int32_t *u, const int32_t *v, int64
         const int64_t warps = (int64_t)blocks * 8;
         MCE_TRY(scratch.alloc((size_t)warps * 2 * kSubCap * kSubMaxWords * 8, s));
         int64_t cap = 8 * n_rem + 4096;
+        int64_t pool_cap = 8 * (int64_t)hr[OUT_LIST_WORDS] + 65536;
         MCE_TRY(sstat.alloc(4, s));
         MCE_TRY(nrec.alloc(8, s));
-        unsigned long long nr = 0;
+        MCE_TRY(nwords.alloc(8, s));
+        MCE_TRY(big.alloc((size_t)(n_rem + 1) * 8, s));
+        MCE_TRY(nbig.alloc(8, s));
+        unsigned long long nr = 0, nw = 0;
         int32_t hst = 0;
+        int64_t bk_threads = 0;
         for (int attempt = 0;; ++attempt) {
             int64_t tcap = 1024;
             while (tcap < 2 * cap) tcap *= 2;
-            MCE_TRY(rc.alloc((size_t)cap * 8, s));
+            MCE_TRY(roffr.alloc((size_t)cap * 8, s));
             MCE_TRY(rh.alloc((size_t)cap * 8, s));
-            MCE_TRY(rm.alloc((size_t)cap * kSubMaxWords * 8, s));
+            MCE_TRY(rpool.alloc((size_t)pool_cap * 4, s));
             MCE_TRY(rw.alloc((size_t)(cap + 1) * 4, s));
             MCE_TRY(tid.alloc((size_t)tcap * 4, s));
             MCE_CUDA(cudaMemsetAsync(rw.p, 0, (size_t)(cap + 1) * 4, s));
             MCE_CUDA(cudaMemsetAsync(tid.p, 0, (size_t)tcap * 4, s));
             MCE_CUDA(cudaMemsetAsync(nrec.p, 0, 8, s));
+            MCE_CUDA(cudaMemsetAsync(nwords.p, 0, 8, s));
             MCE_CUDA(cudaMemsetAsync(sstat.p, 0, 4, s));
+            MCE_CUDA(cudaMemsetAsync(nbig.p, 0, 8, s));
             MCE_CUDA(cudaMemsetAsync(cout_.p, 0, OUT_WORDS * 8, s));
             DelParams Q{};
             Q.roff = rloff.as<int64_t>();
@@ -1578,29 +1582,48 @@ mce_status remove_edges(imce_state *S, const int32_t *u, const int32_t *v, int64
             Q.col = gm.g->col;
             Q.seed = S->seed;
             Q.scratch = scratch.as<unsigned long long>();
-            Q.rec_c = rc.as<int64_t>();
             Q.rec_h = rh.as<unsigned long long>();
-            Q.rec_m = rm.as<unsigned long long>();
+            Q.rec_off = roffr.as<int64_t>();
+            Q.rec_pool = rpool.as<int32_t>();
             Q.rec_win = rw.as<int32_t>();
             Q.n_rec = nrec.as<unsigned long long>();
+            Q.n_words = nwords.as<unsigned long long>();
             Q.rec_cap = cap;
+            Q.pool_cap = pool_cap;
             Q.tid = tid.as<int32_t>();
             Q.tmask = tcap - 1;
             Q.out = cout_.as<unsigned long long>();
             Q.status = sstat.as<int32_t>();
+            Q.big = big.as<int64_t>();
+            Q.n_big = nbig.as<unsigned long long>();
             MCE_LAUNCH(k_dmce_created, blocks, 256, 0, s, Q);
+            // removed cliques that the split loop left: enumerating fallback
+            unsigned long long hbig = 0;
+            MCE_CUDA(cudaMemcpyAsync(&hbig, nbig.p, 8, cudaMemcpyDeviceToHost, s));
+            MCE_CUDA(cudaStreamSynchronize(s));
+            if (hbig) {
+                const int64_t threads = (int64_t)hbig < 4096 ? (int64_t)hbig : 4096;
+                if (threads > bk_threads) {
+                    MCE_TRY(bkscr.alloc((size_t)threads * kBkWords * 8, s));
+                    bk_threads = threads;
+                }
+                Q.bk_scratch = bkscr.as<unsigned long long>();
+                MCE_LAUNCH(k_dmce_created_bk, (unsigned)((threads + 63) / 64), 64, 0, s, Q, (int64_t)hbig);
+            }
             MCE_CUDA(cudaMemcpyAsync(&nr, nrec.p, 8, cudaMemcpyDeviceToHost, s));
+            MCE_CUDA(cudaMemcpyAsync(&nw, nwords.p, 8, cudaMemcpyDeviceToHost, s));
             MCE_CUDA(cudaMemcpyAsync(&hst, sstat.p, 4, cudaMemcpyDeviceToHost, s));
             MCE_CUDA(cudaMemcpyAsync(hc, cout_.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
             MCE_CUDA(cudaStreamSynchronize(s));
-            if (hst & 3) {
-                g_last_error = hst & 1 ? "imce: removed clique larger than 256 vertices"
-                                       : "imce: too many split candidates";
+            if (hst & 1) {
+                g_last_error = "imce: more than 256 endpoints of deleted edges inside one removed clique";
                 return MCE_ESTATE;
             }
             if (!(hst & 4)) break;
             if (attempt >= 4) return MCE_EOVERFLOW;
-            cap = (int64_t)nr + 1024;   // room for every record of the last try
+            // room for every record of the last try
+            cap = (int64_t)nr + 1024;
+            pool_cap = (int64_t)nw + 65536;
         }
         // winning records -> sorted lists
         const int64_t nrec_all = (int64_t)nr;
@@ -1608,8 +1631,8 @@ mce_status remove_edges(imce_state *S, const int32_t *u, const int32_t *v, int64
         MCE_TRY(flag.alloc((size_t)(nrec_all + 1) * 4, s));
         MCE_TRY(words.alloc((size_t)(nrec_all + 1) * 8, s));
         if (nrec_all)
-            MCE_LAUNCH(k_rec_words, grid_for(nrec_all, 256), 256, 0, s, rw.as<int32_t>(), rm.as<unsigned long long>(),
-                       nrec_all, flag.as<int32_t>(), words.as<int64_t>());
+            MCE_LAUNCH(k_rec_words, grid_for(nrec_all, 256), 256, 0, s, rw.as<int32_t>(), roffr.as<int64_t>(),
+                       rpool.as<int32_t>(), nrec_all, flag.as<int32_t>(), words.as<int64_t>());
         MCE_TRY(exclusive_scan_i32(flag.as<int32_t>(), flag.as<int32_t>(), nrec_all, s));
         MCE_TRY(exclusive_scan_i64(words.as<int64_t>(), words.as<int64_t>(), nrec_all, s));
         int32_t ncr = 0;
@@ -1622,8 +1645,7 @@ mce_status remove_edges(imce_state *S, const int32_t *u, const int32_t *v, int64
         MCE_TRY(clvtx.alloc((size_t)(nwd + 1) * 4, s));
         if (nrec_all)
             MCE_LAUNCH(k_rec_lists, grid_for(nrec_all, 256), 256, 0, s, flag.as<int32_t>(), words.as<int64_t>(),
-                       rc.as<int64_t>(), rm.as<unsigned long long>(), nrec_all, rloff.as<int64_t>(),
-                       rlvtx.as<int32_t>(), cloff.as<int64_t>(), clvtx.as<int32_t>());
+                       roffr.as<int64_t>(), rpool.as<int32_t>(), nrec_all, cloff.as<int64_t>(), clvtx.as<int32_t>());
     }
     // ---- commit: removed cliques leave the index, created ones enter it, G := G - H
     DevBuf claimed, nclaimed, missing;

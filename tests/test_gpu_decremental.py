@@ -184,3 +184,80 @@ def test_invalid_or_failed_deletion_leaves_state(gpu_lib):
     ost = O.Imce(og)
     ost.remove(u[:20], v[:20])
     assert st.cliques(4096, 65536) == ost.cliques().cliques
+
+
+# ---------------------------------------------------------------- created cliques beyond the warp's buffers
+
+def _remove_vs_oracle(mce, n, pairs, rem):
+    u = np.array([a for a, b in pairs], np.int32)
+    v = np.array([b for a, b in pairs], np.int32)
+    st = mce.Imce(mce.Graph(n, _t(u), _t(v)))
+    ost = O.Imce(O.Graph(n, u, v))
+    ru = np.array([a for a, b in rem], np.int32)
+    rv = np.array([b for a, b in rem], np.int32)
+    rho, orem, ocre = ost.remove(ru, rv)
+    d = st.remove_edges(ru, rv)
+    assert _key(d) == _okey(len(ru), rho, orem, ocre, ost.alive)
+    assert st.cliques(1 << 16, 1 << 20) == ost.cliques().cliques
+    return d
+
+
+def test_removed_clique_over_256_vertices(gpu_lib):
+    """K_300 minus (0, 1): the removed clique has 300 vertices; Algorithm 8's
+    masks run over the two endpoints only, so it splits into K_300 - 0 and
+    K_300 - 1."""
+    n = 300
+    d = _remove_vs_oracle(gpu_lib, n, list(itertools.combinations(range(n), 2)), [(0, 1)])
+    assert (d.sub_count, d.new_count, d.alive) == (1, 2, 2)
+
+
+def test_created_set_beyond_the_warp_buffer(gpu_lib):
+    """K_24 minus the 24 edges inside 8 parts of 3: the removed K_24 splits
+    into the 3^8 = 6,561 maximal cliques of the Moon-Moser graph, more than
+    the split set holds in a warp's buffer (4,096), so the enumerating
+    fallback produces them."""
+    k = 8
+    parts = [list(range(3 * i, 3 * i + 3)) for i in range(k)]
+    rem = [(p[0], p[1]) for p in parts] + [(p[0], p[2]) for p in parts] + [(p[1], p[2]) for p in parts]
+    d = _remove_vs_oracle(gpu_lib, 3 * k, list(itertools.combinations(range(3 * k), 2)), rem)
+    assert (d.sub_count, d.new_count) == (1, 3 ** k)
+    assert list(d.new_hist) == [0] * k + [3 ** k]
+
+
+def test_more_than_512_deleted_edges_in_one_clique(gpu_lib):
+    """K_40 with all 780 edges deleted: K_40 is removed and the 40 singletons
+    are created (the enumerating fallback takes cliques with more than 512
+    deleted edges inside)."""
+    n = 40
+    pairs = list(itertools.combinations(range(n), 2))
+    d = _remove_vs_oracle(gpu_lib, n, pairs, pairs)
+    assert (d.sub_count, d.new_count, d.alive) == (1, n, n)
+
+
+def test_cocktail_party_from_complete_graph(gpu_lib):
+    """K_30 minus a perfect matching of 15 edges: the removed K_30 splits
+    into the 2^15 = 32,768 maximal cliques of the cocktail-party graph, each
+    of size 15 (enumerating fallback, record space grown on the way)."""
+    n = 30
+    rem = [(2 * i, 2 * i + 1) for i in range(n // 2)]
+    d = _remove_vs_oracle(gpu_lib, n, list(itertools.combinations(range(n), 2)), rem)
+    assert (d.sub_count, d.new_count, d.alive) == (1, 2 ** 15, 2 ** 15)
+
+
+def test_more_than_256_endpoints_in_one_clique_is_refused(gpu_lib):
+    """K_300 minus a perfect matching (300 endpoints of deleted edges inside
+    the one removed clique) is beyond Algorithm 8's masks: MCE_ESTATE, and the
+    graph and the clique set are unchanged."""
+    mce = gpu_lib
+    n = 300
+    pairs = list(itertools.combinations(range(n), 2))
+    g, _ = _pairs_graph(mce, n, pairs)
+    st = mce.Imce(g)
+    before = st.cliques(16, 1024)
+    row0, col0 = st.graph().csr()
+    with pytest.raises(mce.MceError) as e:
+        st.remove_edges(np.arange(0, n, 2, dtype=np.int32), np.arange(1, n, 2, dtype=np.int32))
+    assert e.value.status == mce.MCE_ESTATE
+    assert st.cliques(16, 1024) == before
+    row1, col1 = st.graph().csr()
+    assert np.array_equal(np.asarray(row0), np.asarray(row1)) and np.array_equal(np.asarray(col0), np.asarray(col1))
