@@ -147,12 +147,15 @@ SPLIT_NODES = 4096
 LANE_SEARCH_WORDS = 0
 LANE_HOLD_WAITING = 0
 
-# DRAM bytes (read + write) of one k_bk launch from an ncu capture of this
-# workload (a 10 % sample of its subproblems), scaled by
-# tree nodes; valid only for the kernel sources it was taken with.
-K_BK_TRAFFIC = {"bytes": 80_302_848 + 119_014_400, "tree_nodes": 437_700_333,
-                "sha256": {"bk.cu": "06eab31bd1dcfa9afd27d1a9357e21c563df4902c7363ba689fa68622d0b5f61",
-                           "bk.cuh": "4f0536c7e58b1fa2d93c8fbfb6d1239c9d7f1ea953402c032d8caea9ecda0be9"}}
+# Counters of one k_bk launch of this workload from ncu, valid only for the
+# kernel sources they were taken with (profiles/k_bk_rmat18_sample30pct.md):
+# DRAM bytes (read + write) of a capture of a 30 % sample of the subproblems
+# (8 passes), scaled by tree nodes; warp instructions of a one-pass capture
+# of the whole timed launch.
+K_BK_COUNTERS = {"dram_bytes": 2_021_479_936 + 3_748_293_632, "dram_tree_nodes": 1_290_883_126,
+                 "warp_inst": 253_248_724_366, "inst_tree_nodes": 4_057_750_785,
+                 "sha256": {"bk.cu": "4c0d418e37770e4ae3ee243bce6e3a09ec3fbe980c669379be89b593370ca73c",
+                            "bk.cuh": "0783344092d66dc92f6bdce679dcf59b9e129df2f325e0716946537a1730e1da"}}
 
 
 def _same_sources(digests) -> bool:
@@ -166,19 +169,19 @@ def _same_sources(digests) -> bool:
 
 
 def k_bk_traffic(tree_nodes: int):
-    if not _same_sources(K_BK_TRAFFIC["sha256"]):
+    if not _same_sources(K_BK_COUNTERS["sha256"]):
         return None
-    return K_BK_TRAFFIC["bytes"] * tree_nodes / K_BK_TRAFFIC["tree_nodes"]
+    return K_BK_COUNTERS["dram_bytes"] * tree_nodes / K_BK_COUNTERS["dram_tree_nodes"]
 
 
 def issue_roofline(tree_nodes: int, kernel_s: float, sms: int, sm_mhz: float):
     """Issue-rate roofline of the search kernel: warp instructions per tree
-    node (from the ncu capture K_BK_TRAFFIC was taken with) times the tree
+    node (from the one-pass ncu capture of the whole launch) times the tree
     nodes per second, against 4 schedulers x SMs x clock (one warp
     instruction per scheduler per clock)."""
-    if not _same_sources(K_BK_TRAFFIC["sha256"]) or kernel_s <= 0:
+    if not _same_sources(K_BK_COUNTERS["sha256"]) or kernel_s <= 0:
         return None
-    per_node = K_BK_TRAFFIC["warp_inst"] / K_BK_TRAFFIC["tree_nodes"]
+    per_node = K_BK_COUNTERS["warp_inst"] / K_BK_COUNTERS["inst_tree_nodes"]
     achieved = per_node * tree_nodes / kernel_s
     peak = 4 * sms * sm_mhz * 1e6
     return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
