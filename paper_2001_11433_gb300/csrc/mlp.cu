@@ -142,10 +142,15 @@ __global__ void k_features_light(const int32_t *__restrict__ row_ptr, const int3
 
 // ------------------------------------------------------------------ MLP
 
-template <bool BF16>
-__global__ void k_mlp_fwd(const float *__restrict__ wts, int H, const float *__restrict__ feat, int32_t rows,
+// One thread per row.  HC > 0 fixes the hidden width at compile time, so
+// that the hidden activations stay in registers and the weight rows are read
+// from shared memory four at a time (same operations in the same order as
+// the generic path, HC = 0).
+template <bool BF16, int HC>
+__global__ void k_mlp_fwd(const float *__restrict__ wts, int H_rt, const float *__restrict__ feat, int32_t rows,
                           float *out) {
-    extern __shared__ float sw[];
+    extern __shared__ __align__(16) float sw[];
+    const int H = HC > 0 ? HC : H_rt;
     const Off o = offsets(H);
     for (int64_t i = threadIdx.x; i < o.n; i += blockDim.x) {
         float w = wts[i];
@@ -162,24 +167,55 @@ __global__ void k_mlp_fwd(const float *__restrict__ wts, int H, const float *__r
             x[k] = t;
         }
         float h1[kMaxH];
-#pragma unroll 4
-        for (int j = 0; j < H; ++j) {
-            float a = sw[o.b1 + j];
-#pragma unroll
-            for (int k = 0; k < kFeat; ++k) a = fmaf(sw[o.W1 + j * kFeat + k], x[k], a);
-            a = fmaxf(a, 0.f);
-            if (BF16) a = __bfloat162float(__float2bfloat16(a));
-            h1[j] = a;
-        }
         float y = sw[o.b3];
-        for (int j = 0; j < H; ++j) {
-            float a = sw[o.b2 + j];
-            const float *wr = sw + o.W2 + (int64_t)j * H;
+        if constexpr (HC > 0) {
+            static_assert(HC % 4 == 0 && HC <= kMaxH, "fixed hidden width");
+            // weights are read per row, not held in registers across rows
+            asm volatile("" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < HC; ++j) {
+                float a = sw[o.b1 + j];
+#pragma unroll
+                for (int k = 0; k < kFeat; ++k) a = fmaf(sw[o.W1 + j * kFeat + k], x[k], a);
+                a = fmaxf(a, 0.f);
+                if (BF16) a = __bfloat162float(__float2bfloat16(a));
+                h1[j] = a;
+            }
+#pragma unroll 1
+            for (int j = 0; j < HC; ++j) {
+                float a = sw[o.b2 + j];
+                const float4 *wr = reinterpret_cast<const float4 *>(sw + o.W2 + j * HC);
+#pragma unroll
+                for (int i = 0; i < HC / 4; ++i) {
+                    const float4 w = wr[i];
+                    a = fmaf(w.x, h1[4 * i], a);
+                    a = fmaf(w.y, h1[4 * i + 1], a);
+                    a = fmaf(w.z, h1[4 * i + 2], a);
+                    a = fmaf(w.w, h1[4 * i + 3], a);
+                }
+                a = fmaxf(a, 0.f);
+                if (BF16) a = __bfloat162float(__float2bfloat16(a));
+                y = fmaf(sw[o.w3 + j], a, y);
+            }
+        } else {
+#pragma unroll 4
+            for (int j = 0; j < H; ++j) {
+                float a = sw[o.b1 + j];
+#pragma unroll
+                for (int k = 0; k < kFeat; ++k) a = fmaf(sw[o.W1 + j * kFeat + k], x[k], a);
+                a = fmaxf(a, 0.f);
+                if (BF16) a = __bfloat162float(__float2bfloat16(a));
+                h1[j] = a;
+            }
+            for (int j = 0; j < H; ++j) {
+                float a = sw[o.b2 + j];
+                const float *wr = sw + o.W2 + (int64_t)j * H;
 #pragma unroll 8
-            for (int i = 0; i < H; ++i) a = fmaf(wr[i], h1[i], a);
-            a = fmaxf(a, 0.f);
-            if (BF16) a = __bfloat162float(__float2bfloat16(a));
-            y = fmaf(sw[o.w3 + j], a, y);
+                for (int i = 0; i < H; ++i) a = fmaf(wr[i], h1[i], a);
+                a = fmaxf(a, 0.f);
+                if (BF16) a = __bfloat162float(__float2bfloat16(a));
+                y = fmaf(sw[o.w3 + j], a, y);
+            }
         }
         out[r] = y;
     }
@@ -341,13 +377,12 @@ mce_status model_predict(const mce_model *m, const float *feat, int32_t rows, in
                          float *out) {
     if (rows <= 0) return MCE_OK;
     const size_t smem = (size_t)offsets(m->H).n * 4;
-    if (bf16) {
-        MCE_CUDA(cudaFuncSetAttribute(k_mlp_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MCE_LAUNCH(k_mlp_fwd<true>, grid_for(rows, 128), 128, smem, s, m->w, m->H, feat, rows, out);
-    } else {
-        MCE_CUDA(cudaFuncSetAttribute(k_mlp_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MCE_LAUNCH(k_mlp_fwd<false>, grid_for(rows, 128), 128, smem, s, m->w, m->H, feat, rows, out);
-    }
+    // the default width has its own compiled kernel
+    void (*kf)(const float *, int, const float *, int32_t, float *) =
+        m->H == kMaxH ? (bf16 ? k_mlp_fwd<true, kMaxH> : k_mlp_fwd<false, kMaxH>)
+                      : (bf16 ? k_mlp_fwd<true, 0> : k_mlp_fwd<false, 0>);
+    MCE_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MCE_LAUNCH(kf, grid_for(rows, 128), 128, smem, s, m->w, m->H, feat, rows, out);
     return MCE_OK;
 }
 
