@@ -325,7 +325,7 @@ def run_ours(args):
     def step_device():
         g = mce.Graph(w.n, dev_u, dev_v)
         r = mce.enumerate_cliques(g, rank="degen", subset=dev_subset, blocks_per_sm=args.blocks_per_sm,
-                                  split_nodes=SPLIT_NODES, warp_small_search=args.warp_small_search,
+                                  split_nodes=args.split_nodes, warp_small_search=args.warp_small_search,
                                   lane_search_words=args.lane_search_words,
                                   lane_hold_waiting=args.lane_hold_waiting)
         g.close()
@@ -365,7 +365,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         g = mce.Graph(w.n, pin_u.numpy(), pin_v.numpy())
         r2 = mce.enumerate_cliques(g, rank="degen", subset=pin_subset.numpy(), blocks_per_sm=args.blocks_per_sm,
-                                   split_nodes=SPLIT_NODES, warp_small_search=args.warp_small_search,
+                                   split_nodes=args.split_nodes, warp_small_search=args.warp_small_search,
                                   lane_search_words=args.lane_search_words,
                                   lane_hold_waiting=args.lane_hold_waiting)
         g.close()
@@ -399,7 +399,7 @@ def run_ours(args):
         # the GPU on the very same subproblems (enumeration time: Γ+ lists, prepass, search)
         gs = mce.Graph(w.n, dev_u, dev_v)
         gpu_runs = [mce.enumerate_cliques(gs, rank="degen", subset=torch.from_numpy(sample).cuda(),
-                                          blocks_per_sm=args.blocks_per_sm, split_nodes=SPLIT_NODES,
+                                          blocks_per_sm=args.blocks_per_sm, split_nodes=args.split_nodes,
                                           warp_small_search=args.warp_small_search,
                                           lane_search_words=args.lane_search_words,
                                   lane_hold_waiting=args.lane_hold_waiting) for _ in range(3)]
@@ -431,7 +431,7 @@ def run_ours(args):
                    "max_clique": len(res.hist) - 1, "tree_nodes": res.tree_nodes,
                    "tree_nodes_per_s": world * res.tree_nodes / (ms / 1000.0),
                    "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{world}",
-                   "launch": {"blocks_per_sm": args.blocks_per_sm, "warps_per_block": 8, "split_nodes": SPLIT_NODES,
+                   "launch": {"blocks_per_sm": args.blocks_per_sm, "warps_per_block": 8, "split_nodes": args.split_nodes,
                               "small_search": "warp" if args.warp_small_search else "lane-parallel",
                               "lane_search_words": args.lane_search_words,
                               "lane_hold_waiting": args.lane_hold_waiting}},
@@ -853,6 +853,7 @@ def main():
     ap.add_argument("--sample", type=float, default=1.0, help="rmat18: timed fraction of the subproblem set")
     ap.add_argument("--workload", choices=["rmat18", "batched", "serve", "ranks", "scaling"], default="rmat18")
     ap.add_argument("--blocks-per-sm", type=int, default=BLOCKS_PER_SM, help="rmat18: resident search blocks per SM")
+    ap.add_argument("--split-nodes", type=int, default=SPLIT_NODES, help="rmat18: proactive hand-over interval (nodes)")
     ap.add_argument("--lane-search-words", type=int, default=LANE_SEARCH_WORDS,
                     help="rmat18: per-warp shared words of the lane-parallel small search (0 = automatic)")
     ap.add_argument("--lane-hold-waiting", type=int, default=LANE_HOLD_WAITING,

@@ -955,16 +955,29 @@ __device__ __forceinline__ void small_relabel(const BkParams &P, const Ws &s, in
     cidX = lane < u.xn ? Xl[lane] : 0;
     u.adjC = u.adjX = u.exclC = 0u;
     {
+        // C_k is the k-th candidate column in ascending order, so lane l's
+        // rows restricted to C are read word by word over the non-empty words
+        // of cand: one load per word and row, then a bit per candidate
         const uint32_t *rowC = s.A + (int64_t)cidC * s.S;
         const uint32_t *rowX = s.A + (int64_t)cidX * s.S;
         const uint32_t *xrow = imce ? s.X + (int64_t)cidC * s.S : nullptr;
-        for (int k = 0; k < u.cn; ++k) {
-            const int32_t ck = Cl[k];
-            const int wd = ck >> 5;
-            const uint32_t bit = 1u << (ck & 31);
-            if (lane < u.cn && (rowC[wd] & bit)) u.adjC |= 1u << k;
-            if (lane < u.xn && (rowX[wd] & bit)) u.adjX |= 1u << k;
-            if (imce && lane < u.cn && (xrow[wd] & bit)) u.exclC |= 1u << k;
+        int k = 0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            for (uint32_t nz = __ballot_sync(FULL, rc[r] != 0u); nz; nz &= nz - 1u) {
+                const int j = __ffs(nz) - 1;
+                const int w = j + 32 * r;
+                uint32_t cw = __shfl_sync(FULL, rc[r], j);
+                const uint32_t a = lane < u.cn ? rowC[w] : 0u;
+                const uint32_t x = lane < u.xn ? rowX[w] : 0u;
+                const uint32_t e = (imce && lane < u.cn) ? xrow[w] : 0u;
+                for (; cw; cw &= cw - 1u, ++k) {
+                    const int b = __ffs(cw) - 1;
+                    u.adjC |= ((a >> b) & 1u) << k;
+                    u.adjX |= ((x >> b) & 1u) << k;
+                    u.exclC |= ((e >> b) & 1u) << k;
+                }
+            }
         }
     }
     {
@@ -993,7 +1006,6 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
                             const uint32_t (&rc)[NR], const uint32_t (&rf)[NR], const uint32_t (&rx)[NR],
                             const int32_t *Fd, int flen) {
     const bool imce = P.mode == BK_IMCE;
-    const int wc = s.wc;
     SmallU u;
     int32_t gC, cidC, cidX;
     small_relabel<NR>(P, s, lane, rc, rf, Fd, flen, u, gC, cidC, cidX);
@@ -1241,10 +1253,11 @@ __device__ int search_small(const BkParams &P, Ws &s, const Task &T, Acc &acc, u
 // whole warp one node at a time.  The warp relabels each small node it
 // reaches (small_relabel) into a universe in its shared-memory arena and goes
 // on with the wide search; when the arena or the root table is full, or the
-// task ends, every lane runs whole small subtrees on its own (lp_run): the
-// TTT step of search_small on 32-bit masks, one lane per subtree, a lane
-// taking the next universe when it is done.  Trees, node counts, word
-// operations and cliques are those of search_small.
+// task ends, the lanes search the buffered subtrees (lp_run): the TTT step of
+// search_small on 32-bit masks, one node per lane at a time, the nodes taken
+// 32 at a time from a stack of entered nodes that the lanes share, so that
+// the heavy-tailed subtree sizes spread over the lanes node by node.  Trees,
+// node counts, word operations and cliques are those of search_small.
 //
 // Universe of a small node with cn candidates and xn fini vertices (arena
 // words): h(C_k) as uint64 [2 cn]; per C member its row adjC and tie key
@@ -1523,7 +1536,7 @@ __device__ __forceinline__ LpNode lp_task_get(const uint32_t *lp, const uint32_t
 // and one-candidate children are settled at once); a child that finds the
 // list full is searched here instead.
 __device__ void lp_expand(const BkParams &P, unsigned long long *shist, LpNode u, int r, LpSums &o, uint32_t *dst,
-                          uint32_t *dst_n) {
+                          uint32_t *dst_n, uint32_t cap) {
     if (u.cand == 0u) {
         if ((u.finc | u.xs) == 0u) lp_emit(P, shist, o, u.base + (uint32_t)u.depth, u.hs);
         return;
@@ -1545,45 +1558,41 @@ __device__ void lp_expand(const BkParams &P, unsigned long long *shist, LpNode u
         c.hs = u.hs + hq;
         c.depth = u.depth + 1;
         const uint32_t slot = atomicAdd(dst_n, 1u);
-        if (slot < (uint32_t)P.lp_task_cap) lp_task_put(dst + (int64_t)slot * BK_LP_TASK_WORDS, r, c);
+        if (slot < cap) lp_task_put(dst + (int64_t)slot * BK_LP_TASK_WORDS, r, c);
         else lp_dfs(P, shist, c, o);
     }
 }
 
-// The buffered small subtrees, one lane per task.  The roots are expanded
-// breadth first (one level, and up to two more while the tasks number fewer
-// than eight per lane) so that the heavy-tailed subtree sizes spread over the lanes;
-// the last list is then taken task by task, each searched depth first.
+// The buffered small subtrees, searched from one stack of nodes (entered,
+// not yet pivoted) shared by the warp's lanes: each round the lanes take up
+// to 32 nodes off the top together and push the children that are not
+// settled at once; a child that finds the stack full is searched depth
+// first by its lane.
 __device__ __noinline__ LpSums lp_run(const BkParams &P, uint32_t *lp, int nroots, unsigned long long *shist,
                                       uint32_t *tasks, int lane) {
     LpSums o = {0ULL, 0ULL, 0u, 0u, 0u};
-    uint32_t *ctr = lp + BK_LP_MAX_ROOTS * 4;   // [0] list A size, [1] list B size, [2] next task
-    uint32_t *la = tasks, *lb = tasks + (int64_t)P.lp_task_cap * BK_LP_TASK_WORDS;
-    if (lane == 0) ctr[0] = ctr[1] = ctr[2] = 0u;
+    uint32_t *ctr = lp + BK_LP_MAX_ROOTS * 4;   // [0] stack top
+    const uint32_t cap = (uint32_t)P.lp_task_cap;
+    for (int r = lane; r < nroots; r += 32) lp_task_put(tasks + (int64_t)r * BK_LP_TASK_WORDS, r, lp_root_node(lp, r));
+    if (lane == 0) ctr[0] = (uint32_t)nroots;
     __syncwarp();
-    for (int r = lane; r < nroots; r += 32) lp_expand(P, shist, lp_root_node(lp, r), r, o, la, &ctr[0]);
-    __syncwarp();
-    uint32_t n = min(ctr[0], (uint32_t)P.lp_task_cap);
-    uint32_t *list = la, *other = lb;
-    // up to two more levels while the tasks number fewer than eight per lane
-    for (int round = 0; round < 2 && n > 0u && n < 256u; ++round) {
-        if (lane == 0) ctr[1] = 0u;
-        __syncwarp();
-        for (uint32_t i = (uint32_t)lane; i < n; i += 32u) {
-            const uint32_t *t = list + (int64_t)i * BK_LP_TASK_WORDS;
-            lp_expand(P, shist, lp_task_get(lp, t), (int)(t[0] & 0xffu), o, other, &ctr[1]);
+    for (;;) {
+        const uint32_t top = min(ctr[0], cap);
+        if (top == 0u) break;
+        const uint32_t take = min(top, 32u), base = top - take;
+        LpNode u;
+        int r = -1;
+        if ((uint32_t)lane < take) {
+            const uint32_t *t = tasks + (int64_t)(base + (uint32_t)lane) * BK_LP_TASK_WORDS;
+            r = (int)(t[0] & 0xffu);
+            u = lp_task_get(lp, t);
         }
+        __syncwarp();   // every taken record is read before pushes reuse its slot
+        if (lane == 0) ctr[0] = base;
         __syncwarp();
-        n = min(ctr[1], (uint32_t)P.lp_task_cap);
-        uint32_t *tmp = list;
-        list = other;
-        other = tmp;
+        if (r >= 0) lp_expand(P, shist, u, r, o, tasks, &ctr[0], cap);
+        __syncwarp();
     }
-    for (uint32_t i = atomicAdd(&ctr[2], 1u); i < n; i = atomicAdd(&ctr[2], 1u)) {
-        const uint32_t *t = list + (int64_t)i * BK_LP_TASK_WORDS;
-        lp_dfs(P, shist, lp_task_get(lp, t), o);
-    }
-    __syncwarp();
     return o;
 }
 
@@ -1591,7 +1600,7 @@ __device__ __noinline__ LpSums lp_run(const BkParams &P, uint32_t *lp, int nroot
 __device__ void lp_flush(const BkParams &P, Ws &s, Acc &acc, unsigned long long *shist, int lane, int &node_tick) {
     if (s.lp_n == 0) return;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const LpSums r = lp_run(P, s.lp, s.lp_n, shist, P.lp_tasks + gwarp * 2 * (int64_t)P.lp_task_cap * BK_LP_TASK_WORDS,
+    const LpSums r = lp_run(P, s.lp, s.lp_n, shist, P.lp_tasks + gwarp * (int64_t)P.lp_task_cap * BK_LP_TASK_WORDS,
                             lane);
     unsigned long long cnt = r.count, nodes = r.nodes, hsh = r.hash, wops = r.wops;
     uint32_t smax = r.smax;

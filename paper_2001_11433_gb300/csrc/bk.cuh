@@ -99,7 +99,7 @@ struct BkParams {
     uint64_t timeout_ns;      // bound on any single wait
     uint64_t max_run_ns;      // bound on a warp's time in one launch
     int32_t lp_words;         // per-warp shared words of the lane-parallel small search (0 = off)
-    uint32_t *lp_tasks;       // per warp: two lists of lp_task_cap node records (BK_LP_TASK_WORDS each)
+    uint32_t *lp_tasks;       // per warp: a stack of lp_task_cap node records (BK_LP_TASK_WORDS each)
     int32_t lp_task_cap;
     int32_t sm_limit;         // SMs the persistent grid covers (0 = all)
     const uint8_t *heavy;     // per vertex: 1 = predicted heavy, splits every heavy_split_nodes (or null)
@@ -139,7 +139,7 @@ constexpr int BK_LP_TABLE_WORDS = BK_LP_MAX_ROOTS * 4 + 4;
 // A node of a small subtree waiting for a lane: root index | depth << 8,
 // cand, finc, xs, hash sum (2 words).
 constexpr int BK_LP_TASK_WORDS = 6;
-constexpr int BK_LP_TASK_CAP = 1024;
+constexpr int BK_LP_TASK_CAP = 2048;
 
 // Dynamic shared memory of one search block: 256 histogram bins, the pivot
 // scratch of every warp, the optional per-warp workspace slots, then the

@@ -246,7 +246,7 @@ mce_status alloc_lp_tasks(BkParams &P, int64_t nwarps, cudaStream_t s, BkBuffers
         return MCE_OK;
     }
     P.lp_task_cap = BK_LP_TASK_CAP;
-    MCE_TRY(b.lp_tasks.alloc((size_t)nwarps * 2 * BK_LP_TASK_CAP * BK_LP_TASK_WORDS * 4, s));
+    MCE_TRY(b.lp_tasks.alloc((size_t)nwarps * BK_LP_TASK_CAP * BK_LP_TASK_WORDS * 4, s));
     P.lp_tasks = b.lp_tasks.as<uint32_t>();
     return MCE_OK;
 }
