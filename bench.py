@@ -140,11 +140,12 @@ def load_peaks():
 
 
 TREE_CAP = 1 << 24          # nodes per subproblem search tree in the benchmark set
-# launch shape for this workload, from a sweep on GB300 (2 or 3 resident
-# blocks of 8 warps per SM x hand-over every 2048..16384 nodes): 3 x 4096
-BLOCKS_PER_SM = 3
-SPLIT_NODES = 4096
-LANE_SEARCH_WORDS = 0
+# launch shape for this workload, from a sweep on GB300 (2, 3 or 4 resident
+# blocks of 8 warps per SM x hand-over every 2048..32768 nodes x 1024..3040
+# words of lane-search arena per warp): 2 x 12288 x 2048
+BLOCKS_PER_SM = 2
+SPLIT_NODES = 12288
+LANE_SEARCH_WORDS = 2048
 LANE_HOLD_WAITING = 0
 
 # Counters of one k_bk launch of this workload from ncu, valid only for the
@@ -737,7 +738,8 @@ def balance_stats(r):
     mean_busy = (st[0] + st[1]) / warps
     return {"search_ms": r.ms_search, "max_warp_busy_ms": st[5] / 1e6, "mean_warp_busy_ms": mean_busy / 1e6,
             "imbalance": st[5] / mean_busy if mean_busy else None, "idle_frac": st[2] / max(st[0] + st[1] + st[2], 1),
-            "endgame_ms": st[7] / 1e6, "pieces": st[4], "builds": st[3]}
+            "endgame_ms": st[7] / 1e6, "pieces": st[4], "builds": st[3],
+            "build_frac": st[0] / max(st[0] + st[1], 1)}
 
 
 def measure_ranks(mce, steps=3, warmup=1, kinds=("degree", "degen", "triangle", "learned", "learned_split")):
@@ -826,10 +828,11 @@ def run_scaling(args):
     scaling = {}
     for k in (sms // 8, sms // 4, sms // 2, sms):
         scaling[str(k)] = timed(g, rank="degen", subset=sub, blocks_per_sm=BLOCKS_PER_SM, split_nodes=SPLIT_NODES,
-                                sm_limit=k)
+                                lane_search_words=LANE_SEARCH_WORDS, sm_limit=k)
         print(json.dumps({"sms": k, **scaling[str(k)]}), flush=True)
     ablation = {"rmat18_split_on": scaling[str(sms)],
-                "rmat18_split_off": timed(g, reps=1, rank="degen", subset=sub, blocks_per_sm=BLOCKS_PER_SM, split=False)}
+                "rmat18_split_off": timed(g, reps=1, rank="degen", subset=sub, blocks_per_sm=BLOCKS_PER_SM,
+                                             lane_search_words=LANE_SEARCH_WORDS, split=False)}
     c3 = graphgen.chung_lu_planted()
     g3 = mce.Graph(c3.n, torch.from_numpy(c3.u).cuda(), torch.from_numpy(c3.v).cuda())
     ablation["chunglu_split_on"] = timed(g3, rank="degree")
