@@ -149,14 +149,14 @@ LANE_SEARCH_WORDS = 2048
 LANE_HOLD_WAITING = 0
 
 # Counters of one k_bk launch of this workload from ncu, valid only for the
-# kernel sources they were taken with (profiles/k_bk_rmat18_sample30pct.md):
+# kernel sources they were taken with (profiles/k_bk_rmat18.md):
 # DRAM bytes (read + write) of a capture of a 30 % sample of the subproblems
 # (8 passes), scaled by tree nodes; warp instructions of a one-pass capture
 # of the whole timed launch.
-K_BK_COUNTERS = {"dram_bytes": 2_021_479_936 + 3_748_293_632, "dram_tree_nodes": 1_290_883_126,
-                 "warp_inst": 253_248_724_366, "inst_tree_nodes": 4_057_750_785,
-                 "sha256": {"bk.cu": "4c0d418e37770e4ae3ee243bce6e3a09ec3fbe980c669379be89b593370ca73c",
-                            "bk.cuh": "0783344092d66dc92f6bdce679dcf59b9e129df2f325e0716946537a1730e1da"}}
+K_BK_COUNTERS = {"dram_bytes": 207_874_816 + 297_239_040, "dram_tree_nodes": 1_290_883_126,
+                 "warp_inst": 100_342_053_550, "inst_tree_nodes": 4_057_750_785,
+                 "sha256": {"bk.cu": "42462b27ab8c6e4cb2a75af8f30d9fbb78afda0a2d2be88713c4fc8f1799127c",
+                            "bk.cuh": "d9fa8e1939f66d2b6c308311c6b18445d4626afaaa28ed2370183903ba90b2b2"}}
 
 
 def _same_sources(digests) -> bool:

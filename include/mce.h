@@ -135,12 +135,14 @@ typedef struct {
      * too and equals Algorithm 1's count on the whole graph.  rank_kind,
      * user_rank and subset are ignored. */
     int32_t whole_graph;
-    /* Streaming multiprocessors the search launch covers (0 = all), for
-     * scaling measurements; the result does not depend on it. */
+    /* Streaming multiprocessors that take search work (0 = all), for scaling
+     * measurements: the whole grid is launched and only blocks on SMs with an
+     * id below sm_limit search.  The result does not depend on it. */
     int32_t sm_limit;
     /* Per-warp shared-memory words of the lane-parallel small search (0 =
-     * automatic; values below 512 turn it off).  Shared memory comes out of
-     * the SM's L1, which also caches the per-lane search stacks. */
+     * automatic: what the block's shared memory leaves, at most 2048; values
+     * below 512 turn it off).  Shared memory comes out of the SM's L1, which
+     * also caches the lane search's node stacks. */
     int32_t lane_search_words;
     /* Learned heavy-subtree splitting: a model that predicts log(1 + search-
      * tree nodes) of each subproblem under the rank in use.  When set, the

@@ -101,7 +101,7 @@ struct BkParams {
     int32_t lp_words;         // per-warp shared words of the lane-parallel small search (0 = off)
     uint32_t *lp_tasks;       // per warp: a stack of lp_task_cap node records (BK_LP_TASK_WORDS each)
     int32_t lp_task_cap;
-    int32_t sm_limit;         // SMs the persistent grid covers (0 = all)
+    int32_t sm_limit;         // blocks on SMs with %smid >= sm_limit do no work (0 = all SMs work)
     const uint8_t *heavy;     // per vertex: 1 = predicted heavy, splits every heavy_split_nodes (or null)
     uint32_t heavy_split_nodes;
     uint32_t lp_hold_waiting; // waiting warps from which small subtrees stay with the whole warp (0 = 1)

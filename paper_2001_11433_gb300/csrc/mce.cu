@@ -224,10 +224,13 @@ LaunchShape launch_shape(const mce_opts *o) {
     else if (o->shared_words < words) words = o->shared_words & ~3;
     ls.smem_words = (int32_t)words;
     // what is left of the block's shared memory goes to the lane-parallel small
-    // search (up to 16 KB a warp; below 2 KB a warp it stays off)
+    // search, up to 8 KB a warp (below 2 KB a warp it stays off).  Measured on
+    // GB300: larger arenas take shared memory from L1, which the lane search's
+    // node stacks and the subproblem rows need more (R-MAT 18 and Chung-Lu
+    // searches 5-14 % faster at 8 KB than at 12 KB).
     if (!o || !o->warp_small_search) {
         int64_t lp = (per_block - 2048) / 4 / ls.warps_per_block - BK_PIV_WORDS - ls.smem_words;
-        if (lp > 4096) lp = 4096;
+        if (lp > 2048) lp = 2048;
         if (o && o->lane_search_words > 0 && o->lane_search_words < lp) lp = o->lane_search_words;
         lp &= ~int64_t(1);
         ls.lp_words = lp >= 512 ? (int32_t)lp : 0;

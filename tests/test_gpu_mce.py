@@ -441,8 +441,8 @@ def test_stream_rmat12_summary(gpu_lib):
 
 @pytest.mark.parametrize("rank", ["degen", "degree"])
 def test_lane_search_equals_warp_search(gpu_lib, rank):
-    """The lane-parallel small search (one small subtree per lane, closed
-    forms for one- and two-candidate children) and the whole-warp small
+    """The lane-parallel small search (nodes taken by the lanes from a shared
+    stack, closed forms for one- and two-candidate children) and the whole-warp small
     search visit the same trees: equal per-subproblem counts, hashes and node
     counts, and equal algorithmic word operations."""
     mce = gpu_lib
@@ -458,3 +458,26 @@ def test_lane_search_equals_warp_search(gpu_lib, rank):
         (b.count, b.hash, list(b.hist), b.tree_nodes, b.word_ops)
     for x, y in zip(pa, pb):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("sms", [1, 19])
+def test_sm_limit_keeps_results(gpu_lib, sms):
+    """With only the blocks on the first 1 or 19 SMs taking work, every
+    subproblem's count, hash and tree nodes equal the unrestricted run's and
+    the oracle's totals."""
+    mce = gpu_lib
+    n, u, v = rmat(12, seed=3)
+    g = gpu_graph(mce, n, u, v)
+    og = O.Graph(n, u, v)
+    ref = O.parmce(og, O.rank(og, "degen"))
+    outs = []
+    for lim in (0, sms):
+        pv = per_vertex_bufs(n)
+        r = mce.enumerate_cliques(g, rank="degen", per_vertex=pv, sm_limit=lim, split_nodes=256)
+        outs.append((r, [u64(t) for t in pv]))
+    (a, pa), (b, pb) = outs
+    assert (b.count, b.hash, b.tree_nodes) == (ref.count, ref.hash, ref.nodes)
+    assert (a.count, a.hash, list(a.hist), a.tree_nodes) == (b.count, b.hash, list(b.hist), b.tree_nodes)
+    for x, y in zip(pa, pb):
+        assert np.array_equal(x, y)
+    assert b.stats[6] <= sms * 4 * 8       # warps that took part: at most those of sms SMs
