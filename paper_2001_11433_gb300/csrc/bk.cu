@@ -2004,7 +2004,7 @@ __device__ int search(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigne
     }
 }
 
-// The same search for candidate sets wider than 64 words (more than 2048
+// The same search for candidate sets wider than 32 words (more than 1024
 // candidates, which some ranks produce for hubs): frames stay in memory and
 // every set operation loops over its words.  Returns as search<NR>.
 __device__ int search_mem(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsigned long long *shist, int lane,
@@ -2288,9 +2288,12 @@ __device__ bool run_task(const BkParams &P, Ws &s, const Task &T, Acc &acc, unsi
     __syncwarp();
 
     __syncwarp();
-    const int code = s.wc <= 32   ? search<1>(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter)
-                     : s.wc <= 64 ? search<2>(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter)
-                                  : search_mem(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter);
+    // candidate sets of up to 1024 columns keep the frame in registers; wider
+    // ones (hubs under some ranks) run with frames in memory.  A second
+    // register width was measured slower overall on GB300: the larger kernel
+    // costs instruction-fetch stalls on every node.
+    const int code = s.wc <= 32 ? search<1>(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter)
+                                : search_mem(P, s, T, acc, shist, lane, node_tick, t_start, root, k0, enter);
     return code != 1;
 }
 
