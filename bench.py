@@ -149,14 +149,13 @@ LANE_SEARCH_WORDS = 2048
 LANE_HOLD_WAITING = 0
 
 # Counters of one k_bk launch of this workload from ncu, valid only for the
-# kernel sources they were taken with (profiles/k_bk_rmat18.md):
-# DRAM bytes (read + write) of a capture of a 30 % sample of the subproblems
-# (8 passes), scaled by tree nodes; warp instructions of a one-pass capture
-# of the whole timed launch.
-K_BK_COUNTERS = {"dram_bytes": 207_874_816 + 297_239_040, "dram_tree_nodes": 1_290_883_126,
-                 "warp_inst": 100_342_053_550, "inst_tree_nodes": 4_057_750_785,
-                 "sha256": {"bk.cu": "42462b27ab8c6e4cb2a75af8f30d9fbb78afda0a2d2be88713c4fc8f1799127c",
-                            "bk.cuh": "d9fa8e1939f66d2b6c308311c6b18445d4626afaaa28ed2370183903ba90b2b2"}}
+# kernel sources they were taken with (profiles/k_bk_rmat18.md): DRAM bytes
+# (read + write) and warp instructions of one-pass captures of the whole
+# timed launch (DRAM bytes as ncu printed them, to 3 significant digits).
+K_BK_COUNTERS = {"dram_bytes": 1_100_000_000 + 896_820_000, "dram_tree_nodes": 4_057_750_785,
+                 "warp_inst": 95_709_876_787, "inst_tree_nodes": 4_057_750_785,
+                 "sha256": {"bk.cu": "32f53fb462e3b1fa3e9eac500a151b753cb0bbe334b7459c72b48e01db8c831d",
+                            "bk.cuh": "46878bf93e68a8fac1a9fd948adb51137c5b9eebc0eb2775d789126daf185cab"}}
 
 
 def _same_sources(digests) -> bool:
@@ -507,6 +506,11 @@ def run_batched(args):
     launches = mce.kernel_launches() - launches0
     clocks = sampler.stop()
     counts, hashes, status, tot = first
+    # after the timed region: the tuner again, at the full per-graph budget,
+    # to check the shape it picked from the cheaper lowered-budget runs
+    t1 = time.perf_counter()
+    bps_full, split_full = plan.tune(tune_budget=0, repeats=1)
+    tune_full_s = time.perf_counter() - t1
     ok = status == 0
     ms = float(np.mean(times))
     done_cl = int(counts[ok].sum())
@@ -529,7 +533,11 @@ def run_batched(args):
                    "node_budget_per_graph": budget, "completed": int(ok.sum()),
                    "cliques_completed": done_cl, "cliques_all": int(tot.count), "tree_nodes": int(tot.tree_nodes),
                    "tree_nodes_per_s": tot.tree_nodes / (ms / 1000.0),
-                   "tuned": {"blocks_per_sm": bps, "split_nodes": split, "tune_s": tune_s},
+                   "tuned": {"blocks_per_sm": bps, "split_nodes": split, "tune_s": tune_s,
+                             "tune_budget": max(budget // 16, 1 << 12),
+                             "best_at_full_budget": {"blocks_per_sm": bps_full, "split_nodes": split_full,
+                                                     "tune_s": tune_full_s},
+                             "pick_matches_full_budget": (bps, split) == (bps_full, split_full)},
                    "l2": "512 MB buffer written between timed steps"},
         "e2e": {"value": done_cl / (e2e_ms / 1000.0), "unit": "cliques/s", "h2d_bytes_per_step": 8 * len(w.u)
                 + 4 * len(gptr), "d2h_bytes_per_step": 20 * (len(gptr) - 1)},

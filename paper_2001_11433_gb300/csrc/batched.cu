@@ -367,7 +367,7 @@ mce_status mce_batched_tune(mce_batched *b, void *stream, uint64_t tune_budget, 
         int32_t bps;
         uint32_t split;
     };
-    const Cand cands[] = {{3, 4096}, {2, 4096}, {4, 4096}, {3, 2048}, {3, 8192}};
+    const Cand cands[] = {{2, 4096}, {2, 12288}, {2, 2048}, {3, 4096}, {3, 12288}, {4, 4096}};
     const uint64_t keep_budget = b->P.graph_budget;
     const LaunchShape keep_ls = b->ls;
     const uint32_t keep_split = b->P.split_nodes;

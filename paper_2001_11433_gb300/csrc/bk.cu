@@ -694,7 +694,7 @@ __device__ int poll(const BkParams &P, Acc &acc, int lane, int32_t root, uint64_
             const unsigned long long qlen = qt > qh ? qt - qh : 0ULL;
             // while warps wait for work, small subtrees are searched by the whole
             // warp, whose frames can be handed over
-            lph = hungry > qlen && hungry - qlen >= (unsigned long long)(P.lp_hold_waiting ? P.lp_hold_waiting : 1u);
+            lph = P.lp_hold_waiting && hungry > qlen && hungry - qlen >= (unsigned long long)P.lp_hold_waiting;
             if (qlen >= hungry) hungry = 0;
             // a subproblem predicted heavy spreads its subtree from the start
             const bool heavy = P.heavy && P.heavy[P.mode == BK_MCE ? root : 0];

@@ -104,7 +104,7 @@ struct BkParams {
     int32_t sm_limit;         // blocks on SMs with %smid >= sm_limit do no work (0 = all SMs work)
     const uint8_t *heavy;     // per vertex: 1 = predicted heavy, splits every heavy_split_nodes (or null)
     uint32_t heavy_split_nodes;
-    uint32_t lp_hold_waiting; // waiting warps from which small subtrees stay with the whole warp (0 = 1)
+    uint32_t lp_hold_waiting; // waiting warps from which small subtrees stay with the whole warp (0 = never)
 };
 
 // Words of the read-only part of a built subproblem with w local vertices of

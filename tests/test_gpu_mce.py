@@ -482,3 +482,22 @@ def test_sm_limit_keeps_results(gpu_lib, sms):
     for x, y in zip(pa, pb):
         assert np.array_equal(x, y)
     assert b.stats[6] <= sms * 4 * 8       # warps that took part: at most those of sms SMs
+
+
+def test_hold_policy_keeps_results(gpu_lib):
+    """With small subtrees kept by the whole warp while any warp waits (the
+    hold policy, off by default), and with hand-overs forced often, every
+    subproblem's count, hash and tree nodes equal the default run's."""
+    mce = gpu_lib
+    n, u, v = rmat(13, seed=11)
+    g = gpu_graph(mce, n, u, v)
+    outs = []
+    for hold in (0, 1):
+        pv = per_vertex_bufs(n)
+        r = mce.enumerate_cliques(g, rank="degen", per_vertex=pv, lane_hold_waiting=hold, split_nodes=512)
+        outs.append((r, [u64(t) for t in pv]))
+    (a, pa), (b, pb) = outs
+    assert (a.count, a.hash, list(a.hist), a.tree_nodes, a.word_ops) == \
+        (b.count, b.hash, list(b.hist), b.tree_nodes, b.word_ops)
+    for x, y in zip(pa, pb):
+        assert np.array_equal(x, y)
