@@ -476,7 +476,7 @@ def run_batched(args):
     g = mce.Graph(w.n, torch.from_numpy(w.u).cuda(), torch.from_numpy(w.v).cuda())
     plan = mce.BatchedPlan(g, gptr, node_budget=budget)
     t0 = time.perf_counter()
-    bps, split = plan.tune(tune_budget=max(budget // 16, 1 << 12), repeats=1)
+    bps, split, ws = plan.tune(tune_budget=max(budget // 16, 1 << 12), repeats=1)
     tune_s = time.perf_counter() - t0
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -509,7 +509,7 @@ def run_batched(args):
     # after the timed region: the tuner again, at the full per-graph budget,
     # to check the shape it picked from the cheaper lowered-budget runs
     t1 = time.perf_counter()
-    bps_full, split_full = plan.tune(tune_budget=0, repeats=1)
+    bps_full, split_full, ws_full = plan.tune(tune_budget=0, repeats=1)
     tune_full_s = time.perf_counter() - t1
     ok = status == 0
     ms = float(np.mean(times))
@@ -533,11 +533,11 @@ def run_batched(args):
                    "node_budget_per_graph": budget, "completed": int(ok.sum()),
                    "cliques_completed": done_cl, "cliques_all": int(tot.count), "tree_nodes": int(tot.tree_nodes),
                    "tree_nodes_per_s": tot.tree_nodes / (ms / 1000.0),
-                   "tuned": {"blocks_per_sm": bps, "split_nodes": split, "tune_s": tune_s,
+                   "tuned": {"blocks_per_sm": bps, "split_nodes": split, "warp_small_search": ws, "tune_s": tune_s,
                              "tune_budget": max(budget // 16, 1 << 12),
                              "best_at_full_budget": {"blocks_per_sm": bps_full, "split_nodes": split_full,
-                                                     "tune_s": tune_full_s},
-                             "pick_matches_full_budget": (bps, split) == (bps_full, split_full)},
+                                                     "warp_small_search": ws_full, "tune_s": tune_full_s},
+                             "pick_matches_full_budget": (bps, split, ws) == (bps_full, split_full, ws_full)},
                    "l2": "512 MB buffer written between timed steps"},
         "e2e": {"value": done_cl / (e2e_ms / 1000.0), "unit": "cliques/s", "h2d_bytes_per_step": 8 * len(w.u)
                 + 4 * len(gptr), "d2h_bytes_per_step": 20 * (len(gptr) - 1)},

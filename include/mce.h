@@ -344,10 +344,14 @@ mce_status mce_batched_run(mce_batched *b, void *stream);
 mce_status mce_batched_read(mce_batched *b, void *stream, uint64_t *counts, uint64_t *hashes, int32_t *status,
                             mce_result *total);
 /* Autotuner: times `repeats` runs of each launch shape (resident blocks per
- * SM x hand-over interval) with the per-graph budget lowered to tune_budget
- * (0 = keep it) and keeps the fastest; the choice is returned. */
+ * SM x hand-over interval x small nodes searched by the whole warp or by the
+ * lanes) with the per-graph budget lowered to tune_budget (0 = keep it) and
+ * keeps the fastest; the choice is returned (each pointer may be NULL).
+ * Without tuning, a plan with a per-graph budget searches small nodes with
+ * the whole warp unless lane_search_words > 0: the lane search finishes its
+ * buffered small subtrees even past a graph's budget. */
 mce_status mce_batched_tune(mce_batched *b, void *stream, uint64_t tune_budget, int32_t repeats,
-                            int32_t *best_blocks_per_sm, uint32_t *best_split_nodes);
+                            int32_t *best_blocks_per_sm, uint32_t *best_split_nodes, int32_t *best_warp_small);
 void mce_batched_free(mce_batched *b);
 
 /* ---------------------------------------------------------------- incremental MCE */

@@ -189,7 +189,7 @@ SIGNATURES = {
     "mce_batched_create": ([_vp, _vp, _i32, _P(Opts), _P(_vp)], _i32),
     "mce_batched_run": ([_vp, _vp], _i32),
     "mce_batched_read": ([_vp, _vp, _vp, _vp, _vp, _P(ResultC)], _i32),
-    "mce_batched_tune": ([_vp, _vp, _u64, _i32, _P(_i32), _P(ctypes.c_uint32)], _i32),
+    "mce_batched_tune": ([_vp, _vp, _u64, _i32, _P(_i32), _P(ctypes.c_uint32), _P(_i32)], _i32),
     "mce_batched_free": ([_vp], None),
     "imce_open": ([_vp, _P(Opts), _P(_vp)], _i32),
     "imce_server_opts_init": ([_P(ServerOpts)], None),
@@ -622,10 +622,11 @@ class BatchedPlan:
         return counts, hashes, status, _result(r, st)
 
     def tune(self, tune_budget=0, repeats=1):
-        bps, sp = ctypes.c_int32(), ctypes.c_uint32()
+        """Returns (blocks per SM, hand-over interval, whole-warp small search)."""
+        bps, sp, ws = ctypes.c_int32(), ctypes.c_uint32(), ctypes.c_int32()
         _check(load().mce_batched_tune(self._h, _stream_ptr(self._stream), tune_budget, repeats, ctypes.byref(bps),
-                                       ctypes.byref(sp)), "mce_batched_tune")
-        return int(bps.value), int(sp.value)
+                                       ctypes.byref(sp), ctypes.byref(ws)), "mce_batched_tune")
+        return int(bps.value), int(sp.value), bool(ws.value)
 
 
 @dataclass

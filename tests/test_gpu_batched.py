@@ -90,8 +90,8 @@ def test_plan_replay_and_tune_keep_results(gpu_lib):
         seen.append((tot.count, tot.hash, tot.tree_nodes, list(tot.hist)))
     assert seen[0] == seen[1] == seen[2]
     assert mce.kernel_launches() - before == 9      # reset, search, status per run
-    bps, split = plan.tune(tune_budget=0, repeats=1)
-    assert bps in (2, 3, 4) and split in (2048, 4096, 12288)
+    bps, split, warp_small = plan.tune(tune_budget=0, repeats=1)
+    assert bps in (2, 3, 4) and split in (4096, 8192, 12288) and warp_small in (False, True)
     plan.run()
     counts, hashes, status, tot = plan.read()
     assert (tot.count, tot.hash, tot.tree_nodes, list(tot.hist)) == seen[0]
