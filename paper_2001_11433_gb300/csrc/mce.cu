@@ -4,8 +4,10 @@
 //   2. prepass: isolated vertices are maximal cliques {v} (Algorithm 1 with
 //      cand = fini = ∅); a vertex with no higher-ranked neighbour but some
 //      lower-ranked one has an empty subproblem; the rest are scheduled;
-//   3. order the subproblems, heaviest expected first (|Γ+(v)|, then degree,
-//      or a learned cost), and run the persistent search kernel.
+//   3. order the subproblems, heaviest expected first (|Γ+(v)|^2 + 64 deg v:
+//      the search and the build, whose scan of the neighbourhood makes hubs
+//      with few candidates expensive too; or a learned cost), and run the
+//      persistent search kernel.
 #include "bk.cuh"
 #include "mce_host.h"
 
@@ -13,7 +15,6 @@ namespace mce {
 
 namespace {
 
-constexpr int32_t kCBits = 20, kWBits = 21;
 
 __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ up_ptr, int32_t n,
                               int32_t idb, uint64_t seed, const float *cost, unsigned long long *out,
@@ -68,10 +69,11 @@ __global__ void k_mce_prepass(const int32_t *__restrict__ row_ptr, const int32_t
                 b ^= (b >> 31) ? 0xffffffffu : 0x80000000u;
                 k = ((uint64_t)(~b) << idb) | (uint64_t)v;
             } else {
-                const uint64_t cc = (uint64_t)min(c, (1 << kCBits) - 1);
-                const uint64_t ww = (uint64_t)min(w, (1 << kWBits) - 1);
-                k = ((((1ULL << kCBits) - 1 - cc) << (idb + kWBits)) | (((1ULL << kWBits) - 1 - ww) << idb)) |
-                    (uint64_t)v;
+                // expected cost: the search grows with c^2 at least, the build
+                // with the neighbourhood (each of the w local vertices is scanned)
+                const uint64_t est = (uint64_t)c * (uint64_t)c + 64ULL * (uint64_t)w;
+                const uint64_t cap = (1ULL << (63 - idb)) - 1;
+                k = ((cap - (est < cap ? est : cap)) << idb) | (uint64_t)v;
             }
             keys[v] = k;
             req = max(req, (unsigned long long)bk_ws_words(w, c, BK_MCE));
@@ -367,10 +369,6 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
     cudaStream_t s = (cudaStream_t)o->stream;
     const int32_t n = g->n;
     const int32_t idb = g->id_bits;
-    if (idb > 64 - kCBits - kWBits) {
-        g_last_error = "too many vertices for the subproblem order key";
-        return MCE_EINVAL;
-    }
     cudaEvent_t e0, e1, e2;
     MCE_CUDA(cudaEventCreate(&e0));
     MCE_CUDA(cudaEventCreate(&e1));
