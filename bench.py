@@ -151,9 +151,9 @@ LANE_HOLD_WAITING = 0
 # Counters of one k_bk launch of this workload from ncu, valid only for the
 # kernel sources they were taken with (profiles/k_bk_rmat18.md): DRAM bytes
 # (read + write) and warp instructions of one-pass captures of the whole
-# timed launch (DRAM bytes as ncu printed them, to 3 significant digits).
-K_BK_COUNTERS = {"dram_bytes": 1_100_000_000 + 896_820_000, "dram_tree_nodes": 4_057_750_785,
-                 "warp_inst": 95_709_876_787, "inst_tree_nodes": 4_057_750_785,
+# timed launch.
+K_BK_COUNTERS = {"dram_bytes": 984_233_216 + 899_319_296, "dram_tree_nodes": 4_057_750_785,
+                 "warp_inst": 95_832_110_570, "inst_tree_nodes": 4_057_750_785,
                  "sha256": {"bk.cu": "32f53fb462e3b1fa3e9eac500a151b753cb0bbe334b7459c72b48e01db8c831d",
                             "bk.cuh": "46878bf93e68a8fac1a9fd948adb51137c5b9eebc0eb2775d789126daf185cab"}}
 
