@@ -97,7 +97,7 @@ typedef struct {
     uint64_t *pv_nodes;
     int32_t split;                /* 1 = split heavy subtrees across warps (default) */
     uint32_t split_nodes;         /* with split: a task hands over a piece every this many nodes even
-                                     when no warp waits (0 = 12288); pieces also go to waiting warps */
+                                     when no warp waits (0 = 4096); pieces also go to waiting warps */
     int32_t order_by_model;       /* 1 = schedule subproblems by the model's prediction */
     int32_t warps_per_block;      /* search warps per block, 1..8 (0 = 8) */
     int32_t blocks_per_sm;        /* resident search blocks per SM, 2..4 (0 = 2: 128 registers a

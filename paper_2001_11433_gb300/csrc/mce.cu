@@ -518,9 +518,10 @@ mce_status enumerate(const mce_graph *g, const mce_opts *o, mce_result *res, con
             P.sub_budget = o->subproblem_budget;
         }
         P.split = o->split;
-        // measured on GB300 with the lane search: pieces of 12,288 nodes keep
-        // the R-MAT 18 search fastest (4,096: 263 vs 221 ms) and Chung-Lu equal
-        P.split_nodes = o->split ? (o->split_nodes ? o->split_nodes : 12288u) : 0u;
+        // measured on GB300 with the lane search: 4,096 keeps every rank of the
+        // Chung-Lu graph balanced (12,288 costs the learned rank 18 %), while
+        // the R-MAT 18 benchmark set is fastest at 12,288, which it asks for
+        P.split_nodes = o->split ? (o->split_nodes ? o->split_nodes : 4096u) : 0u;
         P.sm_limit = o->sm_limit;
         P.lp_hold_waiting = o->lane_hold_waiting;
         if (heavy.p && o->split) {
