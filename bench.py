@@ -22,7 +22,8 @@ the rank comparison on the Chung-Lu 1.7M graph with planted cliques (rank
 and enumeration time per rank, learned vs degree, degeneracy and triangles,
 with makespan and imbalance: key "c3_ranks") and the incremental serving
 loop on the Chung-Lu 500k graph with its 10^6-edge stream (edges/s, p50/p99
-batch latency, per-batch latency against change size: key "c5_serving").
+batch latency, per-batch latency against change size, and the same stream
+deleted again batch by batch: key "c5_serving").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batched   # 4,096 disjoint G(n, p), batched plan
@@ -421,6 +422,7 @@ def run_ours(args):
     if not args.no_secondary:
         secondary["c3_ranks"] = measure_ranks(mce, steps=3, warmup=1)
         secondary["c5_serving"] = measure_serve(mce)
+        secondary["c5_serving"]["deletions"] = measure_deletions(mce)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -603,6 +605,50 @@ def measure_serve(mce, slots=4, load=0.7):
     }
 
 
+def measure_deletions(mce):
+    """Edge deletions (imce_remove_edges, by the reduction G = (G - H) + H):
+    the serving stream's 45 batches are added to the Chung-Lu 500k base graph
+    (untimed), then deleted again in reverse order; each deletion batch is
+    timed by the library (CUDA events around the call).  The clique set must
+    return to the base graph's (same number of alive cliques, and every
+    batch's removed cliques are the cliques its addition created)."""
+    import torch
+    import graphgen
+    w = graphgen.chung_lu_stream()
+    su, sv = w.extra["stream_u"], w.extra["stream_v"]
+    sizes = w.extra["batch_sizes"]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    g = mce.Graph(w.n, torch.from_numpy(w.u).cuda(), torch.from_numpy(w.v).cuda())
+    st = mce.Imce(g)
+    alive0 = st.add_edges(np.zeros(0, np.int32), np.zeros(0, np.int32)).alive
+    du = [torch.from_numpy(np.ascontiguousarray(su[offs[i]:offs[i + 1]])).cuda() for i in range(len(sizes))]
+    dv = [torch.from_numpy(np.ascontiguousarray(sv[offs[i]:offs[i + 1]])).cuda() for i in range(len(sizes))]
+    added = [st.add_edges(du[i], dv[i]) for i in range(len(sizes))]
+    launches0 = mce.kernel_launches()
+    dels = {}
+    for i in reversed(range(len(sizes))):
+        dels[i] = st.remove_edges(du[i], dv[i])
+    launches = mce.kernel_launches() - launches0
+    alive_end = dels[0].alive
+    st.close()
+    g.close()
+    for i in range(len(sizes)):
+        assert (dels[i].sub_count, dels[i].sub_hash) == (added[i].new_count, added[i].new_hash), i
+        assert (dels[i].new_count, dels[i].new_hash) == (added[i].sub_count, added[i].sub_hash), i
+    assert alive_end == alive0
+    ms = np.array([dels[i].ms for i in range(len(sizes))], float)
+    edges = int(sum(dels[i].applied for i in range(len(sizes))))
+    return {"batches": int(len(sizes)), "edges": edges, "device_ms_total": float(ms.sum()),
+            "edges_per_s": edges / (ms.sum() / 1000.0), "batch_ms_p50": float(np.percentile(ms, 50)),
+            "batch_ms_p99": float(np.percentile(ms, 99)),
+            "removed_cliques": int(sum(dels[i].sub_count for i in range(len(sizes)))),
+            "created_cliques": int(sum(dels[i].new_count for i in range(len(sizes)))),
+            "alive_restored": bool(alive_end == alive0), "gpu_launches": int(launches),
+            "latency_vs_change": latency_vs_change([int(sizes[i]) for i in range(len(sizes))],
+                                                   [int(dels[i].new_count + dels[i].sub_count)
+                                                    for i in range(len(sizes))], list(ms))}
+
+
 def latency_vs_change(edges, changes, ms):
     """Device time of a batch against its size and its change |Λnew| + |Λdel|
     (the analogue of the paper's latency-against-change-size figure): least-
@@ -625,6 +671,7 @@ def run_serve(args):
     sampler = ClockSampler(0)
     sampler.start()
     m = measure_serve(mce, args.slots, args.load)
+    m["deletions"] = measure_deletions(mce)
     clocks = sampler.stop()
     line = {
         "metric": "IMCE serving: edges/s and p99 batch latency (arrival to completion)",
@@ -639,6 +686,7 @@ def run_serve(args):
         "cliques": {"new": m["new_cliques"], "subsumed": m["subsumed_cliques"], "alive_after": m["alive_after"],
                     "applied_edges": m["applied_edges"]},
         "device_ms_total": m["device_ms_total"],
+        "deletions": m["deletions"],
         "e2e": {"value": m["edges_per_s"], "unit": "edges/s", "h2d_bytes_per_step": int(8 * m["stream_edges"] /
                                                                                        m["batches"]),
                 "d2h_bytes_per_step": 2 * 8 * (1024 + 8)},
